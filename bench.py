@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""ANLS-BPP NMF benchmark: iterations per second of the whole per-iteration hot
+path (Gram H H^T, A H^T, BPP for W, Gram W^T W, W^T A, BPP for H, objective)
+on one GB300, with roofline, clocks, end-to-end and CPU-oracle numbers.
+
+Default workload: the dense 96000 x 64000, k = 50 recipe (A = W0 H0 +
+|N(0, 0.05^2)|, 24.6 GB FP32, inputs larger than L2), warm-started BPP.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16x3]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+With N > 1 (torchrun), every rank runs an independent replica of the workload
+(the method has no exchange step on one GPU: replicas only); value counts the
+iterations of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (m, n, k, sigma, description)
+    "dense-large": (96000, 64000, 50, 0.05,
+                    "dense A=W0*H0+|N(0,0.05^2)| 96000x64000 k=50 fp32 (24.6 GB)"),
+    "dense-small": (2000, 1000, 10, 0.01,
+                    "dense A=W0*H0+|N(0,0.01^2)| 2000x1000 k=10 fp32"),
+}
+SEED = 1509
+METRIC = "ANLS-BPP iterations/s"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+# DRAM traffic per launch (read + write bytes) of the dominant kernel from one
+# ncu capture, keyed by (kernel, workload, precision); None until captured or
+# when the kernel changed since.
+NCU_TRAFFIC = {}
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as fh:
+            p = json.load(fh)
+        return p, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def oracle_sample(m, n, k, sigma, steps, warm: bool):
+    """Time the FP64 oracle (as it stands) on a crop of the workload and scale
+    to the full size by m*n (the products and objective dominate; they scale
+    with m*n, the NLS work with m+n). Returns (iter/s full-size, sample text,
+    threads, seconds per sample step)."""
+    import oracle
+    import synth
+    ms, ns = (min(m, 6000), min(n, 4000)) if m * n > 6000 * 4000 else (m, n)
+    A = synth.dense_planted(ms, ns, k, sigma, seed=SEED, n_full=n)
+    W0, Ht0 = synth.init_factors(ms, ns, k, seed=SEED)
+    orc = oracle.default()
+    r = orc.anls(A, W0, Ht0, iters=1, warm=warm)        # warm-up (first iteration)
+    t0 = time.perf_counter()
+    orc.anls(A, r["W"].astype("float32"), r["Ht"].astype("float32"), iters=steps, warm=warm)
+    dt = (time.perf_counter() - t0) / steps
+    scale = (m * n) / (ms * ns)
+    sample = (f"oracle ANLS iterations on the {ms}x{ns} crop of the same recipe (k={k}), "
+              f"{steps} iterations, time per iteration x {scale:.1f} (m*n ratio)")
+    return 1.0 / (dt * scale), sample, orc.num_threads(), dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    m, n, k, sigma, desc = WORKLOADS[args.workload]
+    import oracle
+    oracle.build()
+    steps = max(1, args.steps)
+    value, sample, cores, dt = oracle_sample(m, n, k, sigma, steps, args.start == "warm")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s",
+            "n_gpus": world, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "start": args.start},
+            "cpu_baseline": {"value": value, "unit": "iter/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1509_09313_gb300 as nmf
+    import synth
+    from synth import torch_gen
+
+    m, n, k, sigma, desc = WORKLOADS[args.workload]
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+
+    t_gen = time.perf_counter()
+    A = torch_gen.dense_planted_device(m, n, k, sigma, SEED, dev)
+    W0h, Ht0h = synth.init_factors(m, n, k, seed=SEED)
+    W0 = torch.from_numpy(W0h).to(dev)
+    Ht0 = torch.from_numpy(Ht0h).to(dev)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+
+    h = nmf.nmf_init(A, W0, Ht0, precision=args.precision, start=args.start,
+                     max_bpp_rounds=args.max_rounds, objective_every=True)
+    h.nmf_iterate(args.warmup)
+    warm_status = h.nmf_sync()
+    st0 = h.nmf_get_stats()
+    h.nmf_set_timing(True)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    sampler = ClockSampler(local_rank)
+    torch.cuda.synchronize()
+    barrier()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h.nmf_iterate(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    status = h.nmf_sync()
+    st1 = h.nmf_get_stats()
+    f_hist = h.nmf_objective_history()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1000.0)
+
+    # Roofline of the dominant kernel (the two m*n*k products), from the
+    # handle's per-phase CUDA events over the timed region.
+    launches_mm = 2 * args.steps
+    mm_ms = (st1["ms_mm"] - st0["ms_mm"]) / launches_mm
+    nls_ms = (st1["ms_nls"] - st0["ms_nls"]) / launches_mm
+    gram_ms = (st1["ms_gram"] - st0["ms_gram"]) / launches_mm
+    obj_ms = (st1["ms_objective"] - st0["ms_objective"]) / args.steps
+    pk, pk_kind = peaks()
+    bytes_mm = 4.0 * m * n + 4.0 * (m + n) * k     # A once + factor in + product out
+    flops_mm = 2.0 * m * n * k
+    if args.precision == "fp32":
+        fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        achieved = flops_mm / (mm_ms / 1000.0) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "kernel": "mm_simt_kernel",
+                "peak_source": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                               f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max clock)",
+                "achieved_gbs": bytes_mm / (mm_ms / 1000.0) / 1e9}
+    else:
+        achieved = bytes_mm / (mm_ms / 1000.0) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "kernel": "mm_tc_kernel",
+                "peak_source": f"{pk_kind} hbm_gbs",
+                "achieved_tflops": flops_mm / (mm_ms / 1000.0) / 1e12}
+    roof["traffic"] = NCU_TRAFFIC.get((roof["kernel"], args.workload, args.precision))
+
+    # End to end through the public API from pinned host memory: upload A and the
+    # starting point, nmf_init, K iterations, download W, H^T and the objective.
+    e2e = None
+    if not args.no_e2e:
+        A_host = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
+        A_host.copy_(A)
+        W0_host = torch.from_numpy(W0h).pin_memory()
+        Ht0_host = torch.from_numpy(Ht0h).pin_memory()
+        W_out = torch.empty((m, k), dtype=torch.float32, pin_memory=True)
+        Ht_out = torch.empty((n, k), dtype=torch.float32, pin_memory=True)
+        h.nmf_destroy()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        A.copy_(A_host, non_blocking=True)
+        W0.copy_(W0_host, non_blocking=True)
+        Ht0.copy_(Ht0_host, non_blocking=True)
+        h2 = nmf.nmf_init(A, W0, Ht0, precision=args.precision, start=args.start,
+                          max_bpp_rounds=args.max_rounds, objective_every=True)
+        h2.nmf_iterate(args.steps)
+        Wd, Htd = h2.nmf_get_factors()
+        W_out.copy_(Wd, non_blocking=True)
+        Ht_out.copy_(Htd, non_blocking=True)
+        f_e2e = h2.nmf_objective_history()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        barrier()
+        if world > 1:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        h2.nmf_destroy()
+        h2d = 4 * (m * n + (m + n) * k)
+        d2h = 4 * (m + n) * k + 8 * len(f_e2e)
+        e2e = {"value": world * args.steps / dt, "unit": "iter/s",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "note": "upload A + start, nmf_init, K iterations, download W, H^T, objective"}
+    else:
+        h.nmf_destroy()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sample, cores, _ = oracle_sample(m, n, k, sigma, args.cpu_steps, args.start == "warm")
+        cpu = {"value": v, "unit": "iter/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        rounds = st1["bpp_rounds"] - st0["bpp_rounds"]
+        rhs = st1["bpp_rhs"] - st0["bpp_rhs"]
+        line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.precision == "fp32" else "bf16x3/f32",
+                "data": "synthetic",
+                "config": {"workload": desc, "precision": args.precision, "start": args.start,
+                           "seed": SEED, "l2": "inputs larger than L2 (A = 24.6 GB)"
+                           if args.workload == "dense-large" else "small input (L2-resident)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
+                "phase_ms_per_launch": {"mm": mm_ms, "nls": nls_ms, "gram": gram_ms,
+                                        "objective": obj_ms},
+                "bpp": {"rounds_per_rhs": rounds / max(rhs, 1),
+                        "fp64_solves": st1["bpp_fp64_solves"] - st0["bpp_fp64_solves"],
+                        "fp64_halfsteps": st1["bpp_fp64_halfsteps"] - st0["bpp_fp64_halfsteps"],
+                        "status": nmf.nmf_status_str(status),
+                        "warmup_status": nmf.nmf_status_str(warm_status)},
+                "objective_last": f_hist[-1] if f_hist else None,
+                "setup_s": {"generate": t_gen}}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "bf16x3"], default="fp32")
+    ap.add_argument("--start", choices=["cold", "warm"], default="warm")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dense-large")
+    ap.add_argument("--max-rounds", type=int, default=100)
+    ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local_rank = env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * nmf_gb300.h - C ABI of the single-GPU (sm_103a) ANLS-NMF / BPP library.
+ *
+ * The library computes the per-iteration hot path of alternating nonnegative
+ * least squares NMF with block principal pivoting, after Kannan, Ballard and
+ * Park, "A High-Performance Parallel Algorithm for Nonnegative Matrix
+ * Factorization" (arXiv 1509.09313):
+ *
+ *   minimise f(W, H) = ||A - W H||_F^2 over W >= 0 (m x k), H >= 0 (k x n)
+ *   (Eq. 1), by the two-block scheme of Eq. 2 / Alg. 1: each iteration updates
+ *   W from (H H^T, A H^T), then H from (W^T W, W^T A), every row of W and
+ *   column of H being one NLS problem (Eq. 3) solved by BPP (Sec. 4.2).
+ *
+ * Conventions for every call:
+ *   - All matrices are row-major. H is always passed and stored as H^T
+ *     (n x k), so that each right-hand side of either half-step is one
+ *     contiguous k-vector.
+ *   - Pointers documented as "device" must point to memory the current CUDA
+ *     device can read/write (cudaMalloc'd, or managed). "host" pointers are
+ *     ordinary CPU memory. The library never frees memory it did not allocate.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Calls are asynchronous on that stream unless stated otherwise.
+ *   - Arguments are validated on the host before anything is launched; an
+ *     invalid argument returns NMF_ERR_INVALID_ARG and launches nothing.
+ *     No call aborts the process, traps on the device or spins without bound.
+ *   - 1 <= k <= NMF_MAX_K.
+ */
+#ifndef NMF_GB300_H
+#define NMF_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NMF_MAX_K 128
+
+typedef enum nmf_status {
+    NMF_OK = 0,
+    NMF_ERR_INVALID_ARG = 1,   /* bad size, null pointer, unsupported mode */
+    NMF_ERR_CUDA = 2,          /* a CUDA runtime call or launch failed */
+    NMF_ERR_OOM = 3,           /* device allocation failed */
+    NMF_ERR_NOT_CONVERGED = 4, /* a BPP solve hit its exchange-round cap */
+    NMF_ERR_SINGULAR_GRAM = 5, /* a passive-set system was singular even in FP64 */
+    NMF_ERR_NONFINITE = 6      /* NaN/Inf met in an input or a result */
+} nmf_status;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *nmf_status_str(nmf_status s);
+
+/* Arithmetic used for the two m*n*k products (A H^T and W^T A) and for the
+ * objective:
+ *   NMF_PREC_FP32   plain FP32 FMAs on the SIMT pipes;
+ *   NMF_PREC_BF16X3 tensor cores (tcgen05): each FP32 operand is split into a
+ *                   BF16 head and a BF16 tail and three products are summed in
+ *                   FP32 (head*head + head*tail + tail*head). */
+typedef enum nmf_precision { NMF_PREC_FP32 = 0, NMF_PREC_BF16X3 = 1 } nmf_precision;
+
+/* ===================================================================== *
+ * Stand-alone local kernels. These are the three local tasks the paper times
+ * separately (Sec. 6.2, "Time Breakdown"): MM, Gram and NLS.
+ * ===================================================================== */
+
+/* Gram (Alg. 1: H H^T and W^T W).
+ *   X      device, rows x k float32 row-major (X = H^T gives H H^T, X = W gives
+ *          W^T W).
+ *   G      device, k x k float64 output, the full symmetric matrix X^T X.
+ * FP32 products summed in FP32 over short row tiles, tiles summed in FP64 in a
+ * fixed order (bitwise reproducible). rows = 0 gives G = 0. */
+nmf_status nmf_gram(const float *X, int64_t rows, int32_t k, double *G, void *stream);
+
+/* Dense products of Alg. 1 (the "MM" task).
+ *   A      device, m x n float32 row-major, leading dimension lda >= n.
+ *   F      device, float32 row-major factor:
+ *            trans = 0: F = H^T (n x k), out = A H^T       (m x k);
+ *            trans = 1: F = W   (m x k), out = A^T W = (W^T A)^T (n x k).
+ *   out    device float32 row-major, no aliasing with A or F.
+ *   precision  an nmf_precision value.
+ * Zero-sized m or n is allowed (out is zero-filled when the contraction length
+ * is 0). */
+nmf_status nmf_mm_dense(const float *A, int64_t m, int64_t n, int64_t lda, const float *F,
+                        int32_t k, int32_t trans, int32_t precision, float *out, void *stream);
+
+/* Sparse product with a CSR matrix (the "MM" task, sparse case of Sec. 4.3):
+ *   out (rows x k) = S F, S given by rowptr (rows+1, int64, rowptr[0] = 0),
+ *   colidx (int32, in [0, cols)), vals (float32), all device; F (cols x k) device.
+ * For A H^T pass the CSR of A and F = H^T; for (W^T A)^T pass the CSR of A^T
+ * and F = W (nmf_csr_transpose builds it). Empty rows give zero rows. */
+nmf_status nmf_mm_csr(const int64_t *rowptr, const int32_t *colidx, const float *vals,
+                      int64_t rows, int64_t cols, const float *F, int32_t k, float *out,
+                      void *stream);
+
+/* CSR transpose on the device: (rowptr, colidx, vals) of an m x n matrix with
+ * nnz entries -> (t_rowptr (n+1), t_colidx (nnz), t_vals (nnz)) of its
+ * transpose, columns of every output row in increasing order (deterministic).
+ * All pointers device; output buffers caller-allocated. */
+nmf_status nmf_csr_transpose(const int64_t *rowptr, const int32_t *colidx, const float *vals,
+                             int64_t m, int64_t n, int64_t nnz, int64_t *t_rowptr,
+                             int32_t *t_colidx, float *t_vals, void *stream);
+
+/* Batched NLS by block principal pivoting (Eq. 3, Eq. 4, Sec. 4.2): for every
+ * row b_j of B,   x_j = argmin_{x >= 0} 0.5 x^T G x - b_j^T x,
+ * i.e. Eq. 3 in normal-equations form with G = C^T C and b_j = C^T (rhs j).
+ * Exchange rules: full exchange of all infeasible indices while their number
+ * drops, up to three further full exchanges otherwise, then single exchange
+ * of the largest infeasible index. Indices with G_ii <= 0 stay active. */
+typedef struct nmf_nls_desc {
+    int32_t k;                 /* problem size, 1..NMF_MAX_K */
+    int64_t nrhs;              /* number of right-hand sides (>= 0) */
+    const double *G;           /* device, k x k float64, symmetric PSD */
+    const float *B;            /* device, nrhs x k float32 (one RHS per row) */
+    float *X;                  /* device, nrhs x k float32 output */
+    const uint64_t *passive_in;/* device, nullable: nrhs x ceil(k/64) bitmasks
+                                  (bit i of word i/64 set = index i passive);
+                                  non-null selects a warm start */
+    uint64_t *passive_out;     /* device, nullable: final passive sets, same layout */
+    int32_t *rounds_out;       /* device, nullable: exchange rounds per RHS */
+    int8_t *status_out;        /* device, nullable: per-RHS nmf_status */
+    int32_t max_rounds;        /* exchange-round cap per RHS (>= 0) */
+} nmf_nls_desc;
+
+/* Runs asynchronously on `stream`, then waits for it and returns the worst
+ * per-RHS status (NMF_OK, NMF_ERR_NOT_CONVERGED or NMF_ERR_SINGULAR_GRAM).
+ * A failing right-hand side never changes the others' results. Uses a small
+ * internal device workspace (stream-ordered allocation, freed on return). */
+nmf_status nmf_nls_bpp(const nmf_nls_desc *d, void *stream);
+
+/* Objective of Eq. 1 for dense A: f = sum_ij (A_ij - w_i . h_j)^2 with W
+ * (m x k) and H^T (n x k), all device; the residuals are formed in FP32 and
+ * their squares summed in FP64. Synchronises `stream`; writes *f_out (host). */
+nmf_status nmf_objective_dense(const float *A, int64_t m, int64_t n, int64_t lda,
+                               const float *W, const float *Ht, int32_t k, int32_t precision,
+                               double *f_out, void *stream);
+
+/* ===================================================================== *
+ * Whole ANLS iterations (Alg. 1) on a handle.
+ * ===================================================================== */
+
+typedef struct nmf_handle nmf_handle;
+
+typedef enum nmf_input_kind { NMF_INPUT_DENSE = 0, NMF_INPUT_CSR = 1 } nmf_input_kind;
+
+/* How each BPP solve picks its first passive set: empty (cold, the cited
+ * method's start) or the row's final passive set from the previous iteration
+ * (warm). Either way the solution is the same unique minimiser. */
+typedef enum nmf_start_mode { NMF_START_COLD = 0, NMF_START_WARM = 1 } nmf_start_mode;
+
+typedef struct nmf_config {
+    int64_t m, n;              /* A is m x n */
+    int32_t k;                 /* rank, 1..NMF_MAX_K */
+    int32_t input_kind;        /* nmf_input_kind */
+    int32_t precision;         /* nmf_precision for the products and objective */
+    int32_t start_mode;        /* nmf_start_mode */
+    int32_t max_bpp_rounds;    /* per-RHS exchange cap (e.g. 100) */
+    int32_t objective_every;   /* 1: f after every iteration (history kept);
+                                  0: only on nmf_objective() */
+} nmf_config;
+
+/* The input matrix. Its device buffers are BORROWED: the caller keeps them
+ * alive and unchanged until nmf_destroy. */
+typedef struct nmf_matrix {
+    const float *dense;        /* NMF_INPUT_DENSE: m x n float32, device */
+    int64_t lda;               /* leading dimension >= n */
+    const int64_t *rowptr;     /* NMF_INPUT_CSR: m+1 int64, device */
+    const int32_t *colidx;     /* nnz int32, device */
+    const float *vals;         /* nnz float32, device */
+    int64_t nnz;
+} nmf_matrix;
+
+/* Per-handle counters, cumulative since nmf_init (or the last reset). */
+typedef struct nmf_stats {
+    int64_t iterations;        /* ANLS iterations run */
+    int64_t bpp_rhs;           /* right-hand sides solved */
+    int64_t bpp_rounds;        /* exchange rounds summed over all solves */
+    int64_t bpp_max_rounds;    /* largest round count of one solve */
+    int64_t bpp_fp64_solves;   /* passive-set systems redone in FP64 */
+    int64_t bpp_fp64_halfsteps;/* half-steps solved in FP64 (cond_1(G) > 1e4) */
+    int64_t bpp_not_converged; /* solves that hit the round cap */
+    int64_t bpp_singular;      /* solves left singular in FP64 */
+    double ms_gram, ms_mm, ms_nls, ms_objective; /* GPU time per task (timing on) */
+    int64_t kernel_launches;   /* CUDA kernels this handle has launched */
+} nmf_stats;
+
+/* Create a handle. W0 (m x k) and Ht0 (n x k) are the device starting point
+ * (Alg. 1 initialises H with a nonnegative matrix; W0 is only used as the
+ * value W holds before its first update). They are copied; the handle owns
+ * W, H^T, the Grams, right-hand-side buffers, passive-set bitmasks, the
+ * transposed CSR (sparse input) and all other workspace. The handle's work
+ * is issued on `stream`. Synchronises `stream` before returning. */
+nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nmf_matrix *A,
+                    const float *W0, const float *Ht0, void *stream);
+
+/* Run `iters` ANLS iterations asynchronously on the handle's stream. Each
+ * iteration: Gram H H^T, A H^T, BPP for W, Gram W^T W, W^T A, BPP for H, and
+ * (objective_every = 1) f(W, H). Returns NMF_OK once launched; solve failures
+ * are counted in nmf_stats and reported by nmf_sync. */
+nmf_status nmf_iterate(nmf_handle *h, int32_t iters);
+
+/* Wait for the handle's stream; return the worst BPP status since the last
+ * nmf_sync (NMF_OK, NMF_ERR_NOT_CONVERGED or NMF_ERR_SINGULAR_GRAM). */
+nmf_status nmf_sync(nmf_handle *h);
+
+/* f(W, H) of Eq. 1 for the current factors. Synchronises; *f_out is host. */
+nmf_status nmf_objective(nmf_handle *h, double *f_out);
+
+/* Objective history: f after each iteration run with objective_every = 1, in
+ * order, up to `cap` values copied into `f_host` (host); *count gets the
+ * number copied. Synchronises. */
+nmf_status nmf_objective_history(nmf_handle *h, double *f_host, int64_t cap, int64_t *count);
+
+/* Copy the current factors out to (W m x k, Ht n x k) device buffers, or in
+ * from them (checkpoint / resume). Either pointer may be NULL to skip it.
+ * Asynchronous on the handle's stream. Setting factors clears the warm-start
+ * passive sets. */
+nmf_status nmf_get_factors(nmf_handle *h, float *W, float *Ht);
+nmf_status nmf_set_factors(nmf_handle *h, const float *W, const float *Ht);
+
+/* Passive-set bitmasks of the last solves (device, m or n rows of
+ * ceil(k/64) words). */
+nmf_status nmf_get_passive(nmf_handle *h, uint64_t *pW, uint64_t *pH);
+
+/* Counters; synchronises. timing != 0 turns per-task CUDA-event timing on for
+ * later iterations (adds event records, no host waits inside nmf_iterate). */
+nmf_status nmf_get_stats(nmf_handle *h, nmf_stats *out);
+nmf_status nmf_set_timing(nmf_handle *h, int32_t timing);
+
+/* Release everything the handle owns. NULL is ignored. */
+void nmf_destroy(nmf_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NMF_GB300_H */

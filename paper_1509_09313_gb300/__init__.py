@@ -1,0 +1,380 @@
+"""Python binding of the sm_103a ANLS-NMF library (``libnmf_gb300.so``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C ABI declared in ``include/nmf_gb300.h``; PyTorch supplies
+device memory and streams. The functions carry the C names. Importing this
+module loads the library and raises ImportError if it has not been built
+(``python -c "import __graft_entry__ as g; g.build()"``); there is no CPU path.
+
+Method: ANLS-NMF with block principal pivoting (Kannan, Ballard, Park,
+arXiv 1509.09313): minimise ||A - W H||_F^2 over W, H >= 0 (Eq. 1) by
+alternating exact NLS updates of W and H (Eq. 2, Alg. 1), each row solved by
+BPP (Sec. 4.2). H is passed and stored as H^T (n x k).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnmf_gb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run __graft_entry__.build() first")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+NMF_OK = 0
+NMF_ERR_INVALID_ARG = 1
+NMF_ERR_CUDA = 2
+NMF_ERR_OOM = 3
+NMF_ERR_NOT_CONVERGED = 4
+NMF_ERR_SINGULAR_GRAM = 5
+NMF_ERR_NONFINITE = 6
+
+NMF_PREC_FP32 = 0
+NMF_PREC_BF16X3 = 1
+NMF_INPUT_DENSE = 0
+NMF_INPUT_CSR = 1
+NMF_START_COLD = 0
+NMF_START_WARM = 1
+NMF_MAX_K = 128
+
+PRECISIONS = {"fp32": NMF_PREC_FP32, "bf16x3": NMF_PREC_BF16X3}
+
+
+class NMFError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {nmf_status_str(status)}")
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+
+
+class nmf_nls_desc(ctypes.Structure):
+    _fields_ = [("k", _I32), ("nrhs", _I64), ("G", _P), ("B", _P), ("X", _P),
+                ("passive_in", _P), ("passive_out", _P), ("rounds_out", _P),
+                ("status_out", _P), ("max_rounds", _I32)]
+
+
+class nmf_config(ctypes.Structure):
+    _fields_ = [("m", _I64), ("n", _I64), ("k", _I32), ("input_kind", _I32),
+                ("precision", _I32), ("start_mode", _I32), ("max_bpp_rounds", _I32),
+                ("objective_every", _I32)]
+
+
+class nmf_matrix(ctypes.Structure):
+    _fields_ = [("dense", _P), ("lda", _I64), ("rowptr", _P), ("colidx", _P), ("vals", _P),
+                ("nnz", _I64)]
+
+
+class nmf_stats(ctypes.Structure):
+    _fields_ = [("iterations", _I64), ("bpp_rhs", _I64), ("bpp_rounds", _I64),
+                ("bpp_max_rounds", _I64), ("bpp_fp64_solves", _I64), ("bpp_fp64_halfsteps", _I64),
+                ("bpp_not_converged", _I64), ("bpp_singular", _I64),
+                ("ms_gram", ctypes.c_double), ("ms_mm", ctypes.c_double),
+                ("ms_nls", ctypes.c_double), ("ms_objective", ctypes.c_double),
+                ("kernel_launches", _I64)]
+
+
+def _sig(name, args, res=ctypes.c_int):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_lib.nmf_status_str.argtypes = [ctypes.c_int]
+_lib.nmf_status_str.restype = ctypes.c_char_p
+_c_gram = _sig("nmf_gram", [_P, _I64, _I32, _P, _P])
+_c_mm_dense = _sig("nmf_mm_dense", [_P, _I64, _I64, _I64, _P, _I32, _I32, _I32, _P, _P])
+_c_mm_csr = _sig("nmf_mm_csr", [_P, _P, _P, _I64, _I64, _P, _I32, _P, _P])
+_c_csr_transpose = _sig("nmf_csr_transpose", [_P, _P, _P, _I64, _I64, _I64, _P, _P, _P, _P])
+_c_nls_bpp = _sig("nmf_nls_bpp", [ctypes.POINTER(nmf_nls_desc), _P])
+_c_objective_dense = _sig("nmf_objective_dense",
+                          [_P, _I64, _I64, _I64, _P, _P, _I32, _I32,
+                           ctypes.POINTER(ctypes.c_double), _P])
+_c_init = _sig("nmf_init", [ctypes.POINTER(_P), ctypes.POINTER(nmf_config),
+                            ctypes.POINTER(nmf_matrix), _P, _P, _P])
+_c_iterate = _sig("nmf_iterate", [_P, _I32])
+_c_sync = _sig("nmf_sync", [_P])
+_c_objective = _sig("nmf_objective", [_P, ctypes.POINTER(ctypes.c_double)])
+_c_history = _sig("nmf_objective_history", [_P, _P, _I64, ctypes.POINTER(_I64)])
+_c_get_factors = _sig("nmf_get_factors", [_P, _P, _P])
+_c_set_factors = _sig("nmf_set_factors", [_P, _P, _P])
+_c_get_passive = _sig("nmf_get_passive", [_P, _P, _P])
+_c_get_stats = _sig("nmf_get_stats", [_P, ctypes.POINTER(nmf_stats)])
+_c_set_timing = _sig("nmf_set_timing", [_P, _I32])
+_lib.nmf_destroy.argtypes = [_P]
+_lib.nmf_destroy.restype = None
+
+EXPORTED = ["nmf_status_str", "nmf_gram", "nmf_mm_dense", "nmf_mm_csr", "nmf_csr_transpose",
+            "nmf_nls_bpp", "nmf_objective_dense", "nmf_init", "nmf_iterate", "nmf_sync",
+            "nmf_objective", "nmf_objective_history", "nmf_get_factors", "nmf_set_factors",
+            "nmf_get_passive", "nmf_get_stats", "nmf_set_timing", "nmf_destroy"]
+
+
+def nmf_status_str(status: int) -> str:
+    return _lib.nmf_status_str(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status != NMF_OK:
+        raise NMFError(status, what)
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else t.data_ptr()
+
+
+def _dev(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _prec(precision) -> int:
+    return PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+
+
+def nmf_gram(X: torch.Tensor, stream=None) -> torch.Tensor:
+    """G = X^T X (k x k, float64) for X (rows x k, float32)."""
+    _dev(X, torch.float32, "X")
+    rows, k = X.shape
+    G = torch.empty((k, k), dtype=torch.float64, device=X.device)
+    _check(_c_gram(_ptr(X), rows, k, _ptr(G), _stream(stream)), "nmf_gram")
+    return G
+
+
+def nmf_mm_dense(A: torch.Tensor, F: torch.Tensor, trans: bool, precision="fp32",
+                 out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """trans=False: A @ F with F = H^T (n x k) -> m x k.  trans=True: A^T @ F with
+    F = W (m x k) -> n x k. A may have a row stride > n (2-D view)."""
+    if A.dtype != torch.float32 or not A.is_cuda or A.dim() != 2 or A.stride(1) != 1:
+        raise TypeError("A must be a row-major float32 CUDA matrix")
+    _dev(F, torch.float32, "F")
+    m, n = A.shape
+    k = F.shape[1]
+    rows = n if trans else m
+    if out is None:
+        out = torch.empty((rows, k), dtype=torch.float32, device=A.device)
+    _check(_c_mm_dense(_ptr(A), m, n, A.stride(0), _ptr(F), k, int(trans), _prec(precision),
+                       _ptr(out), _stream(stream)), "nmf_mm_dense")
+    return out
+
+
+def nmf_mm_csr(rowptr, colidx, vals, cols: int, F: torch.Tensor, out=None,
+               stream=None) -> torch.Tensor:
+    """out (rows x k) = S F for S in CSR (int64 rowptr, int32 colidx, float32 vals)."""
+    _dev(rowptr, torch.int64, "rowptr")
+    _dev(colidx, torch.int32, "colidx")
+    _dev(vals, torch.float32, "vals")
+    _dev(F, torch.float32, "F")
+    rows = rowptr.numel() - 1
+    k = F.shape[1]
+    if out is None:
+        out = torch.empty((rows, k), dtype=torch.float32, device=F.device)
+    _check(_c_mm_csr(_ptr(rowptr), _ptr(colidx), _ptr(vals), rows, cols, _ptr(F), k, _ptr(out),
+                     _stream(stream)), "nmf_mm_csr")
+    return out
+
+
+def nmf_csr_transpose(rowptr, colidx, vals, m: int, n: int, stream=None):
+    _dev(rowptr, torch.int64, "rowptr")
+    _dev(colidx, torch.int32, "colidx")
+    _dev(vals, torch.float32, "vals")
+    nnz = colidx.numel()
+    dev = rowptr.device
+    t_rowptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    t_colidx = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)[:nnz]
+    t_vals = torch.empty(max(nnz, 1), dtype=torch.float32, device=dev)[:nnz]
+    _check(_c_csr_transpose(_ptr(rowptr), _ptr(colidx), _ptr(vals), m, n, nnz, _ptr(t_rowptr),
+                            _ptr(t_colidx), _ptr(t_vals), _stream(stream)), "nmf_csr_transpose")
+    return t_rowptr, t_colidx, t_vals
+
+
+def nmf_nls_bpp(G: torch.Tensor, B: torch.Tensor, passive_in: torch.Tensor | None = None,
+                max_rounds: int = 100, outputs: bool = True, stream=None):
+    """Batched BPP: each row b of B gives argmin_{x>=0} 0.5 x^T G x - b^T x.
+
+    G: k x k float64 (CUDA); B: nrhs x k float32. passive_in: nrhs x ceil(k/64)
+    int64 bitmasks (warm start) or None (cold). Returns dict(X, passive, rounds,
+    status (per RHS), worst (aggregate status))."""
+    _dev(G, torch.float64, "G")
+    _dev(B, torch.float32, "B")
+    nrhs, k = B.shape
+    nwords = (k + 63) // 64
+    dev = B.device
+    X = torch.empty_like(B)
+    passive = rounds = status = None
+    if outputs:
+        passive = torch.empty((nrhs, nwords), dtype=torch.int64, device=dev)
+        rounds = torch.empty(nrhs, dtype=torch.int32, device=dev)
+        status = torch.empty(nrhs, dtype=torch.int8, device=dev)
+    if passive_in is not None:
+        _dev(passive_in, torch.int64, "passive_in")
+    d = nmf_nls_desc(k, nrhs, _ptr(G), _ptr(B), _ptr(X), _ptr(passive_in), _ptr(passive),
+                     _ptr(rounds), _ptr(status), max_rounds)
+    worst = _c_nls_bpp(ctypes.byref(d), _stream(stream))
+    if worst in (NMF_ERR_INVALID_ARG, NMF_ERR_CUDA, NMF_ERR_OOM):
+        raise NMFError(worst, "nmf_nls_bpp")
+    return dict(X=X, passive=passive, rounds=rounds, status=status, worst=worst)
+
+
+def nmf_objective_dense(A: torch.Tensor, W: torch.Tensor, Ht: torch.Tensor, precision="fp32",
+                        stream=None) -> float:
+    if A.dtype != torch.float32 or not A.is_cuda or A.dim() != 2 or A.stride(1) != 1:
+        raise TypeError("A must be a row-major float32 CUDA matrix")
+    _dev(W, torch.float32, "W")
+    _dev(Ht, torch.float32, "Ht")
+    f = ctypes.c_double(0.0)
+    m, n = A.shape
+    _check(_c_objective_dense(_ptr(A), m, n, A.stride(0), _ptr(W), _ptr(Ht), W.shape[1],
+                              _prec(precision), ctypes.byref(f), _stream(stream)),
+           "nmf_objective_dense")
+    return f.value
+
+
+class nmf_init:
+    """An ANLS handle (``nmf_init`` ... ``nmf_destroy``).
+
+    A: dense float32 CUDA matrix (m x n, row stride >= n) or a CSR tuple
+    (rowptr int64, colidx int32, vals float32) with ``shape=(m, n)``. The input
+    tensors are borrowed and kept referenced by the handle. W0 (m x k) and
+    Ht0 (n x k) float32 CUDA: starting point (copied)."""
+
+    def __init__(self, A, W0: torch.Tensor, Ht0: torch.Tensor, precision="fp32",
+                 start="cold", max_bpp_rounds: int = 100, objective_every: bool = True,
+                 shape=None, stream=None):
+        _dev(W0, torch.float32, "W0")
+        _dev(Ht0, torch.float32, "Ht0")
+        m, k = W0.shape
+        n = Ht0.shape[0]
+        mat = nmf_matrix()
+        if isinstance(A, torch.Tensor):
+            if A.dtype != torch.float32 or not A.is_cuda or A.stride(1) != 1:
+                raise TypeError("A must be a row-major float32 CUDA matrix")
+            if tuple(A.shape) != (m, n):
+                raise ValueError("A shape does not match W0 / Ht0")
+            mat.dense = A.data_ptr()
+            mat.lda = A.stride(0)
+            kind = NMF_INPUT_DENSE
+        else:
+            rowptr, colidx, vals = A
+            _dev(rowptr, torch.int64, "rowptr")
+            _dev(colidx, torch.int32, "colidx")
+            _dev(vals, torch.float32, "vals")
+            if shape is None or tuple(shape) != (m, n) or rowptr.numel() != m + 1:
+                raise ValueError("CSR input needs shape=(m, n) matching W0 / Ht0")
+            mat.rowptr, mat.colidx, mat.vals = _ptr(rowptr), _ptr(colidx), _ptr(vals)
+            mat.nnz = colidx.numel()
+            kind = NMF_INPUT_CSR
+        self._A = A   # keep the borrowed input alive
+        self.shape = (m, n, k)
+        self.device = W0.device
+        cfg = nmf_config(m, n, k, kind, _prec(precision),
+                         NMF_START_WARM if start == "warm" else NMF_START_COLD,
+                         max_bpp_rounds, int(bool(objective_every)))
+        self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
+        h = _P()
+        _check(_c_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.byref(mat), _ptr(W0), _ptr(Ht0),
+                       _stream(self._stream_obj)), "nmf_init")
+        self._h = h
+
+    def nmf_iterate(self, iters: int = 1):
+        _check(_c_iterate(self._h, iters), "nmf_iterate")
+
+    def nmf_sync(self) -> int:
+        s = _c_sync(self._h)
+        if s in (NMF_ERR_INVALID_ARG, NMF_ERR_CUDA, NMF_ERR_OOM):
+            raise NMFError(s, "nmf_sync")
+        return s
+
+    def nmf_objective(self) -> float:
+        f = ctypes.c_double(0.0)
+        _check(_c_objective(self._h, ctypes.byref(f)), "nmf_objective")
+        return f.value
+
+    def nmf_objective_history(self, cap: int = 1 << 16):
+        buf = (ctypes.c_double * cap)()
+        cnt = _I64(0)
+        _check(_c_history(self._h, ctypes.cast(buf, _P), cap, ctypes.byref(cnt)),
+               "nmf_objective_history")
+        return list(buf[:cnt.value])
+
+    def nmf_get_factors(self):
+        m, n, k = self.shape
+        W = torch.empty((m, k), dtype=torch.float32, device=self.device)
+        Ht = torch.empty((n, k), dtype=torch.float32, device=self.device)
+        _check(_c_get_factors(self._h, _ptr(W), _ptr(Ht)), "nmf_get_factors")
+        self._stream_obj.synchronize()
+        return W, Ht
+
+    def nmf_set_factors(self, W=None, Ht=None):
+        if W is not None:
+            _dev(W, torch.float32, "W")
+        if Ht is not None:
+            _dev(Ht, torch.float32, "Ht")
+        _check(_c_set_factors(self._h, _ptr(W), _ptr(Ht)), "nmf_set_factors")
+        self._stream_obj.synchronize()
+
+    def nmf_get_passive(self):
+        m, n, k = self.shape
+        nw = (k + 63) // 64
+        pW = torch.empty((m, nw), dtype=torch.int64, device=self.device)
+        pH = torch.empty((n, nw), dtype=torch.int64, device=self.device)
+        _check(_c_get_passive(self._h, _ptr(pW), _ptr(pH)), "nmf_get_passive")
+        self._stream_obj.synchronize()
+        return pW, pH
+
+    def nmf_get_stats(self) -> dict:
+        st = nmf_stats()
+        _check(_c_get_stats(self._h, ctypes.byref(st)), "nmf_get_stats")
+        return {name: getattr(st, name) for name, _ in nmf_stats._fields_}
+
+    def nmf_set_timing(self, on: bool = True):
+        _check(_c_set_timing(self._h, int(bool(on))), "nmf_set_timing")
+
+    def nmf_destroy(self):
+        if getattr(self, "_h", None):
+            _lib.nmf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.nmf_destroy()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+
+def passive_to_bool(words: torch.Tensor, k: int) -> torch.Tensor:
+    """Unpack nrhs x ceil(k/64) int64 bitmasks into an nrhs x k bool tensor."""
+    w = words.to(torch.int64)
+    bits = torch.arange(64, device=w.device, dtype=torch.int64)
+    out = ((w.unsqueeze(-1) >> bits) & 1).bool().reshape(w.shape[0], -1)
+    return out[:, :k]
+
+
+def bool_to_passive(P: torch.Tensor) -> torch.Tensor:
+    """Pack an nrhs x k bool tensor into nrhs x ceil(k/64) int64 bitmasks."""
+    nrhs, k = P.shape
+    nw = (k + 63) // 64
+    pad = torch.zeros((nrhs, nw * 64), dtype=torch.int64, device=P.device)
+    pad[:, :k] = P.to(torch.int64)
+    bits = torch.arange(64, device=P.device, dtype=torch.int64)
+    return (pad.reshape(nrhs, nw, 64) << bits).sum(dim=-1)

@@ -1,0 +1,613 @@
+// C ABI of the library (include/nmf_gb300.h): argument checks, workspace
+// management, and the ANLS iteration of Alg. 1 / Eq. 2 on a handle.
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace nmf {
+
+nmf_status launch_csr_transpose(const int64_t *rowptr, const int32_t *colidx, const float *vals,
+                                int64_t m, int64_t n, int64_t nnz, int64_t *t_rowptr,
+                                int32_t *t_colidx, float *t_vals, unsigned long long *cursor,
+                                cudaStream_t s);
+
+unsigned long long launch_count = 0;
+
+nmf_status from_cuda(cudaError_t e, const char *what)
+{
+    (void)what;
+    cudaGetLastError();   // clear a sticky launch error so later calls can proceed
+    return e == cudaErrorMemoryAllocation ? NMF_ERR_OOM : NMF_ERR_CUDA;
+}
+
+}  // namespace nmf
+
+using namespace nmf;
+
+namespace {
+
+cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+bool bad_k(int32_t k) { return k < 1 || k > NMF_MAX_K; }
+
+// Stream-ordered temporary device buffer, freed on scope exit (also
+// stream-ordered), for the stand-alone entry points.
+struct TempBuf {
+    void *p = nullptr;
+    cudaStream_t s;
+    explicit TempBuf(cudaStream_t st) : s(st) {}
+    cudaError_t alloc(size_t bytes) { return cudaMallocAsync(&p, bytes ? bytes : 16, s); }
+    ~TempBuf()
+    {
+        if (p)
+            cudaFreeAsync(p, s);
+    }
+};
+
+}  // namespace
+
+extern "C" const char *nmf_status_str(nmf_status s)
+{
+    switch (s) {
+    case NMF_OK: return "NMF_OK";
+    case NMF_ERR_INVALID_ARG: return "NMF_ERR_INVALID_ARG";
+    case NMF_ERR_CUDA: return "NMF_ERR_CUDA";
+    case NMF_ERR_OOM: return "NMF_ERR_OOM";
+    case NMF_ERR_NOT_CONVERGED: return "NMF_ERR_NOT_CONVERGED";
+    case NMF_ERR_SINGULAR_GRAM: return "NMF_ERR_SINGULAR_GRAM";
+    case NMF_ERR_NONFINITE: return "NMF_ERR_NONFINITE";
+    }
+    return "NMF_ERR_UNKNOWN";
+}
+
+extern "C" nmf_status nmf_gram(const float *X, int64_t rows, int32_t k, double *G, void *stream)
+{
+    if (bad_k(k) || rows < 0 || !G || (rows > 0 && !X))
+        return NMF_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    TempBuf part(s);
+    NMF_CUDA(part.alloc(sizeof(double) * (size_t)gram_partials_len(rows, k)));
+    return launch_gram(X, rows, k, G, static_cast<double *>(part.p), s);
+}
+
+extern "C" nmf_status nmf_mm_dense(const float *A, int64_t m, int64_t n, int64_t lda,
+                                   const float *F, int32_t k, int32_t trans, int32_t precision,
+                                   float *out, void *stream)
+{
+    if (bad_k(k) || m < 0 || n < 0 || lda < n || (trans != 0 && trans != 1))
+        return NMF_ERR_INVALID_ARG;
+    if (precision != NMF_PREC_FP32 && precision != NMF_PREC_BF16X3)
+        return NMF_ERR_INVALID_ARG;
+    const int64_t P = trans ? n : m, Q = trans ? m : n;
+    if (P == 0)
+        return NMF_OK;
+    if (!out || (Q > 0 && (!A || !F)))
+        return NMF_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    if (precision == NMF_PREC_BF16X3) {
+        const size_t wb = mm_tc_work_bytes(m, n, k, trans);
+        TempBuf w(s);
+        NMF_CUDA(w.alloc(wb));
+        return launch_mm_tc(A, m, n, lda, F, k, trans, out, w.p, wb, s);
+    }
+    return launch_mm_simt(A, m, n, lda, F, k, trans, out, s);
+}
+
+extern "C" nmf_status nmf_mm_csr(const int64_t *rowptr, const int32_t *colidx, const float *vals,
+                                 int64_t rows, int64_t cols, const float *F, int32_t k,
+                                 float *out, void *stream)
+{
+    if (bad_k(k) || rows < 0 || cols < 0)
+        return NMF_ERR_INVALID_ARG;
+    if (rows == 0)
+        return NMF_OK;
+    if (!rowptr || !out || !F || !colidx || !vals)
+        return NMF_ERR_INVALID_ARG;
+    return launch_spmm(rowptr, colidx, vals, rows, F, k, out, as_stream(stream));
+}
+
+extern "C" nmf_status nmf_csr_transpose(const int64_t *rowptr, const int32_t *colidx,
+                                        const float *vals, int64_t m, int64_t n, int64_t nnz,
+                                        int64_t *t_rowptr, int32_t *t_colidx, float *t_vals,
+                                        void *stream)
+{
+    if (m < 0 || n < 0 || nnz < 0 || !t_rowptr || !rowptr)
+        return NMF_ERR_INVALID_ARG;
+    if (nnz > 0 && (!colidx || !vals || !t_colidx || !t_vals))
+        return NMF_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    TempBuf cur(s);
+    NMF_CUDA(cur.alloc(sizeof(unsigned long long) * (size_t)(n > 0 ? n : 1)));
+    return launch_csr_transpose(rowptr, colidx, vals, m, n, nnz, t_rowptr, t_colidx, t_vals,
+                                static_cast<unsigned long long *>(cur.p), s);
+}
+
+static nmf_status worst_from_stats(const BppStats &st)
+{
+    if (st.nonfinite)
+        return NMF_ERR_NONFINITE;
+    if (st.singular)
+        return NMF_ERR_SINGULAR_GRAM;
+    if (st.not_converged)
+        return NMF_ERR_NOT_CONVERGED;
+    return NMF_OK;
+}
+
+extern "C" nmf_status nmf_nls_bpp(const nmf_nls_desc *d, void *stream)
+{
+    if (!d || bad_k(d->k) || d->nrhs < 0 || d->max_rounds < 0 || !d->G)
+        return NMF_ERR_INVALID_ARG;
+    if (d->nrhs > 0 && (!d->B || !d->X))
+        return NMF_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    TempBuf w(s), st(s);
+    NMF_CUDA(w.alloc(bpp_work_bytes(d->k)));
+    NMF_CUDA(st.alloc(sizeof(BppStats)));
+    NMF_CUDA(cudaMemsetAsync(st.p, 0, sizeof(BppStats), s));
+    NMF_TRY(launch_bpp(d->k, d->nrhs, d->G, d->B, d->X, d->passive_in, d->passive_out,
+                       d->rounds_out, d->status_out, d->max_rounds, w.p,
+                       static_cast<BppStats *>(st.p), s));
+    BppStats host;
+    NMF_CUDA(cudaMemcpyAsync(&host, st.p, sizeof(BppStats), cudaMemcpyDeviceToHost, s));
+    NMF_CUDA(cudaStreamSynchronize(s));
+    return worst_from_stats(host);
+}
+
+extern "C" nmf_status nmf_objective_dense(const float *A, int64_t m, int64_t n, int64_t lda,
+                                          const float *W, const float *Ht, int32_t k,
+                                          int32_t precision, double *f_out, void *stream)
+{
+    if (bad_k(k) || m < 0 || n < 0 || lda < n || !f_out)
+        return NMF_ERR_INVALID_ARG;
+    if (precision != NMF_PREC_FP32 && precision != NMF_PREC_BF16X3)
+        return NMF_ERR_INVALID_ARG;
+    if (m > 0 && n > 0 && (!A || !W || !Ht))
+        return NMF_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    TempBuf part(s), f(s);
+    NMF_CUDA(part.alloc(sizeof(double) * (size_t)objective_partials_len()));
+    NMF_CUDA(f.alloc(sizeof(double)));
+    NMF_TRY(launch_objective_dense(A, m, n, lda, W, Ht, k, precision,
+                                   static_cast<double *>(part.p), static_cast<double *>(f.p), s));
+    NMF_CUDA(cudaMemcpyAsync(f_out, f.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+    NMF_CUDA(cudaStreamSynchronize(s));
+    return NMF_OK;
+}
+
+// ===========================================================================
+// Handle: whole ANLS iterations.
+// ===========================================================================
+
+struct nmf_handle {
+    nmf_config cfg;
+    nmf_matrix A;
+    cudaStream_t stream;
+    int nwords;
+    // Owned device buffers.
+    float *W = nullptr, *Ht = nullptr;          // factors (m x k, n x k)
+    float *V = nullptr, *Y = nullptr;           // right-hand sides (m x k, n x k)
+    double *GH = nullptr, *GW = nullptr;        // Grams (k x k)
+    uint64_t *pW = nullptr, *pH = nullptr;      // passive sets
+    void *bpp_work = nullptr;
+    BppStats *stats_dev = nullptr;
+    double *gram_part = nullptr;
+    double *obj_part = nullptr;
+    double *f_hist = nullptr;                   // ring of objective values
+    double *f_now = nullptr;
+    void *tc_work = nullptr;
+    size_t tc_work_bytes = 0;
+    int64_t *t_rowptr = nullptr;                // CSR of A^T (sparse input)
+    int32_t *t_colidx = nullptr;
+    float *t_vals = nullptr;
+    // Host state.
+    bool passive_valid = false;
+    int64_t f_count = 0;
+    int64_t iterations = 0;
+    BppStats reported{};                        // stats already turned into a status
+    bool timing = false;
+    int64_t launches = 0;                       // kernels launched by nmf_iterate / objective
+    double ms[4] = {0, 0, 0, 0};                // gram, mm, nls, objective
+    struct Pending {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+};
+
+static constexpr int64_t F_HIST_CAP = 1 << 16;
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (count ? count : 1));
+}
+
+cudaEvent_t take_event(nmf_handle *h)
+{
+    if (!h->pool.empty()) {
+        cudaEvent_t e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct PhaseTimer {
+    nmf_handle *h;
+    int phase;
+    cudaEvent_t a = nullptr;
+    PhaseTimer(nmf_handle *hh, int ph) : h(hh), phase(ph)
+    {
+        if (h->timing) {
+            a = take_event(h);
+            cudaEventRecord(a, h->stream);
+        }
+    }
+    ~PhaseTimer()
+    {
+        if (h->timing) {
+            cudaEvent_t b = take_event(h);
+            cudaEventRecord(b, h->stream);
+            h->pending.push_back({phase, a, b});
+        }
+    }
+};
+
+void collect_timing(nmf_handle *h)
+{
+    for (auto &p : h->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
+            h->ms[p.phase] += ms;
+        h->pool.push_back(p.a);
+        h->pool.push_back(p.b);
+    }
+    h->pending.clear();
+}
+
+nmf_status mm(nmf_handle *h, int trans, const float *F, float *out)
+{
+    const nmf_config &c = h->cfg;
+    if (c.input_kind == NMF_INPUT_CSR) {
+        if (trans == 0)
+            return launch_spmm(h->A.rowptr, h->A.colidx, h->A.vals, c.m, F, c.k, out, h->stream);
+        return launch_spmm(h->t_rowptr, h->t_colidx, h->t_vals, c.n, F, c.k, out, h->stream);
+    }
+    if (c.precision == NMF_PREC_BF16X3)
+        return launch_mm_tc(h->A.dense, c.m, c.n, h->A.lda, F, c.k, trans, out, h->tc_work,
+                            h->tc_work_bytes, h->stream);
+    return launch_mm_simt(h->A.dense, c.m, c.n, h->A.lda, F, c.k, trans, out, h->stream);
+}
+
+nmf_status objective_into(nmf_handle *h, double *f_dev)
+{
+    const nmf_config &c = h->cfg;
+    if (c.input_kind == NMF_INPUT_CSR) {
+        NMF_TRY(launch_gram(h->Ht, c.n, c.k, h->GH, h->gram_part, h->stream));
+        NMF_TRY(launch_gram(h->W, c.m, c.k, h->GW, h->gram_part, h->stream));
+        return launch_objective_csr(h->A.rowptr, h->A.colidx, h->A.vals, c.m, h->W, h->Ht, c.k,
+                                    h->GW, h->GH, h->obj_part, f_dev, h->stream);
+    }
+    return launch_objective_dense(h->A.dense, c.m, c.n, h->A.lda, h->W, h->Ht, c.k, c.precision,
+                                  h->obj_part, f_dev, h->stream);
+}
+
+nmf_status one_iteration(nmf_handle *h)
+{
+    const nmf_config &c = h->cfg;
+    const bool warm = c.start_mode == NMF_START_WARM && h->passive_valid;
+    // W <- argmin_{W >= 0} ||A - W H||: Gram H H^T, right-hand sides A H^T.
+    {
+        PhaseTimer t(h, 0);
+        NMF_TRY(launch_gram(h->Ht, c.n, c.k, h->GH, h->gram_part, h->stream));
+    }
+    {
+        PhaseTimer t(h, 1);
+        NMF_TRY(mm(h, 0, h->Ht, h->V));
+    }
+    {
+        PhaseTimer t(h, 2);
+        NMF_TRY(launch_bpp(c.k, c.m, h->GH, h->V, h->W, warm ? h->pW : nullptr, h->pW, nullptr,
+                           nullptr, c.max_bpp_rounds, h->bpp_work, h->stats_dev, h->stream));
+    }
+    // H <- argmin_{H >= 0} ||A - W H||: Gram W^T W, right-hand sides (W^T A)^T.
+    {
+        PhaseTimer t(h, 0);
+        NMF_TRY(launch_gram(h->W, c.m, c.k, h->GW, h->gram_part, h->stream));
+    }
+    {
+        PhaseTimer t(h, 1);
+        NMF_TRY(mm(h, 1, h->W, h->Y));
+    }
+    {
+        PhaseTimer t(h, 2);
+        NMF_TRY(launch_bpp(c.k, c.n, h->GW, h->Y, h->Ht, warm ? h->pH : nullptr, h->pH, nullptr,
+                           nullptr, c.max_bpp_rounds, h->bpp_work, h->stats_dev, h->stream));
+    }
+    h->passive_valid = true;
+    if (c.objective_every) {
+        PhaseTimer t(h, 3);
+        NMF_TRY(objective_into(h, h->f_hist + (h->f_count % F_HIST_CAP)));
+        h->f_count += 1;
+    }
+    h->iterations += 1;
+    return NMF_OK;
+}
+
+void free_handle(nmf_handle *h)
+{
+    cudaFree(h->W);
+    cudaFree(h->Ht);
+    cudaFree(h->V);
+    cudaFree(h->Y);
+    cudaFree(h->GH);
+    cudaFree(h->GW);
+    cudaFree(h->pW);
+    cudaFree(h->pH);
+    cudaFree(h->bpp_work);
+    cudaFree(h->stats_dev);
+    cudaFree(h->gram_part);
+    cudaFree(h->obj_part);
+    cudaFree(h->f_hist);
+    cudaFree(h->f_now);
+    cudaFree(h->tc_work);
+    cudaFree(h->t_rowptr);
+    cudaFree(h->t_colidx);
+    cudaFree(h->t_vals);
+    for (auto &p : h->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : h->pool)
+        cudaEventDestroy(e);
+    delete h;
+}
+
+}  // namespace
+
+extern "C" nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nmf_matrix *A,
+                               const float *W0, const float *Ht0, void *stream)
+{
+    if (!out || !cfg || !A || !W0 || !Ht0)
+        return NMF_ERR_INVALID_ARG;
+    *out = nullptr;
+    const nmf_config c = *cfg;
+    if (bad_k(c.k) || c.m < 1 || c.n < 1 || c.max_bpp_rounds < 0)
+        return NMF_ERR_INVALID_ARG;
+    if (c.precision != NMF_PREC_FP32 && c.precision != NMF_PREC_BF16X3)
+        return NMF_ERR_INVALID_ARG;
+    if (c.start_mode != NMF_START_COLD && c.start_mode != NMF_START_WARM)
+        return NMF_ERR_INVALID_ARG;
+    if (c.input_kind == NMF_INPUT_DENSE) {
+        if (!A->dense || A->lda < c.n)
+            return NMF_ERR_INVALID_ARG;
+    } else if (c.input_kind == NMF_INPUT_CSR) {
+        if (!A->rowptr || A->nnz < 0 || (A->nnz > 0 && (!A->colidx || !A->vals)))
+            return NMF_ERR_INVALID_ARG;
+    } else {
+        return NMF_ERR_INVALID_ARG;
+    }
+    nmf_handle *h = new nmf_handle();
+    h->cfg = c;
+    h->A = *A;
+    h->stream = as_stream(stream);
+    h->nwords = (c.k + 63) / 64;
+    const size_t k = (size_t)c.k;
+    const int64_t rmax = c.m > c.n ? c.m : c.n;
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t r) {
+        if (e == cudaSuccess)
+            e = r;
+    };
+    chk(dalloc(&h->W, (size_t)c.m * k));
+    chk(dalloc(&h->Ht, (size_t)c.n * k));
+    chk(dalloc(&h->V, (size_t)c.m * k));
+    chk(dalloc(&h->Y, (size_t)c.n * k));
+    chk(dalloc(&h->GH, k * k));
+    chk(dalloc(&h->GW, k * k));
+    chk(dalloc(&h->pW, (size_t)c.m * h->nwords));
+    chk(dalloc(&h->pH, (size_t)c.n * h->nwords));
+    chk(cudaMalloc(&h->bpp_work, bpp_work_bytes(c.k)));
+    chk(dalloc(&h->stats_dev, 1));
+    chk(dalloc(&h->gram_part, (size_t)gram_partials_len(rmax, c.k)));
+    chk(dalloc(&h->obj_part, (size_t)objective_partials_len()));
+    chk(dalloc(&h->f_hist, (size_t)F_HIST_CAP));
+    chk(dalloc(&h->f_now, 1));
+    if (e == cudaSuccess && c.input_kind == NMF_INPUT_DENSE && c.precision == NMF_PREC_BF16X3) {
+        h->tc_work_bytes = mm_tc_work_bytes(c.m, c.n, c.k, 0);
+        const size_t b1 = mm_tc_work_bytes(c.m, c.n, c.k, 1);
+        if (b1 > h->tc_work_bytes)
+            h->tc_work_bytes = b1;
+        chk(cudaMalloc(&h->tc_work, h->tc_work_bytes ? h->tc_work_bytes : 16));
+    }
+    if (e == cudaSuccess && c.input_kind == NMF_INPUT_CSR) {
+        chk(dalloc(&h->t_rowptr, (size_t)c.n + 1));
+        chk(dalloc(&h->t_colidx, (size_t)A->nnz));
+        chk(dalloc(&h->t_vals, (size_t)A->nnz));
+    }
+    if (e != cudaSuccess) {
+        free_handle(h);
+        return from_cuda(e, "nmf_init alloc");
+    }
+    nmf_status st = NMF_OK;
+    auto run = [&]() -> nmf_status {
+        NMF_CUDA(cudaMemsetAsync(h->stats_dev, 0, sizeof(BppStats), h->stream));
+        NMF_CUDA(cudaMemsetAsync(h->pW, 0, sizeof(uint64_t) * (size_t)c.m * h->nwords, h->stream));
+        NMF_CUDA(cudaMemsetAsync(h->pH, 0, sizeof(uint64_t) * (size_t)c.n * h->nwords, h->stream));
+        NMF_CUDA(cudaMemcpyAsync(h->W, W0, sizeof(float) * (size_t)c.m * k,
+                                 cudaMemcpyDeviceToDevice, h->stream));
+        NMF_CUDA(cudaMemcpyAsync(h->Ht, Ht0, sizeof(float) * (size_t)c.n * k,
+                                 cudaMemcpyDeviceToDevice, h->stream));
+        if (c.input_kind == NMF_INPUT_CSR) {
+            unsigned long long *cursor = nullptr;
+            NMF_CUDA(cudaMallocAsync(&cursor, sizeof(unsigned long long) * (size_t)c.n,
+                                     h->stream));
+            nmf_status s2 = launch_csr_transpose(A->rowptr, A->colidx, A->vals, c.m, c.n, A->nnz,
+                                                 h->t_rowptr, h->t_colidx, h->t_vals, cursor,
+                                                 h->stream);
+            cudaFreeAsync(cursor, h->stream);
+            NMF_TRY(s2);
+        }
+        NMF_CUDA(cudaStreamSynchronize(h->stream));
+        return NMF_OK;
+    };
+    st = run();
+    if (st != NMF_OK) {
+        free_handle(h);
+        return st;
+    }
+    *out = h;
+    return NMF_OK;
+}
+
+extern "C" nmf_status nmf_iterate(nmf_handle *h, int32_t iters)
+{
+    if (!h || iters < 0)
+        return NMF_ERR_INVALID_ARG;
+    const unsigned long long before = launch_count;
+    nmf_status st = NMF_OK;
+    for (int32_t t = 0; t < iters && st == NMF_OK; ++t)
+        st = one_iteration(h);
+    h->launches += (int64_t)(launch_count - before);
+    return st;
+}
+
+extern "C" nmf_status nmf_sync(nmf_handle *h)
+{
+    if (!h)
+        return NMF_ERR_INVALID_ARG;
+    BppStats st;
+    NMF_CUDA(cudaMemcpyAsync(&st, h->stats_dev, sizeof(BppStats), cudaMemcpyDeviceToHost,
+                             h->stream));
+    NMF_CUDA(cudaStreamSynchronize(h->stream));
+    BppStats delta = st;
+    delta.not_converged -= h->reported.not_converged;
+    delta.singular -= h->reported.singular;
+    delta.nonfinite -= h->reported.nonfinite;
+    h->reported = st;
+    return worst_from_stats(delta);
+}
+
+extern "C" nmf_status nmf_objective(nmf_handle *h, double *f_out)
+{
+    if (!h || !f_out)
+        return NMF_ERR_INVALID_ARG;
+    const unsigned long long before = launch_count;
+    const nmf_status st = objective_into(h, h->f_now);
+    h->launches += (int64_t)(launch_count - before);
+    NMF_TRY(st);
+    NMF_CUDA(cudaMemcpyAsync(f_out, h->f_now, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    NMF_CUDA(cudaStreamSynchronize(h->stream));
+    return NMF_OK;
+}
+
+extern "C" nmf_status nmf_objective_history(nmf_handle *h, double *f_host, int64_t cap,
+                                            int64_t *count)
+{
+    if (!h || !count || cap < 0 || (cap > 0 && !f_host))
+        return NMF_ERR_INVALID_ARG;
+    NMF_CUDA(cudaStreamSynchronize(h->stream));
+    const int64_t avail = h->f_count < F_HIST_CAP ? h->f_count : F_HIST_CAP;
+    const int64_t nout = avail < cap ? avail : cap;
+    const int64_t first = h->f_count - nout;   // oldest value copied
+    for (int64_t q = 0; q < nout; ++q) {
+        const int64_t slot = (first + q) % F_HIST_CAP;
+        NMF_CUDA(cudaMemcpy(f_host + q, h->f_hist + slot, sizeof(double),
+                            cudaMemcpyDeviceToHost));
+    }
+    *count = nout;
+    return NMF_OK;
+}
+
+extern "C" nmf_status nmf_get_factors(nmf_handle *h, float *W, float *Ht)
+{
+    if (!h)
+        return NMF_ERR_INVALID_ARG;
+    const size_t k = (size_t)h->cfg.k;
+    if (W)
+        NMF_CUDA(cudaMemcpyAsync(W, h->W, sizeof(float) * (size_t)h->cfg.m * k,
+                                 cudaMemcpyDeviceToDevice, h->stream));
+    if (Ht)
+        NMF_CUDA(cudaMemcpyAsync(Ht, h->Ht, sizeof(float) * (size_t)h->cfg.n * k,
+                                 cudaMemcpyDeviceToDevice, h->stream));
+    return NMF_OK;
+}
+
+extern "C" nmf_status nmf_set_factors(nmf_handle *h, const float *W, const float *Ht)
+{
+    if (!h)
+        return NMF_ERR_INVALID_ARG;
+    const size_t k = (size_t)h->cfg.k;
+    if (W)
+        NMF_CUDA(cudaMemcpyAsync(h->W, W, sizeof(float) * (size_t)h->cfg.m * k,
+                                 cudaMemcpyDeviceToDevice, h->stream));
+    if (Ht)
+        NMF_CUDA(cudaMemcpyAsync(h->Ht, Ht, sizeof(float) * (size_t)h->cfg.n * k,
+                                 cudaMemcpyDeviceToDevice, h->stream));
+    h->passive_valid = false;
+    return NMF_OK;
+}
+
+extern "C" nmf_status nmf_get_passive(nmf_handle *h, uint64_t *pW, uint64_t *pH)
+{
+    if (!h)
+        return NMF_ERR_INVALID_ARG;
+    if (pW)
+        NMF_CUDA(cudaMemcpyAsync(pW, h->pW, sizeof(uint64_t) * (size_t)h->cfg.m * h->nwords,
+                                 cudaMemcpyDeviceToDevice, h->stream));
+    if (pH)
+        NMF_CUDA(cudaMemcpyAsync(pH, h->pH, sizeof(uint64_t) * (size_t)h->cfg.n * h->nwords,
+                                 cudaMemcpyDeviceToDevice, h->stream));
+    return NMF_OK;
+}
+
+extern "C" nmf_status nmf_get_stats(nmf_handle *h, nmf_stats *out)
+{
+    if (!h || !out)
+        return NMF_ERR_INVALID_ARG;
+    BppStats st;
+    NMF_CUDA(cudaMemcpyAsync(&st, h->stats_dev, sizeof(BppStats), cudaMemcpyDeviceToHost,
+                             h->stream));
+    NMF_CUDA(cudaStreamSynchronize(h->stream));
+    collect_timing(h);
+    memset(out, 0, sizeof(*out));
+    out->iterations = h->iterations;
+    out->bpp_rhs = (int64_t)st.rhs;
+    out->bpp_rounds = (int64_t)st.rounds;
+    out->bpp_max_rounds = (int64_t)st.max_rounds;
+    out->bpp_fp64_solves = (int64_t)st.fp64_solves;
+    out->bpp_fp64_halfsteps = (int64_t)st.fp64_halfsteps;
+    out->bpp_not_converged = (int64_t)st.not_converged;
+    out->bpp_singular = (int64_t)st.singular;
+    out->ms_gram = h->ms[0];
+    out->ms_mm = h->ms[1];
+    out->ms_nls = h->ms[2];
+    out->ms_objective = h->ms[3];
+    out->kernel_launches = h->launches;
+    return NMF_OK;
+}
+
+extern "C" nmf_status nmf_set_timing(nmf_handle *h, int32_t timing)
+{
+    if (!h)
+        return NMF_ERR_INVALID_ARG;
+    h->timing = timing != 0;
+    return NMF_OK;
+}
+
+extern "C" void nmf_destroy(nmf_handle *h)
+{
+    if (!h)
+        return;
+    cudaStreamSynchronize(h->stream);
+    free_handle(h);
+}

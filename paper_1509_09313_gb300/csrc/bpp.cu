@@ -1,0 +1,870 @@
+// Batched NLS by block principal pivoting (Eq. 3, Eq. 4, Sec. 4.2).
+//
+// Every right-hand side j solves  min_{x >= 0} 0.5 x^T G x - g_j^T x  with one
+// shared k x k Gram G. BPP partitions the indices into a passive set F (free)
+// and an active set (x_i = 0); for a partition the candidate is
+//   x_F = G_FF^{-1} g_F, x_A = 0, y = G x - g (y_F = 0),
+// and the exchange rules of the cited method (full exchange while the number
+// of infeasible indices drops, three more full exchanges otherwise, then the
+// backup single exchange of the largest infeasible index) move infeasible
+// indices (x_i < 0 on F, y_i < 0 off F) across until Eq. 4 holds.
+//
+// GPU design (differs from the paper's column grouping; same result):
+//  * bpp_prep_kernel (one CTA, FP64) factors the usable part of G once per
+//    half-step (G = L L^T; indices with G_ii <= 0 are never passive), forms
+//    M = G^{-1} and cond_1(G) = ||G||_1 ||M||_1, and picks the arithmetic of
+//    the solves: FP32 when cond_1(G) <= 1e4 (mode 0), FP64 otherwise (mode 1),
+//    FP64 without M when G is numerically singular (mode 2).
+//  * bpp_solve_kernel: persistent, one warp per right-hand side, G and M in
+//    shared memory. Lane l holds indices l, l+32, ... of g, x, y and of the
+//    unconstrained solution u = M g. Each exchange round solves the smaller of
+//    two equivalent systems:
+//      direct      G_FF x_F = g_F                          (|F| x |F|)
+//      complement  M_AA y_A = -u_A,  x_F = u_F + M_FA y_A  (|A| x |A|)
+//    (the second follows from G x = g + y with y supported on A and x_A = 0),
+//    by a warp-cooperative Cholesky in shared memory with shuffle-broadcast
+//    substitutions, then refines once (residual g_F - G_FF x_F solved through
+//    the same factor: the explicit inverse alone is not backward stable) and
+//    recomputes y from G. Cost per round O(min(|F|,|A|)^3 + k |F|) instead of
+//    O(|F|^3). In FP32 a pivot below 1e-4 of its diagonal sends that system to
+//    FP64, and a sign test counts as violated only beyond 2^-20 of the
+//    problem's scale (max |x| on F, max |g| off F): values within FP32 noise
+//    of zero are degenerate ties that would otherwise make the exchange rules
+//    cycle. The final x is clamped at 0 there. FP64 modes use the strict test.
+//  * Every loop is bounded: a solve stops at max_rounds with status
+//    NOT_CONVERGED; there are no spin-waits.
+//
+// Roofline: FP32 ALU for the pivoting; HBM traffic is nrhs * k * 8 bytes
+// (right-hand sides in, solutions out) plus bitmasks.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace nmf {
+namespace {
+
+constexpr int BPP_WARPS = 8;
+constexpr int BPP_THREADS = BPP_WARPS * 32;
+constexpr int RHS_CHUNK = 8;
+constexpr float PIVOT_TOL = 1e-4f;
+constexpr double PIVOT_TOL64 = 1e-13;
+constexpr double COND_FP32 = 1e4;          // cond_1(G) up to which solves run in FP32
+constexpr float FEAS_TOL32 = 9.5367431640625e-07f;   // 2^-20
+
+// Workspace layout (bytes, 256-aligned pieces).
+struct WorkLayout {
+    size_t g32, m32, m64, usable, flags, counter, total;
+};
+
+WorkLayout layout(int k)
+{
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    WorkLayout w;
+    size_t off = 0;
+    w.g32 = off; off += al(sizeof(float) * k * k);
+    w.m32 = off; off += al(sizeof(float) * k * k);
+    w.m64 = off; off += al(sizeof(double) * k * k);
+    w.usable = off; off += al(sizeof(uint32_t) * 4);
+    w.flags = off; off += al(sizeof(int) * 4);
+    w.counter = off; off += al(sizeof(unsigned long long));
+    w.total = off;
+    return w;
+}
+
+// ---------------------------------------------------------------------------
+// Prep: FP64 Cholesky of G_UU, its inverse and cond_1; one CTA.
+// flags[0] = mode (0 FP32, 1 FP64 with M, 2 FP64 without M), flags[1] = |U|.
+// ---------------------------------------------------------------------------
+constexpr int PREP_THREADS = 256;
+
+__global__ void __launch_bounds__(PREP_THREADS)
+    bpp_prep_kernel(const double *__restrict__ G, int k, float *__restrict__ G32,
+                    float *__restrict__ M32, double *__restrict__ M64,
+                    uint32_t *__restrict__ usable_words, int *__restrict__ flags,
+                    unsigned long long *__restrict__ counter, BppStats *__restrict__ stats)
+{
+    extern __shared__ double sm[];
+    double *L = sm;                                   // u x u, later M (u x u)
+    int *uidx = reinterpret_cast<int *>(L + k * k);   // k
+    __shared__ int s_u, s_ok;
+    __shared__ unsigned long long s_norm[2];
+    const int tid = threadIdx.x;
+
+    for (int e = tid; e < k * k; e += PREP_THREADS) {
+        G32[e] = (float)G[e];
+        M32[e] = 0.0f;
+        M64[e] = 0.0;
+    }
+    if (tid == 0) {
+        int u = 0;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        for (int i = 0; i < k; ++i)
+            if (G[i * k + i] > 0.0) {
+                uidx[u++] = i;
+                w[i >> 5] |= 1u << (i & 31);
+            }
+        for (int q = 0; q < 4; ++q)
+            usable_words[q] = w[q];
+        s_u = u;
+        s_ok = u > 0;
+        s_norm[0] = s_norm[1] = 0ull;
+        *counter = 0ull;
+    }
+    __syncthreads();
+    const int u = s_u;
+    for (int e = tid; e < u * u; e += PREP_THREADS) {
+        const int a = e / u, b = e % u;
+        L[a * u + b] = G[uidx[a] * k + uidx[b]];
+    }
+    __syncthreads();
+    // Right-looking Cholesky on the lower triangle.
+    for (int j = 0; j < u; ++j) {
+        if (tid == 0) {
+            const double d = L[j * u + j];
+            const double dorig = G[uidx[j] * k + uidx[j]];
+            if (!(d > PIVOT_TOL64 * dorig))
+                s_ok = 0;
+            else
+                L[j * u + j] = sqrt(d);
+        }
+        __syncthreads();
+        if (!s_ok)
+            break;
+        const double ljj = L[j * u + j];
+        for (int i = j + 1 + tid; i < u; i += PREP_THREADS)
+            L[i * u + j] /= ljj;
+        __syncthreads();
+        const int t = u - j - 1;
+        for (int e = tid; e < t * t; e += PREP_THREADS) {
+            const int a = j + 1 + e / t, b = j + 1 + e % t;
+            if (b <= a)
+                L[a * u + b] -= L[a * u + j] * L[b * u + j];
+        }
+        __syncthreads();
+    }
+    if (!s_ok) {
+        if (tid == 0) {
+            flags[0] = 2;
+            flags[1] = u;
+            atomicAdd(&stats->fp64_halfsteps, 1ull);
+        }
+        return;
+    }
+    // Columns of L^{-1} by forward substitution, staged in M64 (u x u).
+    double *Linv = M64;
+    for (int c = tid; c < u; c += PREP_THREADS) {
+        for (int a = 0; a < c; ++a)
+            Linv[a * u + c] = 0.0;
+        Linv[c * u + c] = 1.0 / L[c * u + c];
+        for (int a = c + 1; a < u; ++a) {
+            double s = 0.0;
+            for (int b = c; b < a; ++b)
+                s -= L[a * u + b] * Linv[b * u + c];
+            Linv[a * u + c] = s / L[a * u + a];
+        }
+    }
+    __syncthreads();
+    // M = Linv^T Linv : M[a][b] = sum_{c >= max(a,b)} Linv[c][a] Linv[c][b].
+    for (int e = tid; e < u * u; e += PREP_THREADS) {
+        const int a = e / u, b = e % u;
+        const int c0 = a > b ? a : b;
+        double s = 0.0;
+        for (int c = c0; c < u; ++c)
+            s += Linv[c * u + a] * Linv[c * u + b];
+        L[a * u + b] = s;
+    }
+    __syncthreads();
+    // cond_1 = max column sum of |G_UU| times max column sum of |M|. Non-negative
+    // doubles order like their bit patterns, so an integer max reduces them.
+    for (int c = tid; c < u; c += PREP_THREADS) {
+        double sg = 0.0, sm2 = 0.0;
+        for (int a = 0; a < u; ++a) {
+            sg += fabs(G[uidx[a] * k + uidx[c]]);
+            sm2 += fabs(L[a * u + c]);
+        }
+        atomicMax(&s_norm[0], (unsigned long long)__double_as_longlong(sg));
+        atomicMax(&s_norm[1], (unsigned long long)__double_as_longlong(sm2));
+    }
+    for (int e = tid; e < k * k; e += PREP_THREADS)
+        M64[e] = 0.0;
+    __syncthreads();
+    for (int e = tid; e < u * u; e += PREP_THREADS) {
+        const int a = e / u, b = e % u;
+        const double v = L[a * u + b];
+        M64[uidx[a] * k + uidx[b]] = v;
+        M32[uidx[a] * k + uidx[b]] = (float)v;
+    }
+    if (tid == 0) {
+        const double cond = __longlong_as_double((long long)s_norm[0]) *
+                            __longlong_as_double((long long)s_norm[1]);
+        const int mode = cond <= COND_FP32 ? 0 : 1;
+        flags[0] = mode;
+        flags[1] = u;
+        if (mode)
+            atomicAdd(&stats->fp64_halfsteps, 1ull);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-cooperative Cholesky factorisation of a p x p SPD system S, where
+// S[a][b] = Src[idx[a] * ld + idx[b]] (left-looking, lane-per-row). Lw: p x LS
+// workspace receiving L (lower triangle), invd: p reciprocal pivots.
+// Returns false (uniformly across the warp) on a pivot <= tol * S_jj.
+// ---------------------------------------------------------------------------
+template <typename T, typename SrcT, int PT>
+__device__ bool warp_chol_factor(const SrcT *__restrict__ Src, int ld,
+                                 const int *__restrict__ idx, int p, T *__restrict__ Lw, int LS,
+                                 T *__restrict__ invd, T tol, int lane)
+{
+    for (int j = 0; j < p; ++j) {
+        const int ij = idx[j];
+#pragma unroll
+        for (int t = 0; t < PT; ++t) {
+            const int i = lane + 32 * t;
+            if (i >= j && i < p) {
+                T s = (T)Src[idx[i] * ld + ij];
+                const T *li = Lw + i * LS;
+                const T *lj = Lw + j * LS;
+                for (int c = 0; c < j; ++c)
+                    s -= li[c] * lj[c];
+                Lw[i * LS + j] = s;
+            }
+        }
+        __syncwarp();
+        const T d = Lw[j * LS + j];
+        const T dorig = (T)Src[ij * ld + ij];
+        if (!(d > tol * dorig))
+            return false;
+        const T l = sqrt(d);
+        const T inv = (T)1 / l;
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < PT; ++t) {
+            const int i = lane + 32 * t;
+            if (i > j && i < p)
+                Lw[i * LS + j] *= inv;
+        }
+        if (lane == 0) {
+            Lw[j * LS + j] = l;
+            invd[j] = inv;
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+// Solve L L^T z = r with the factor from warp_chol_factor; row a of r / z in
+// lane a % 32, slot a / 32 (shuffle-broadcast substitutions).
+template <typename T, int PT>
+__device__ void warp_chol_subst(int p, const T *__restrict__ Lw, int LS,
+                                const T *__restrict__ invd, T (&r)[PT], int lane)
+{
+    for (int j = 0; j < p; ++j) {
+        const int tj = j >> 5, owner = j & 31;
+        T rj = r[0];
+#pragma unroll
+        for (int t = 1; t < PT; ++t)
+            if (tj == t)
+                rj = r[t];
+        const T zj = __shfl_sync(FULL, rj, owner) * invd[j];
+#pragma unroll
+        for (int t = 0; t < PT; ++t) {
+            const int i = lane + 32 * t;
+            if (i > j && i < p)
+                r[t] -= Lw[i * LS + j] * zj;
+            if (t == tj && lane == owner)
+                r[t] = zj;
+        }
+    }
+    for (int j = p - 1; j >= 0; --j) {
+        const int tj = j >> 5, owner = j & 31;
+        T rj = r[0];
+#pragma unroll
+        for (int t = 1; t < PT; ++t)
+            if (tj == t)
+                rj = r[t];
+        const T xj = __shfl_sync(FULL, rj, owner) * invd[j];
+        const T *lj = Lw + j * LS;
+#pragma unroll
+        for (int t = 0; t < PT; ++t) {
+            const int i = lane + 32 * t;
+            if (i < j)
+                r[t] -= lj[i] * xj;
+            if (t == tj && lane == owner)
+                r[t] = xj;
+        }
+    }
+    __syncwarp();
+}
+
+// out[s] += sum over set bits f of mask (one word per slot) of Mat[f][i] v_f,
+// i = lane + 32 s, v_f broadcast from lane f % 32 (Mat symmetric with rows
+// contiguous in i, so each step is a conflict-free row read).
+template <typename T, int KW>
+__device__ __forceinline__ void warp_matvec_masked(const T *__restrict__ Mat, int k,
+                                                   const unsigned (&mask)[KW], const T (&v)[KW],
+                                                   T (&out)[KW], int lane)
+{
+#pragma unroll
+    for (int s2 = 0; s2 < KW; ++s2) {
+        unsigned bits = mask[s2];
+        while (bits) {
+            const int l = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const T vf = __shfl_sync(FULL, v[s2], l);
+            const T *row = Mat + (32 * s2 + l) * k;
+#pragma unroll
+            for (int s = 0; s < KW; ++s) {
+                const int i = lane + 32 * s;
+                if (i < k)
+                    out[s] = fma(row[i], vf, out[s]);
+            }
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        v = max(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+
+struct SolveParams {
+    int k, nwords, max_rounds;
+    int64_t nrhs;
+    const float *G32, *M32;
+    const double *G64, *M64;
+    const uint32_t *usable_words;
+    const int *flags;
+    const float *B;
+    float *X;
+    const uint64_t *pin;
+    uint64_t *pout;
+    int32_t *rounds_out;
+    int8_t *status_out;
+    unsigned long long *counter;
+    BppStats *stats;
+};
+
+__device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
+
+template <int MODE> struct ModeType { using T = double; };
+template <> struct ModeType<0> { using T = float; };
+
+__host__ __device__ inline size_t per_warp_bytes(int pmax, int LS)
+{
+    return 128 * sizeof(int) + 256 * sizeof(double) + sizeof(double) * (size_t)pmax * LS;
+}
+
+// Shared-memory matrices of a mode: mode 0 G32 and M32, mode 1 G64 and M64,
+// mode 2 none (no M; G64 read through L1/L2).
+__host__ __device__ inline size_t mats_bytes(int k, int mode)
+{
+    const size_t b = mode == 0 ? 2 * sizeof(float) * (size_t)k * k
+                     : mode == 1 ? 2 * sizeof(double) * (size_t)k * k
+                                 : 0;
+    return (b + 15) & ~size_t(15);
+}
+
+// KW = index slots per lane (k <= 32 KW); PT = compact-system rows per lane
+// (pmax <= 32 PT). The kernel of each MODE returns at once unless the prep
+// kernel chose that mode, so the host never waits for the verdict.
+template <int KW, int PT, int MODE>
+__global__ void __launch_bounds__(BPP_THREADS, 2)
+    bpp_solve_kernel(const SolveParams P, int pmax, int LS, int staged)
+{
+    using T = typename ModeType<MODE>::T;
+    constexpr bool HAVE_M = MODE != 2;
+    if (P.flags[0] != MODE)
+        return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int k = P.k;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const T *Gs;
+    const T *Ms = nullptr;
+    if (!staged) {
+        // Matrices too large for shared memory next to the per-warp space:
+        // read them through L1/L2 (mode 1 at k > ~100, mode 2 always).
+        Gs = reinterpret_cast<const T *>(MODE == 0 ? (const void *)P.G32 : (const void *)P.G64);
+        if (HAVE_M)
+            Ms = reinterpret_cast<const T *>(MODE == 0 ? (const void *)P.M32
+                                                       : (const void *)P.M64);
+    } else {
+        T *gsh = reinterpret_cast<T *>(smem_raw);
+        T *msh = gsh + k * k;
+        for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+            if (MODE == 0) {
+                gsh[e] = (T)P.G32[e];
+                msh[e] = (T)P.M32[e];
+            } else {
+                gsh[e] = (T)P.G64[e];
+                msh[e] = (T)P.M64[e];
+            }
+        }
+        Gs = gsh;
+        Ms = msh;
+    }
+    unsigned char *wp =
+        smem_raw + (staged ? mats_bytes(k, MODE) : 0) + warp * per_warp_bytes(pmax, LS);
+    int *widx = reinterpret_cast<int *>(wp);
+    double *zbuf64 = reinterpret_cast<double *>(wp + 128 * sizeof(int));
+    double *invd64 = zbuf64 + 128;
+    double *Lw64 = invd64 + 128;
+    T *zbuf = reinterpret_cast<T *>(zbuf64);
+    T *invd = reinterpret_cast<T *>(invd64);
+    T *Lw = reinterpret_cast<T *>(Lw64);
+    __syncthreads();
+
+    bool usable[KW];
+    int nU = 0;
+#pragma unroll
+    for (int s = 0; s < KW; ++s) {
+        const uint32_t w = P.usable_words[s];
+        usable[s] = (w >> lane) & 1u;
+        nU += __popc(w);
+    }
+    const T tolrel = MODE == 0 ? (T)FEAS_TOL32 : (T)0;
+
+    unsigned long long st_rounds = 0, st_max = 0, st_fp64 = 0, st_nc = 0, st_sing = 0,
+                       st_nf = 0, st_rhs = 0;
+
+    for (;;) {
+        unsigned long long j0 = 0;
+        if (lane == 0)
+            j0 = atomicAdd(P.counter, (unsigned long long)RHS_CHUNK);
+        j0 = __shfl_sync(FULL, j0, 0);
+        if (j0 >= (unsigned long long)P.nrhs)
+            break;
+        const int64_t jend = min((int64_t)j0 + RHS_CHUNK, P.nrhs);
+        for (int64_t j = (int64_t)j0; j < jend; ++j) {
+            T g[KW], u[KW], x[KW], y[KW];
+            bool inF[KW];
+            bool bad = false;
+            T gmax = 0;
+#pragma unroll
+            for (int s = 0; s < KW; ++s) {
+                const int i = lane + 32 * s;
+                g[s] = i < k ? (T)P.B[j * k + i] : (T)0;
+                bad |= !isfinite(g[s]);
+                gmax = max(gmax, fabs(g[s]));
+                u[s] = 0;
+                x[s] = 0;
+                y[s] = -g[s];
+                inF[s] = false;
+            }
+            bad = __any_sync(FULL, bad);
+            gmax = warp_max(gmax);
+            const T ytol = tolrel * gmax;
+            T xtol = 0;
+            int status = NMF_OK;
+            int rounds = 0;
+            if (bad) {
+                status = NMF_ERR_NONFINITE;
+#pragma unroll
+                for (int s = 0; s < KW; ++s)
+                    x[s] = 0;
+            } else {
+                // Unconstrained solution u = M g.
+                if (HAVE_M) {
+#pragma unroll
+                    for (int s2 = 0; s2 < KW; ++s2) {
+                        for (int l = 0; l < 32; ++l) {
+                            const int jj = 32 * s2 + l;
+                            const T gj = __shfl_sync(FULL, g[s2], l);
+                            if (jj >= k)
+                                break;
+                            const T *mrow = Ms + jj * k;
+#pragma unroll
+                            for (int s = 0; s < KW; ++s) {
+                                const int i = lane + 32 * s;
+                                if (i < k)
+                                    u[s] = fma(mrow[i], gj, u[s]);
+                            }
+                        }
+                    }
+                }
+                // Starting partition: empty (cold) or the given bitmask (warm).
+                if (P.pin) {
+#pragma unroll
+                    for (int s = 0; s < KW; ++s) {
+                        const int i = lane + 32 * s;
+                        bool f = false;
+                        if (i < k) {
+                            const uint64_t wv = P.pin[j * P.nwords + (i >> 6)];
+                            f = (wv >> (i & 63)) & 1ull;
+                        }
+                        inF[s] = f && usable[s];
+                    }
+                }
+
+                // Candidate point of the current partition: fills x and y.
+                auto solve = [&]() -> int {
+                    unsigned fm[KW];
+                    int nF = 0;
+#pragma unroll
+                    for (int s = 0; s < KW; ++s) {
+                        fm[s] = __ballot_sync(FULL, inF[s]);
+                        nF += __popc(fm[s]);
+                    }
+                    const int nA = nU - nF;
+                    const bool comp = HAVE_M && nA < nF;
+                    bool inS[KW];
+                    int rank[KW];
+                    int pos = 0;
+#pragma unroll
+                    for (int s = 0; s < KW; ++s) {
+                        inS[s] = comp ? (usable[s] && !inF[s]) : inF[s];
+                        const unsigned mk = __ballot_sync(FULL, inS[s]);
+                        rank[s] = pos + __popc(mk & lanemask_lt(lane));
+                        if (inS[s]) {
+                            widx[rank[s]] = lane + 32 * s;
+                            zbuf[rank[s]] = comp ? -u[s] : g[s];
+                        }
+                        pos += __popc(mk);
+                    }
+                    const int p = pos;
+                    __syncwarp();
+                    bool ok = true, refine = true;
+                    if (p > 0) {
+                        ok = warp_chol_factor<T, T, PT>(comp ? Ms : Gs, k, widx, p, Lw, LS, invd,
+                                                        MODE == 0 ? (T)PIVOT_TOL
+                                                                  : (T)PIVOT_TOL64,
+                                                        lane);
+                        if (ok) {
+                            T r[PT];
+#pragma unroll
+                            for (int t = 0; t < PT; ++t) {
+                                const int a = lane + 32 * t;
+                                r[t] = a < p ? zbuf[a] : (T)0;
+                            }
+                            warp_chol_subst<T, PT>(p, Lw, LS, invd, r, lane);
+#pragma unroll
+                            for (int t = 0; t < PT; ++t) {
+                                const int a = lane + 32 * t;
+                                if (a < p)
+                                    zbuf[a] = r[t];
+                            }
+                        } else if (MODE == 0) {
+                            // Ill-conditioned in FP32: factor and solve in FP64.
+                            refine = false;
+                            st_fp64 += (lane == 0);
+                            __syncwarp();
+#pragma unroll
+                            for (int s = 0; s < KW; ++s)
+                                if (inS[s])
+                                    zbuf64[rank[s]] = (double)(comp ? -u[s] : g[s]);
+                            __syncwarp();
+                            double r64[PT];
+#pragma unroll
+                            for (int t = 0; t < PT; ++t) {
+                                const int a = lane + 32 * t;
+                                r64[t] = a < p ? zbuf64[a] : 0.0;
+                            }
+                            __syncwarp();
+                            ok = warp_chol_factor<double, double, PT>(
+                                comp ? P.M64 : P.G64, k, widx, p, Lw64, LS, invd64, PIVOT_TOL64,
+                                lane);
+                            if (ok) {
+                                warp_chol_subst<double, PT>(p, Lw64, LS, invd64, r64, lane);
+#pragma unroll
+                                for (int t = 0; t < PT; ++t) {
+                                    const int a = lane + 32 * t;
+                                    if (a < p)
+                                        zbuf[a] = (T)r64[t];
+                                }
+                            }
+                        }
+                        __syncwarp();
+                    }
+                    if (!ok)
+                        return NMF_ERR_SINGULAR_GRAM;
+#pragma unroll
+                    for (int s = 0; s < KW; ++s) {
+                        const int i = lane + 32 * s;
+                        if (!comp) {
+                            x[s] = inF[s] ? zbuf[rank[s]] : (T)0;
+                        } else {
+                            T acc = u[s];
+                            if (inF[s])
+                                for (int a = 0; a < p; ++a)
+                                    acc = fma(Ms[widx[a] * k + i], zbuf[a], acc);
+                            x[s] = inF[s] ? acc : (T)0;
+                        }
+                    }
+                    __syncwarp();
+                    // One refinement step through the same factor.
+                    if (refine && nF > 0) {
+                        T w[KW], res[KW], up[KW];
+#pragma unroll
+                        for (int s = 0; s < KW; ++s) {
+                            w[s] = 0;
+                            up[s] = 0;
+                        }
+                        warp_matvec_masked<T, KW>(Gs, k, fm, x, w, lane);
+#pragma unroll
+                        for (int s = 0; s < KW; ++s)
+                            res[s] = inF[s] ? g[s] - w[s] : (T)0;
+                        if (comp)
+                            warp_matvec_masked<T, KW>(Ms, k, fm, res, up, lane);
+#pragma unroll
+                        for (int s = 0; s < KW; ++s)
+                            if (inS[s])
+                                zbuf[rank[s]] = comp ? -up[s] : res[s];
+                        __syncwarp();
+                        T r[PT];
+#pragma unroll
+                        for (int t = 0; t < PT; ++t) {
+                            const int a = lane + 32 * t;
+                            r[t] = a < p ? zbuf[a] : (T)0;
+                        }
+                        __syncwarp();
+                        warp_chol_subst<T, PT>(p, Lw, LS, invd, r, lane);
+#pragma unroll
+                        for (int t = 0; t < PT; ++t) {
+                            const int a = lane + 32 * t;
+                            if (a < p)
+                                zbuf[a] = r[t];
+                        }
+                        __syncwarp();
+#pragma unroll
+                        for (int s = 0; s < KW; ++s) {
+                            const int i = lane + 32 * s;
+                            T dx;
+                            if (!comp) {
+                                dx = inF[s] ? zbuf[rank[s]] : (T)0;
+                            } else {
+                                T acc = up[s];
+                                if (inF[s])
+                                    for (int a = 0; a < p; ++a)
+                                        acc = fma(Ms[widx[a] * k + i], zbuf[a], acc);
+                                dx = inF[s] ? acc : (T)0;
+                            }
+                            x[s] += dx;
+                        }
+                        __syncwarp();
+                    }
+                    // y = G x - g off F (from G directly), 0 on F.
+                    T w[KW];
+                    T xm = 0;
+#pragma unroll
+                    for (int s = 0; s < KW; ++s) {
+                        w[s] = 0;
+                        xm = max(xm, inF[s] ? fabs(x[s]) : (T)0);
+                    }
+                    warp_matvec_masked<T, KW>(Gs, k, fm, x, w, lane);
+#pragma unroll
+                    for (int s = 0; s < KW; ++s)
+                        y[s] = inF[s] ? (T)0 : w[s] - g[s];
+                    xtol = tolrel * warp_max(xm);
+                    return NMF_OK;
+                };
+
+                bool anyF = false;
+#pragma unroll
+                for (int s = 0; s < KW; ++s)
+                    anyF |= inF[s];
+                if (__any_sync(FULL, anyF))
+                    status = solve();
+                int alpha = 3, beta = k + 1;
+                while (status == NMF_OK) {
+                    bool inf[KW];
+                    unsigned vm[KW];
+                    int nV = 0;
+#pragma unroll
+                    for (int s = 0; s < KW; ++s) {
+                        inf[s] = usable[s] && (inF[s] ? (x[s] < -xtol) : (y[s] < -ytol));
+                        vm[s] = __ballot_sync(FULL, inf[s]);
+                        nV += __popc(vm[s]);
+                    }
+                    if (nV == 0)
+                        break;
+                    if (rounds >= P.max_rounds) {
+                        status = NMF_ERR_NOT_CONVERGED;
+                        break;
+                    }
+                    if (nV < beta) {
+                        beta = nV;
+                        alpha = 3;
+#pragma unroll
+                        for (int s = 0; s < KW; ++s)
+                            inF[s] = inF[s] != inf[s];
+                    } else if (alpha >= 1) {
+                        alpha -= 1;
+#pragma unroll
+                        for (int s = 0; s < KW; ++s)
+                            inF[s] = inF[s] != inf[s];
+                    } else {
+                        int top = -1;
+#pragma unroll
+                        for (int s = KW - 1; s >= 0; --s)
+                            if (top < 0 && vm[s])
+                                top = 32 * s + 31 - __clz(vm[s]);
+#pragma unroll
+                        for (int s = 0; s < KW; ++s)
+                            if (lane + 32 * s == top)
+                                inF[s] = !inF[s];
+                    }
+                    rounds += 1;
+                    status = solve();
+                }
+                bool nf = false;
+#pragma unroll
+                for (int s = 0; s < KW; ++s) {
+                    x[s] = x[s] > (T)0 ? x[s] : (T)0;   // within-tolerance negatives -> 0
+                    nf |= !isfinite(x[s]);
+                }
+                if (__any_sync(FULL, nf) && status == NMF_OK)
+                    status = NMF_ERR_NONFINITE;
+            }
+#pragma unroll
+            for (int s = 0; s < KW; ++s) {
+                const int i = lane + 32 * s;
+                if (i < k)
+                    P.X[j * k + i] = (float)x[s];
+            }
+            if (P.pout) {
+                unsigned bm[KW];
+#pragma unroll
+                for (int s = 0; s < KW; ++s)
+                    bm[s] = __ballot_sync(FULL, inF[s]);
+                if (lane == 0) {
+#pragma unroll
+                    for (int w = 0; w < (KW + 1) / 2; ++w) {
+                        const uint64_t lo = bm[2 * w];
+                        const uint64_t hi = (2 * w + 1 < KW) ? bm[2 * w + 1] : 0u;
+                        P.pout[j * P.nwords + w] = lo | (hi << 32);
+                    }
+                }
+            }
+            if (lane == 0) {
+                if (P.rounds_out)
+                    P.rounds_out[j] = rounds;
+                if (P.status_out)
+                    P.status_out[j] = (int8_t)status;
+                st_rhs += 1;
+                st_rounds += rounds;
+                st_max = st_max > (unsigned long long)rounds ? st_max : (unsigned long long)rounds;
+                st_nc += status == NMF_ERR_NOT_CONVERGED;
+                st_sing += status == NMF_ERR_SINGULAR_GRAM;
+                st_nf += status == NMF_ERR_NONFINITE;
+            }
+        }
+    }
+    if (lane == 0 && st_rhs) {
+        atomicAdd(&P.stats->rhs, st_rhs);
+        atomicAdd(&P.stats->rounds, st_rounds);
+        atomicMax(&P.stats->max_rounds, st_max);
+        if (st_fp64) atomicAdd(&P.stats->fp64_solves, st_fp64);
+        if (st_nc) atomicAdd(&P.stats->not_converged, st_nc);
+        if (st_sing) atomicAdd(&P.stats->singular, st_sing);
+        if (st_nf) atomicAdd(&P.stats->nonfinite, st_nf);
+    }
+}
+
+constexpr size_t SMEM_LIMIT = 227 * 1024;
+
+template <int KW, int PT, int MODE>
+nmf_status launch_solve(const SolveParams &P, cudaStream_t s)
+{
+    const int k = P.k;
+    int pmax = MODE == 2 ? k : k / 2;
+    if (pmax < 1)
+        pmax = 1;
+    const int LS = pmax | 1;   // odd row stride: conflict-free lane-per-row reads
+    int nwarps = BPP_WARPS;
+    // Stage G (and M) in shared memory when they leave room for >= 2 warps.
+    const int staged = MODE != 2 &&
+                       mats_bytes(k, MODE) + 2 * per_warp_bytes(pmax, LS) <= SMEM_LIMIT;
+    const size_t mats = staged ? mats_bytes(k, MODE) : 0;
+    auto bytes = [&](int nw) { return mats + (size_t)nw * per_warp_bytes(pmax, LS); };
+    while (nwarps > 1 && bytes(nwarps) > SMEM_LIMIT)
+        --nwarps;
+    const size_t smem = bytes(nwarps);
+    if (smem > SMEM_LIMIT)
+        return NMF_ERR_INVALID_ARG;
+    static int configured_bytes = 0;
+    if ((int)smem > configured_bytes) {
+        NMF_CUDA(cudaFuncSetAttribute(bpp_solve_kernel<KW, PT, MODE>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured_bytes = (int)smem;
+    }
+    int per_sm = 0;
+    NMF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, bpp_solve_kernel<KW, PT, MODE>, nwarps * 32, smem));
+    if (per_sm < 1)
+        return NMF_ERR_INVALID_ARG;
+    int64_t blocks = (int64_t)per_sm * sm_count();
+    const int64_t need = cdiv(cdiv(P.nrhs, RHS_CHUNK), nwarps);
+    if (need < blocks)
+        blocks = need < 1 ? 1 : need;
+    bpp_solve_kernel<KW, PT, MODE><<<(unsigned)blocks, nwarps * 32, smem, s>>>(P, pmax, LS,
+                                                                              staged);
+    NMF_LAUNCHED("bpp_solve_kernel");
+    return NMF_OK;
+}
+
+template <int KW>
+nmf_status launch_modes(const SolveParams &P, cudaStream_t s)
+{
+    NMF_TRY((launch_solve<KW, (KW + 1) / 2, 0>(P, s)));
+    NMF_TRY((launch_solve<KW, (KW + 1) / 2, 1>(P, s)));
+    return launch_solve<KW, KW, 2>(P, s);
+}
+
+}  // namespace
+
+size_t bpp_work_bytes(int k) { return layout(k).total; }
+
+nmf_status launch_bpp(int k, int64_t nrhs, const double *G, const float *B, float *X,
+                      const uint64_t *passive_in, uint64_t *passive_out, int32_t *rounds_out,
+                      int8_t *status_out, int max_rounds, void *work, BppStats *stats_dev,
+                      cudaStream_t s)
+{
+    const WorkLayout L = layout(k);
+    unsigned char *w = static_cast<unsigned char *>(work);
+    SolveParams P;
+    P.k = k;
+    P.nwords = (k + 63) / 64;
+    P.max_rounds = max_rounds;
+    P.nrhs = nrhs;
+    P.G32 = reinterpret_cast<float *>(w + L.g32);
+    P.M32 = reinterpret_cast<float *>(w + L.m32);
+    P.G64 = G;
+    P.M64 = reinterpret_cast<double *>(w + L.m64);
+    P.usable_words = reinterpret_cast<uint32_t *>(w + L.usable);
+    P.flags = reinterpret_cast<int *>(w + L.flags);
+    P.B = B;
+    P.X = X;
+    P.pin = passive_in;
+    P.pout = passive_out;
+    P.rounds_out = rounds_out;
+    P.status_out = status_out;
+    P.counter = reinterpret_cast<unsigned long long *>(w + L.counter);
+    P.stats = stats_dev;
+
+    const size_t prep_smem = sizeof(double) * (size_t)k * k + sizeof(int) * (size_t)k;
+    static int prep_configured = 0;
+    if ((int)prep_smem > 48 * 1024 && (int)prep_smem > prep_configured) {
+        NMF_CUDA(cudaFuncSetAttribute(bpp_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)prep_smem));
+        prep_configured = (int)prep_smem;
+    }
+    bpp_prep_kernel<<<1, PREP_THREADS, prep_smem, s>>>(
+        G, k, const_cast<float *>(P.G32), const_cast<float *>(P.M32),
+        const_cast<double *>(P.M64), const_cast<uint32_t *>(P.usable_words),
+        const_cast<int *>(P.flags), P.counter, stats_dev);
+    NMF_LAUNCHED("bpp_prep_kernel");
+    if (nrhs == 0)
+        return NMF_OK;
+    if (k <= 32)
+        return launch_modes<1>(P, s);
+    if (k <= 64)
+        return launch_modes<2>(P, s);
+    if (k <= 96)
+        return launch_modes<3>(P, s);
+    return launch_modes<4>(P, s);
+}
+
+}  // namespace nmf

@@ -1,0 +1,103 @@
+// Shared definitions of the sm_103a ANLS-NMF library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nmf_gb300.h"
+
+namespace nmf {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Record the first CUDA error text for nmf_last_error-style diagnostics and
+// map a cudaError_t to the ABI status.
+nmf_status from_cuda(cudaError_t e, const char *what);
+
+#define NMF_CUDA(expr)                                                             \
+    do {                                                                           \
+        cudaError_t e_ = (expr);                                                   \
+        if (e_ != cudaSuccess)                                                     \
+            return ::nmf::from_cuda(e_, #expr);                                    \
+    } while (0)
+
+// Every kernel launch is followed by NMF_LAUNCHED, which also counts it.
+extern unsigned long long launch_count;
+
+#define NMF_LAUNCHED(what)                                                         \
+    do {                                                                           \
+        ::nmf::launch_count += 1;                                                  \
+        cudaError_t e_ = cudaGetLastError();                                       \
+        if (e_ != cudaSuccess)                                                     \
+            return ::nmf::from_cuda(e_, what);                                     \
+    } while (0)
+
+#define NMF_TRY(expr)                                                              \
+    do {                                                                           \
+        nmf_status s_ = (expr);                                                    \
+        if (s_ != NMF_OK)                                                          \
+            return s_;                                                             \
+    } while (0)
+
+inline int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0)
+            n = 1;
+    }
+    return n;
+}
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ---------------------------------------------------------------------------
+// Internal launchers (all asynchronous on `s`).
+// ---------------------------------------------------------------------------
+
+// Gram X^T X in FP64. `partials` must hold gram_partials_len(rows, k) doubles.
+int64_t gram_partials_len(int64_t rows, int k);
+nmf_status launch_gram(const float *X, int64_t rows, int k, double *G, double *partials,
+                       cudaStream_t s);
+
+// Dense products, plain FP32 SIMT: trans 0 -> A F (m x k), 1 -> A^T F (n x k).
+nmf_status launch_mm_simt(const float *A, int64_t m, int64_t n, int64_t lda, const float *F,
+                          int k, int trans, float *out, cudaStream_t s);
+
+// Dense products on tcgen05 tensor cores with BF16 head/tail operand splits.
+nmf_status launch_mm_tc(const float *A, int64_t m, int64_t n, int64_t lda, const float *F,
+                        int k, int trans, float *out, void *work, size_t work_bytes,
+                        cudaStream_t s);
+size_t mm_tc_work_bytes(int64_t m, int64_t n, int k, int trans);
+
+// CSR SpMM: out (rows x k) = S F.
+nmf_status launch_spmm(const int64_t *rowptr, const int32_t *colidx, const float *vals,
+                       int64_t rows, const float *F, int k, float *out, cudaStream_t s);
+
+// Objective pieces. Dense: per-block FP64 partial sums of squared residuals,
+// reduced in a fixed order into *f_dev. `partials` holds objective_partials_len().
+int64_t objective_partials_len();
+nmf_status launch_objective_dense(const float *A, int64_t m, int64_t n, int64_t lda,
+                                  const float *W, const float *Ht, int k, int precision,
+                                  double *partials, double *f_dev, cudaStream_t s);
+// Sparse: f = sum over stored (A_ij - wh)^2 - wh^2, plus trace(GW GH).
+nmf_status launch_objective_csr(const int64_t *rowptr, const int32_t *colidx,
+                                const float *vals, int64_t m, const float *W, const float *Ht,
+                                int k, const double *GW, const double *GH, double *partials,
+                                double *f_dev, cudaStream_t s);
+
+// Batched BPP. Workspace layout is private to bpp.cu; size from bpp_work_bytes.
+size_t bpp_work_bytes(int k);
+struct BppStats {
+    unsigned long long rhs, rounds, max_rounds, fp64_solves, not_converged, singular, nonfinite,
+        fp64_halfsteps;
+};
+nmf_status launch_bpp(int k, int64_t nrhs, const double *G, const float *B, float *X,
+                      const uint64_t *passive_in, uint64_t *passive_out, int32_t *rounds_out,
+                      int8_t *status_out, int max_rounds, void *work, BppStats *stats_dev,
+                      cudaStream_t s);
+
+}  // namespace nmf

@@ -1,0 +1,118 @@
+"""Whole ANLS iterations on the GPU (C-ABI handle) against the FP64 oracle run
+from the same seeded inputs and starting point.
+
+Tolerances (the benchmark spec): relative objective <= 1e-5 and relative factor error
+(Frobenius) <= 1e-4 after the fixed iteration count; the GPU objective must be
+non-increasing up to 1e-6 relative (each half-step is an exact minimisation,
+Eq. 2).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nmf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1509_09313_gb300 as lib
+    return lib
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run_gpu(nmf, A, W0, Ht0, iters, precision="fp32", start="cold", csr=None, shape=None):
+    if csr is None:
+        Ad = dev(A)
+    else:
+        Ad = tuple(dev(x) for x in csr)
+    h = nmf.nmf_init(Ad, dev(W0), dev(Ht0), precision=precision, start=start, shape=shape)
+    h.nmf_iterate(iters)
+    status = h.nmf_sync()
+    W, Ht = h.nmf_get_factors()
+    f = np.array(h.nmf_objective_history())
+    stats = h.nmf_get_stats()
+    h.nmf_destroy()
+    return dict(W=W.double().cpu().numpy(), Ht=Ht.double().cpu().numpy(), f=f, status=status,
+                stats=stats)
+
+
+def check(nmf, g, ref, ftol=1e-5, xtol=1e-4):
+    assert g["status"] == nmf.NMF_OK
+    f_or = ref["f"][1:]
+    assert len(g["f"]) == len(f_or)
+    errf = np.abs(g["f"] - f_or) / f_or
+    errW, errH = rel(g["W"], ref["W"]), rel(g["Ht"], ref["Ht"])
+    print(f"max rel f err {errf.max():.2e} (at iteration {int(errf.argmax()) + 1})  "
+          f"W {errW:.2e}  H {errH:.2e}  stats {g['stats']}")
+    assert errf.max() <= ftol
+    assert errW <= xtol and errH <= xtol
+    assert (g["f"][1:] <= g["f"][:-1] * (1 + 1e-6)).all()
+
+
+@pytest.mark.parametrize("start", ["cold", "warm"])
+def test_dense_small_config(nmf, start):
+    # A = W0 H0 + |N(0, 0.01^2)|, 2000 x 1000, k = 10, 10 iterations.
+    m, n, k, T = 2000, 1000, 10, 10
+    A = synth.dense_planted(m, n, k, 0.01)
+    W0, Ht0 = synth.init_factors(m, n, k)
+    ref = oracle.anls(A, W0, Ht0, iters=T)
+    g = run_gpu(nmf, A, W0, Ht0, T, start=start)
+    check(nmf, g, ref)
+
+
+def test_dense_large_config_crop(nmf):
+    # The 96000 x 64000 recipe (k = 50, sigma = 0.05) on its 4000 x 2000 crop,
+    # 30 iterations.
+    m, n, k, T = 4000, 2000, 50, 30
+    A = synth.dense_planted(m, n, k, 0.05, m_full=96000, n_full=64000)
+    W0, Ht0 = synth.init_factors(m, n, k)
+    ref = oracle.anls(A, W0, Ht0, iters=T)
+    g = run_gpu(nmf, A, W0, Ht0, T, start="warm")
+    check(nmf, g, ref)
+
+
+def test_sparse_config_scaled(nmf):
+    # The sparse recipe (uniform positions, values in (0, 1], k = 50) scaled to
+    # 20000 x 10000 with 200k draws, 5 iterations.
+    m, n, k, T = 20000, 10000, 50, 5
+    csr = synth.csr_uniform(m, n, 200000)
+    W0, Ht0 = synth.init_factors(m, n, k)
+    ref = oracle.anls(None, W0, Ht0, iters=T, csr=csr, shape=(m, n))
+    g = run_gpu(nmf, None, W0, Ht0, T, start="warm", csr=csr, shape=(m, n))
+    check(nmf, g, ref)
+
+
+def test_checkpoint_resume(nmf):
+    m, n, k = 600, 400, 8
+    A = synth.dense_planted(m, n, k, 0.01, seed=5)
+    W0, Ht0 = synth.init_factors(m, n, k, seed=5)
+    h = nmf.nmf_init(dev(A), dev(W0), dev(Ht0))
+    h.nmf_iterate(3)
+    W3, H3 = h.nmf_get_factors()
+    h.nmf_iterate(2)
+    W5, H5 = h.nmf_get_factors()
+    h2 = nmf.nmf_init(dev(A), W3.contiguous(), H3.contiguous())
+    h2.nmf_iterate(2)
+    W5b, H5b = h2.nmf_get_factors()
+    assert torch.equal(W5, W5b) and torch.equal(H5, H5b)
+    h.nmf_destroy()
+    h2.nmf_destroy()
+
+
+def test_invalid_config_raises(nmf):
+    W0 = torch.zeros((10, 0), dtype=torch.float32, device="cuda")
+    with pytest.raises(Exception):
+        nmf.nmf_init(torch.zeros((10, 5), device="cuda"), W0,
+                     torch.zeros((5, 0), dtype=torch.float32, device="cuda"))

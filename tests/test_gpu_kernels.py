@@ -1,0 +1,286 @@
+"""Parity of each CUDA kernel with the FP64 oracle, called through the C ABI.
+
+Tolerances (derived from the arithmetic; the oracle is FP64):
+  * Gram: FP32 products summed in FP32 over 32-row tiles, tiles in FP64:
+    |err| <= 2e-6 * (|X|^T |X|) elementwise.
+  * Products (plain FP32): 16-term FP32 tile sums merged with Kahan
+    compensation, so the result is near FP32 rounding:
+    |err| <= 2e-6 * (|A| |F|) elementwise, and RMS relative error <= 2e-7.
+  * BPP: FP32 factorisations of systems whose data (G and b rounded to FP32)
+    already perturb x by ~cond(G) * 6e-8: ||x - x_or|| / ||x_or|| <= 200 * cond
+    * 6e-8 per batch; passive sets and round counts identical on RHS whose
+    KKT margin (O3) is at least 1e-3 of the problem scale.
+  * Objective: residuals formed in FP32, squares summed in FP64: rel 1e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+EPS32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def nmf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1509_09313_gb300 as lib
+    return lib
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+# ----------------------------------------------------------------------------- Gram
+@pytest.mark.parametrize("k", [1, 7, 10, 16, 17, 33, 50, 64, 65, 100, 128])
+@pytest.mark.parametrize("rows", [0, 1, 31, 33, 1000, 4099])
+def test_gram(nmf, k, rows):
+    rng = np.random.default_rng(k * 1000 + rows)
+    X = rng.uniform(-1, 1, (rows, k)).astype(np.float32)
+    G = nmf.nmf_gram(dev(X)).cpu().numpy()
+    ref = oracle.gram(X.astype(np.float64))
+    bound = 2e-6 * oracle.gram(np.abs(X).astype(np.float64)) + 1e-30
+    assert np.all(np.abs(G - ref) <= bound)
+    assert np.array_equal(G, G.T)
+
+
+# ----------------------------------------------------------------------------- products
+@pytest.mark.parametrize("shape", [(1, 1), (37, 23), (129, 257), (300, 1000), (1000, 300),
+                                   (2050, 17)])
+@pytest.mark.parametrize("k", [1, 5, 10, 16, 17, 50, 64, 100, 128])
+@pytest.mark.parametrize("trans", [0, 1])
+def test_mm_dense_fp32(nmf, shape, k, trans):
+    m, n = shape
+    rng = np.random.default_rng(m * 7 + n * 13 + k + trans)
+    A = rng.uniform(0, 1, (m, n)).astype(np.float32)
+    F = rng.uniform(0, 1, (n if trans == 0 else m, k)).astype(np.float32)
+    out = nmf.nmf_mm_dense(dev(A), dev(F), bool(trans)).cpu().numpy().astype(np.float64)
+    ref = oracle.mm_dense(A, F.astype(np.float64), bool(trans))
+    assert out.shape == ref.shape
+    assert np.all(np.abs(out - ref) <= 2e-6 * ref + 1e-30)
+    rel = (out - ref) / np.where(ref == 0, 1, ref)
+    assert np.sqrt(np.mean(rel ** 2)) <= 2e-7
+
+
+@pytest.mark.parametrize("trans", [0, 1])
+def test_mm_dense_strided_and_signed(nmf, trans):
+    # Leading dimension > n and not a multiple of 4 (scalar-load path), signed data.
+    m, n, k = 333, 517, 50
+    rng = np.random.default_rng(5)
+    Afull = rng.uniform(-1, 1, (m, n + 3)).astype(np.float32)
+    F = rng.uniform(-1, 1, (n if trans == 0 else m, k)).astype(np.float32)
+    Ad = dev(Afull)[:, :n]
+    out = nmf.nmf_mm_dense(Ad, dev(F), bool(trans)).cpu().numpy().astype(np.float64)
+    A = np.ascontiguousarray(Afull[:, :n])
+    ref = oracle.mm_dense(A, F.astype(np.float64), bool(trans))
+    bound = 2e-6 * oracle.mm_dense(np.abs(A), np.abs(F).astype(np.float64), bool(trans))
+    assert np.all(np.abs(out - ref) <= bound + 1e-30)
+
+
+def test_mm_dense_zero_contraction(nmf):
+    A = torch.empty((5, 0), dtype=torch.float32, device="cuda")
+    F = torch.empty((0, 3), dtype=torch.float32, device="cuda")
+    out = nmf.nmf_mm_dense(A, F, False)
+    assert out.shape == (5, 3) and torch.all(out == 0)
+
+
+# ----------------------------------------------------------------------------- sparse
+@pytest.mark.parametrize("k", [1, 10, 50, 100])
+def test_spmm_and_transpose(nmf, k):
+    m, n = 3001, 1777
+    rowptr, colidx, vals = synth.csr_uniform(m, n, 40000, seed=k)
+    rowptr[5:] += 0   # rows 0..m-1 include empty rows at this density
+    d_rp, d_ci, d_v = dev(rowptr), dev(colidx), dev(vals)
+    rng = np.random.default_rng(k)
+    Ht = rng.uniform(0, 1, (n, k)).astype(np.float32)
+    W = rng.uniform(0, 1, (m, k)).astype(np.float32)
+    V = nmf.nmf_mm_csr(d_rp, d_ci, d_v, n, dev(Ht)).cpu().numpy().astype(np.float64)
+    refV = oracle.mm_csr(rowptr, colidx, vals, m, n, Ht.astype(np.float64), False)
+    assert np.all(np.abs(V - refV) <= 2e-6 * refV + 1e-30)
+    t_rp, t_ci, t_v = nmf.nmf_csr_transpose(d_rp, d_ci, d_v, m, n)
+    # Expected transpose, built with numpy: stable sort by (column, row).
+    rows = np.repeat(np.arange(m), np.diff(rowptr))
+    order = np.lexsort((rows, colidx))
+    exp_ci = rows[order].astype(np.int32)
+    exp_v = vals[order]
+    exp_rp = np.concatenate([[0], np.cumsum(np.bincount(colidx, minlength=n))])
+    assert np.array_equal(t_rp.cpu().numpy(), exp_rp)
+    assert np.array_equal(t_ci.cpu().numpy(), exp_ci)
+    assert np.array_equal(t_v.cpu().numpy(), exp_v)
+    Y = nmf.nmf_mm_csr(t_rp, t_ci, t_v, m, dev(W)).cpu().numpy().astype(np.float64)
+    refY = oracle.mm_csr(rowptr, colidx, vals, m, n, W.astype(np.float64), True)
+    assert np.all(np.abs(Y - refY) <= 2e-6 * refY + 1e-30)
+
+
+# ----------------------------------------------------------------------------- BPP
+def margin_ok(G, B, X, P, rel=1e-3):
+    """RHS whose KKT margin is safely away from zero: every passive x_i is at
+    least rel * max|x| and every active y_i at least rel * max|b|."""
+    Y = X @ G - B
+    xm = np.where(P, X, np.inf).min(axis=1) / np.maximum(np.abs(X).max(axis=1), 1e-300)
+    ym = np.where(~P, Y, np.inf).min(axis=1) / np.maximum(np.abs(B).max(axis=1), 1e-300)
+    return np.minimum(xm, ym) >= rel
+
+
+def run_bpp(nmf, G, B32, passive_in=None, max_rounds=100):
+    r = nmf.nmf_nls_bpp(dev(G), dev(B32), None if passive_in is None else dev(passive_in),
+                        max_rounds=max_rounds)
+    k = G.shape[0]
+    return (r["X"].cpu().numpy().astype(np.float64),
+            nmf.passive_to_bool(r["passive"], k).cpu().numpy(),
+            r["rounds"].cpu().numpy(), r["status"].cpu().numpy(), r["worst"])
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 10, 20, 32, 33, 50, 64, 65, 100, 128])
+def test_bpp_matches_oracle(nmf, k):
+    nrhs = 3000 if k <= 64 else 800
+    G, B = synth.nls_batch(k, nrhs, seed=100 + k)
+    B32 = B.astype(np.float32)
+    Bd = B32.astype(np.float64)
+    X, P, R, S, worst = run_bpp(nmf, G, B32)
+    Xo, Po, Ro, So, wo = oracle.bpp(G, Bd)
+    assert worst == nmf.NMF_OK and (S == 0).all()
+    cond = np.linalg.cond(G)
+    err = np.linalg.norm(X - Xo) / np.linalg.norm(Xo)
+    print(f"k={k} cond={cond:.0f} rel err {err:.2e} ({err / (cond * 6e-8):.3f} x cond*eps)")
+    assert err <= 20 * cond * 6e-8, (err, cond)
+    assert (X >= 0).all()
+    ok = margin_ok(G, Bd, Xo, Po.astype(bool))
+    assert ok.mean() > 0.4
+    assert np.array_equal(P[ok], Po.astype(bool)[ok])
+    # Round counts follow the same exchange rules; an intermediate partition can
+    # still flip on a near-zero FP32 value, so allow a small fraction to differ.
+    assert (R[ok] == Ro[ok]).mean() >= 0.98
+    assert (X[~P] == 0).all()
+
+
+@pytest.mark.parametrize("k", [10, 50])
+def test_bpp_anls_like(nmf, k):
+    # The W-update of Alg. 1 from a uniform start: G = H H^T of a positive H
+    # (one dominant eigenvalue, so G^{-1} has large entries of mixed sign) and
+    # right-hand sides A H^T. Every solve must converge and match the oracle.
+    m, n = 4000, 1000
+    A = synth.dense_planted(m, n, k, 0.05, seed=k)
+    _, Ht = synth.init_factors(m, n, k, seed=k + 1)
+    G = oracle.gram(Ht.astype(np.float64))
+    B32 = oracle.mm_dense(A, Ht.astype(np.float64), False).astype(np.float32)
+    X, P, R, S, worst = run_bpp(nmf, G, B32)
+    Xo, Po, Ro, So, wo = oracle.bpp(G, B32.astype(np.float64))
+    assert worst == nmf.NMF_OK and (S == 0).all(), np.bincount(S.astype(np.int64))
+    cond = np.linalg.cond(G)
+    err = np.linalg.norm(X - Xo) / np.linalg.norm(Xo)
+    print(f"k={k} cond={cond:.0f} rel err {err:.2e} max rounds {R.max()} vs {Ro.max()}")
+    assert err <= 20 * cond * 6e-8
+    ok = margin_ok(G, B32.astype(np.float64), Xo, Po.astype(bool))
+    assert np.array_equal(P[ok], Po.astype(bool)[ok])
+
+
+def test_bpp_warm_start(nmf):
+    k, nrhs = 50, 2000
+    G, B = synth.nls_batch(k, nrhs, seed=77)
+    B32 = B.astype(np.float32)
+    Xo, Po, Ro, So, wo = oracle.bpp(G, B32.astype(np.float64))
+    words = nmf.bool_to_passive(torch.from_numpy(Po.astype(bool))).numpy()
+    X, P, R, S, worst = run_bpp(nmf, G, B32, passive_in=words)
+    ok = margin_ok(G, B32.astype(np.float64), Xo, Po.astype(bool))
+    assert (R[ok] == 0).all()
+    assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 1e-4
+    # Warm start from a perturbed partition reaches the same point.
+    Pp = Po.astype(bool).copy()
+    Pp[:, ::4] = ~Pp[:, ::4]
+    X2, P2, R2, S2, w2 = run_bpp(nmf, G, B32,
+                                 passive_in=nmf.bool_to_passive(torch.from_numpy(Pp)).numpy())
+    assert w2 == nmf.NMF_OK
+    assert np.linalg.norm(X2 - Xo) / np.linalg.norm(Xo) <= 1e-4
+
+
+def test_bpp_round_cap_and_nonfinite(nmf):
+    k, nrhs = 20, 300
+    G, B = synth.nls_batch(k, nrhs, seed=9)
+    B32 = B.astype(np.float32)
+    X, P, R, S, worst = run_bpp(nmf, G, B32, max_rounds=0)
+    assert worst == nmf.NMF_ERR_NOT_CONVERGED
+    assert set(np.unique(S)) <= {0, nmf.NMF_ERR_NOT_CONVERGED}
+    B32[7, 3] = np.nan
+    X, P, R, S, worst = run_bpp(nmf, G, B32)
+    assert S[7] == nmf.NMF_ERR_NONFINITE and (X[7] == 0).all()
+    others = np.delete(np.arange(nrhs), 7)
+    assert (S[others] == 0).all() and worst == nmf.NMF_ERR_NONFINITE
+
+
+def test_bpp_zero_diagonal(nmf):
+    # A zero row of the factor: G_ii = 0 and b_i = 0; index stays active.
+    k, nrhs = 12, 400
+    G, B = synth.nls_batch(k, nrhs, seed=21)
+    G[4, :] = 0.0
+    G[:, 4] = 0.0
+    B[:, 4] = 0.0
+    B32 = B.astype(np.float32)
+    X, P, R, S, worst = run_bpp(nmf, G, B32)
+    Xo = oracle.bpp(G, B32.astype(np.float64))[0]
+    assert worst == nmf.NMF_OK and (X[:, 4] == 0).all()
+    assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 1e-4
+
+
+def test_bpp_ill_conditioned_fp64(nmf):
+    # cond(G) ~ 3e8: FP32 cannot resolve these systems, so the whole half-step
+    # runs in FP64 (cond_1(G) > 1e4) with the strict sign tests of the oracle.
+    k, nrhs = 24, 500
+    G, B = synth.nls_batch(k, nrhs, seed=31, cond_boost=1000.0)
+    assert np.linalg.cond(G) > 1e8
+    B32 = B.astype(np.float32)
+    Bd = B32.astype(np.float64)
+    X, P, R, S, worst = run_bpp(nmf, G, B32)
+    Xo, Po, Ro, So, wo = oracle.bpp(G, Bd)
+    assert worst == nmf.NMF_OK and (S == 0).all()
+    err = np.linalg.norm(X - Xo) / np.linalg.norm(Xo)
+    assert err <= 1e-6, err
+    ok = margin_ok(G, Bd, Xo, Po.astype(bool))
+    assert np.array_equal(P[ok], Po.astype(bool)[ok])
+
+
+def test_bpp_singular_gram(nmf):
+    # Two identical factor rows: G is singular even in FP64, so no inverse is
+    # formed and every system is solved directly in FP64. Solves whose passive
+    # set holds both copies are singular; the rest must satisfy Eq. 4.
+    k, nrhs = 16, 400
+    rng = np.random.default_rng(8)
+    C = rng.uniform(0, 1, (64, k))
+    C[:, 5] = C[:, 9]
+    G = C.T @ C
+    D = rng.uniform(-0.5, 1.0, (nrhs, 64))
+    B32 = (D @ C).astype(np.float32)
+    X, P, R, S, worst = run_bpp(nmf, G, B32)
+    assert set(np.unique(S)) <= {0, nmf.NMF_ERR_SINGULAR_GRAM}
+    good = S == 0
+    Bd = B32.astype(np.float64)
+    Y = X @ G - Bd
+    scale = np.abs(Bd).max(axis=1)
+    assert (X[good] >= 0).all()
+    assert (Y[good] >= -1e-9 * scale[good, None]).all()
+    assert (np.abs((X * Y)[good]).sum(axis=1) <= 1e-9 * (scale[good] * np.abs(X[good]).max(axis=1) + 1e-30)).all()
+
+
+def test_bpp_empty_batch(nmf):
+    G, B = synth.nls_batch(10, 1, seed=1)
+    r = nmf.nmf_nls_bpp(dev(G), torch.empty((0, 10), dtype=torch.float32, device="cuda"))
+    assert r["worst"] == nmf.NMF_OK and r["X"].shape == (0, 10)
+
+
+# ----------------------------------------------------------------------------- objective
+@pytest.mark.parametrize("shape,k", [((37, 23), 3), ((300, 1000), 10), ((1000, 300), 50),
+                                     ((129, 65), 100)])
+def test_objective_dense(nmf, shape, k):
+    m, n = shape
+    A = synth.dense_planted(m, n, k, 0.05, seed=m + n)
+    rng = np.random.default_rng(3)
+    W = rng.uniform(0, 1, (m, k)).astype(np.float32)
+    Ht = rng.uniform(0, 1, (n, k)).astype(np.float32)
+    f = nmf.nmf_objective_dense(dev(A), dev(W), dev(Ht))
+    ref = oracle.objective_dense(A, W, Ht)
+    assert abs(f - ref) <= 1e-5 * ref
