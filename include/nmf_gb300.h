@@ -127,6 +127,28 @@ typedef struct nmf_nls_desc {
  * internal device workspace (stream-ordered allocation, freed on return). */
 nmf_status nmf_nls_bpp(const nmf_nls_desc *d, void *stream);
 
+/* Allocation-free variant of nmf_nls_bpp (no counterpart in the paper; an
+ * interface of this library). Same arguments, computation and results as
+ * nmf_nls_bpp, but it never allocates device memory, for callers that cannot
+ * call cudaMalloc: code under a memory manager that owns all device memory
+ * (a framework's caching allocator or a fixed pool), latency-critical loops
+ * where cudaMalloc / cudaFree may synchronise the device, and programs that
+ * must not grow their device footprint after start-up. The caller supplies
+ * every input and output buffer, as for nmf_nls_bpp.
+ *   - Workspace: one fixed array of NMF_NOALLOC_SCRATCH_BYTES compiled into
+ *     the library; every GPU that loads the library holds it until exit.
+ *   - k > NMF_NOALLOC_MAX_K returns NMF_ERR_INVALID_ARG and launches nothing;
+ *     nrhs is not limited.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents:
+ *     calls that overlap on the GPU (for example on two streams at once)
+ *     race and corrupt each other's results. Keep them ordered.
+ *   - Waits for `stream` and returns the worst per-RHS status. */
+#define NMF_NOALLOC_MAX_K 128
+#define NMF_NOALLOC_SCRATCH_BYTES (272 * 1024)
+nmf_status nmf_nls_bpp_noalloc(const nmf_nls_desc *d, void *stream);
+
 /* Objective of Eq. 1 for dense A: f = sum_ij (A_ij - w_i . h_j)^2 with W
  * (m x k) and H^T (n x k), all device; the residuals are formed in FP32 and
  * their squares summed in FP64. Synchronises `stream`; writes *f_out (host). */

@@ -96,6 +96,7 @@ _c_mm_dense = _sig("nmf_mm_dense", [_P, _I64, _I64, _I64, _P, _I32, _I32, _I32, 
 _c_mm_csr = _sig("nmf_mm_csr", [_P, _P, _P, _I64, _I64, _P, _I32, _P, _P])
 _c_csr_transpose = _sig("nmf_csr_transpose", [_P, _P, _P, _I64, _I64, _I64, _P, _P, _P, _P])
 _c_nls_bpp = _sig("nmf_nls_bpp", [ctypes.POINTER(nmf_nls_desc), _P])
+_c_nls_bpp_noalloc = _sig("nmf_nls_bpp_noalloc", [ctypes.POINTER(nmf_nls_desc), _P])
 _c_objective_dense = _sig("nmf_objective_dense",
                           [_P, _I64, _I64, _I64, _P, _P, _I32, _I32,
                            ctypes.POINTER(ctypes.c_double), _P])
@@ -114,7 +115,7 @@ _lib.nmf_destroy.argtypes = [_P]
 _lib.nmf_destroy.restype = None
 
 EXPORTED = ["nmf_status_str", "nmf_gram", "nmf_mm_dense", "nmf_mm_csr", "nmf_csr_transpose",
-            "nmf_nls_bpp", "nmf_objective_dense", "nmf_init", "nmf_iterate", "nmf_sync",
+            "nmf_nls_bpp", "nmf_nls_bpp_noalloc", "nmf_objective_dense", "nmf_init", "nmf_iterate", "nmf_sync",
             "nmf_objective", "nmf_objective_history", "nmf_get_factors", "nmf_set_factors",
             "nmf_get_passive", "nmf_get_stats", "nmf_set_timing", "nmf_destroy"]
 
@@ -215,6 +216,20 @@ def nmf_nls_bpp(G: torch.Tensor, B: torch.Tensor, passive_in: torch.Tensor | Non
     G: k x k float64 (CUDA); B: nrhs x k float32. passive_in: nrhs x ceil(k/64)
     int64 bitmasks (warm start) or None (cold). Returns dict(X, passive, rounds,
     status (per RHS), worst (aggregate status))."""
+    return _nls_bpp(_c_nls_bpp, "nmf_nls_bpp", G, B, passive_in, max_rounds, outputs, stream)
+
+
+def nmf_nls_bpp_noalloc(G: torch.Tensor, B: torch.Tensor, passive_in: torch.Tensor | None = None,
+                        max_rounds: int = 100, outputs: bool = True, stream=None):
+    """Same as nmf_nls_bpp, through the allocation-free entry point: the
+    library allocates no device memory for the call (its workspace is a fixed
+    array inside the library). The output tensors are allocated here, by the
+    caller's side, as for nmf_nls_bpp."""
+    return _nls_bpp(_c_nls_bpp_noalloc, "nmf_nls_bpp_noalloc", G, B, passive_in, max_rounds,
+                    outputs, stream)
+
+
+def _nls_bpp(fn, name, G, B, passive_in, max_rounds, outputs, stream):
     _dev(G, torch.float64, "G")
     _dev(B, torch.float32, "B")
     nrhs, k = B.shape
@@ -230,9 +245,9 @@ def nmf_nls_bpp(G: torch.Tensor, B: torch.Tensor, passive_in: torch.Tensor | Non
         _dev(passive_in, torch.int64, "passive_in")
     d = nmf_nls_desc(k, nrhs, _ptr(G), _ptr(B), _ptr(X), _ptr(passive_in), _ptr(passive),
                      _ptr(rounds), _ptr(status), max_rounds)
-    worst = _c_nls_bpp(ctypes.byref(d), _stream(stream))
+    worst = fn(ctypes.byref(d), _stream(stream))
     if worst in (NMF_ERR_INVALID_ARG, NMF_ERR_CUDA, NMF_ERR_OOM):
-        raise NMFError(worst, "nmf_nls_bpp")
+        raise NMFError(worst, name)
     return dict(X=X, passive=passive, rounds=rounds, status=status, worst=worst)
 
 
