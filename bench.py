@@ -31,6 +31,8 @@ WORKLOADS = {
     # name: (m, n, k, sigma, description)
     "dense-large": (96000, 64000, 50, 0.05,
                     "dense A=W0*H0+|N(0,0.05^2)| 96000x64000 k=50 fp32 (24.6 GB)"),
+    "dense-medium": (24000, 16000, 50, 0.05,
+                     "dense A=W0*H0+|N(0,0.05^2)| 24000x16000 k=50 fp32 (1.5 GB)"),
     "dense-small": (2000, 1000, 10, 0.01,
                     "dense A=W0*H0+|N(0,0.01^2)| 2000x1000 k=10 fp32"),
 }
@@ -288,8 +290,9 @@ def run_ours(args, rank, world, local_rank):
                 "dtype": "f32" if args.precision == "fp32" else "bf16x3/f32",
                 "data": "synthetic",
                 "config": {"workload": desc, "precision": args.precision, "start": args.start,
-                           "seed": SEED, "l2": "inputs larger than L2 (A = 24.6 GB)"
-                           if args.workload == "dense-large" else "small input (L2-resident)",
+                           "seed": SEED,
+                           "l2": "small input (L2-resident)" if args.workload == "dense-small"
+                           else f"inputs larger than L2 (A = {4 * m * n / 1e9:.1f} GB)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
