@@ -77,7 +77,9 @@ nmf_status nmf_gram(const float *X, int64_t rows, int32_t k, double *G, void *st
  *            trans = 0: F = H^T (n x k), out = A H^T       (m x k);
  *            trans = 1: F = W   (m x k), out = A^T W = (W^T A)^T (n x k).
  *   out    device float32 row-major, no aliasing with A or F.
- *   precision  an nmf_precision value.
+ *   precision  an nmf_precision value. NMF_PREC_BF16X3 reads A with TMA and
+ *          needs a 16-byte-aligned A with lda a multiple of 4 (else
+ *          NMF_ERR_INVALID_ARG); it also needs k <= NMF_MAX_K only.
  * Zero-sized m or n is allowed (out is zero-filled when the contraction length
  * is 0). */
 nmf_status nmf_mm_dense(const float *A, int64_t m, int64_t n, int64_t lda, const float *F,
@@ -173,7 +175,9 @@ typedef struct nmf_config {
     int64_t m, n;              /* A is m x n */
     int32_t k;                 /* rank, 1..NMF_MAX_K */
     int32_t input_kind;        /* nmf_input_kind */
-    int32_t precision;         /* nmf_precision for the products and objective */
+    int32_t precision;         /* nmf_precision for the products and objective
+                                  (NMF_PREC_BF16X3: dense A 16-byte aligned,
+                                  lda a multiple of 4) */
     int32_t start_mode;        /* nmf_start_mode */
     int32_t max_bpp_rounds;    /* per-RHS exchange cap (e.g. 100) */
     int32_t objective_every;   /* 1: f after every iteration (history kept);

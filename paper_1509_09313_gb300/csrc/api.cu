@@ -390,6 +390,10 @@ extern "C" nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nm
     if (c.input_kind == NMF_INPUT_DENSE) {
         if (!A->dense || A->lda < c.n)
             return NMF_ERR_INVALID_ARG;
+        // The tensor-core path reads A with TMA: 16-byte-aligned rows.
+        if (c.precision == NMF_PREC_BF16X3 &&
+            ((reinterpret_cast<uintptr_t>(A->dense) & 15) || (A->lda % 4)))
+            return NMF_ERR_INVALID_ARG;
     } else if (c.input_kind == NMF_INPUT_CSR) {
         if (!A->rowptr || A->nnz < 0 || (A->nnz > 0 && (!A->colidx || !A->vals)))
             return NMF_ERR_INVALID_ARG;

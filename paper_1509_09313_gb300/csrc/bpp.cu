@@ -23,9 +23,9 @@
 //      complement  M_AA y_A = -u_A,  x_F = u_F + M_FA y_A  (|A| x |A|)
 //    (the second follows from G x = g + y with y supported on A and x_A = 0),
 //    by a warp-cooperative Cholesky in shared memory with shuffle-broadcast
-//    substitutions, then refines once (residual g_F - G_FF x_F solved through
-//    the same factor: the explicit inverse alone is not backward stable) and
-//    recomputes y from G. Cost per round O(min(|F|,|A|)^3 + k |F|) instead of
+//    substitutions. In FP32 it then refines once (residual g_F - G_FF x_F
+//    solved through the same factor: the explicit inverse alone is not
+//    backward stable) and recomputes y from G; in FP64 neither is needed. Cost per round O(min(|F|,|A|)^3 + k |F|) instead of
 //    O(|F|^3). In FP32 a pivot below 1e-4 of its diagonal sends that system to
 //    FP64, and a sign test counts as violated only beyond 2^-20 of the
 //    problem's scale (max |x| on F, max |g| off F): values within FP32 noise
@@ -594,8 +594,9 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                         }
                     }
                     __syncwarp();
-                    // One refinement step through the same factor.
-                    if (refine && nF > 0) {
+                    // One refinement step through the same factor (FP32 only:
+                    // in FP64 the explicit inverse is accurate to cond * 1e-16).
+                    if (MODE == 0 && refine && nF > 0) {
                         T w[KW], res[KW], up[KW];
 #pragma unroll
                         for (int s = 0; s < KW; ++s) {
@@ -645,18 +646,26 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                         }
                         __syncwarp();
                     }
-                    // y = G x - g off F (from G directly), 0 on F.
-                    T w[KW];
+                    // y = G x - g off F, 0 on F: recomputed from G in FP32; in
+                    // FP64 the complement solve's y_A is used as it stands.
                     T xm = 0;
 #pragma unroll
-                    for (int s = 0; s < KW; ++s) {
-                        w[s] = 0;
-                        xm = max(xm, inF[s] ? fabs(x[s]) : (T)0);
-                    }
-                    warp_matvec_masked<T, KW>(Gs, k, fm, x, w, lane);
-#pragma unroll
                     for (int s = 0; s < KW; ++s)
-                        y[s] = inF[s] ? (T)0 : w[s] - g[s];
+                        xm = max(xm, inF[s] ? fabs(x[s]) : (T)0);
+                    if (MODE != 0 && comp) {
+#pragma unroll
+                        for (int s = 0; s < KW; ++s)
+                            y[s] = inS[s] ? zbuf[rank[s]] : (inF[s] ? (T)0 : -g[s]);
+                    } else {
+                        T w[KW];
+#pragma unroll
+                        for (int s = 0; s < KW; ++s)
+                            w[s] = 0;
+                        warp_matvec_masked<T, KW>(Gs, k, fm, x, w, lane);
+#pragma unroll
+                        for (int s = 0; s < KW; ++s)
+                            y[s] = inF[s] ? (T)0 : w[s] - g[s];
+                    }
                     xtol = tolrel * warp_max(xm);
                     return NMF_OK;
                 };

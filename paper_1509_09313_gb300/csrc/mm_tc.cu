@@ -1,14 +1,671 @@
-// Dense products on tcgen05 tensor cores (BF16 head/tail split): not built yet.
+// Dense products of Alg. 1 (the "MM" task) on the 5th-generation tensor cores,
+// with BF16 head/tail operand splitting:
+//   trans = 0: out (m x k) = A H^T   (contract over n)
+//   trans = 1: out (n x k) = A^T W   (contract over m)
+// i.e. out[p][r] = sum_q A(p, q) F[q][r] with A(p, q) = A[p][q] or A[q][p].
+//
+// Every FP32 value v is split as v = hi + lo + O(2^-17 |v|), hi = bf16(v),
+// lo = bf16(v - hi); the product uses hi*hi + hi*lo + lo*hi (each term exact
+// in the FP32 accumulator's input), so a product's relative error is about
+// 2^-17 and unbiased.
+//
+// Kernel (one CTA per 128 output rows, 448 threads):
+//   warp 0     TMA producer: FP32 A tiles (128 x 64, or 64 x 128 for trans = 1)
+//              into a 3-stage staging ring; pre-split BF16 F tiles (N x 64,
+//              128-byte swizzle) into a 2-stage operand ring.
+//   warp 1     allocates TMEM; one lane issues tcgen05.mma (M = 128, N = 16,
+//              32 or 64, K = 16; 3 MMAs per 16-element step) and commits to
+//              mbarriers.
+//   warps 2-5  split each FP32 A tile into BF16 hi/lo tiles in the canonical
+//              K-major 128-byte-swizzled layout (transposing when trans = 1).
+//   warps 6-13 drain the TMEM accumulators (tcgen05.ld) into registers; two
+//              warps per TMEM lane quarter, each owning half of the N columns.
+// Accuracy: the tensor cores' FP32 accumulation truncates, so every MMA that
+// adds into an accumulator biases it by about half an ulp of its value;
+// accumulating all n / 16 * 3 steps in one place would bias the result by
+// ~1e-6 relative and spread it by as much, which the NLS solves amplify by
+// cond(G). The dominant hi*hi products therefore go to their own ping-pong
+// accumulator pair, drained after every K-block (4 MMAs), and the two cross
+// products (about 2^-8 smaller) to a second pair drained every 4 K-blocks;
+// warps 6-13 add each drained tile into registers with Kahan compensation.
+// Measured against FP64: bias and spread at the level of FP32 rounding.
+// F (H^T or W) is split once per call by mm_tc_split_kernel into a padded
+// N x Qp BF16 pair (the workspace); k > 64 is processed in 64-column chunks.
+// Every mbarrier wait is bounded (about 2 s); on timeout the kernel records
+// an error code in the workspace, leaves its loops, frees TMEM and returns.
+//
+// Roofline: HBM (A read once, 4 bytes per element; 2k flops per element).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
 #include "common.cuh"
 
 namespace nmf {
+namespace {
 
-size_t mm_tc_work_bytes(int64_t, int64_t, int, int) { return 0; }
+constexpr int TC_BM = 128;        // output rows per CTA (MMA M)
+constexpr int TC_BK = 64;         // contraction elements per K-block (128-byte BF16 row)
+constexpr int TC_F32_STAGES = 3;  // FP32 A staging ring
+constexpr int TC_BF_STAGES = 2;   // BF16 operand ring
+constexpr int TC_WIN2 = 4;        // K-blocks per cross-term accumulation window
+constexpr int TC_THREADS = 448;
+constexpr int TC_DRAIN_WARPS = 8;
+constexpr long long TC_WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
-nmf_status launch_mm_tc(const float *, int64_t, int64_t, int64_t, const float *, int, int,
-                        float *, void *, size_t, cudaStream_t)
+template <int N>
+struct TcLayout {
+    static constexpr int F32_BYTES = TC_BM * TC_BK * 4;   // 32 KB
+    static constexpr int A_BYTES = TC_BM * TC_BK * 2;     // 16 KB
+    static constexpr int B_BYTES = N * TC_BK * 2;
+    static constexpr int OFF_F32 = 0;
+    static constexpr int OFF_AHI = OFF_F32 + TC_F32_STAGES * F32_BYTES;
+    static constexpr int OFF_ALO = OFF_AHI + TC_BF_STAGES * A_BYTES;
+    static constexpr int OFF_BHI = OFF_ALO + TC_BF_STAGES * A_BYTES;
+    static constexpr int OFF_BLO = OFF_BHI + TC_BF_STAGES * B_BYTES;
+    static constexpr int OFF_BAR = (OFF_BLO + TC_BF_STAGES * B_BYTES + 1023) & ~1023;
+    // barriers: f32_full[3], f32_empty[3], b_full[2], a_full[2], bf_empty[2],
+    // acc1_full[2], acc1_empty[2], acc2_full[2], acc2_empty[2]
+    static constexpr int NBAR = 2 * TC_F32_STAGES + 3 * TC_BF_STAGES + 8;
+    static constexpr int OFF_TMEM = OFF_BAR + NBAR * 8;
+    static constexpr int OFF_ABORT = OFF_TMEM + 4;
+    static constexpr int BYTES = OFF_ABORT + 4;
+    static constexpr int TMEM_COLS = 4 * N < 32 ? 32 : 4 * N;   // D1 x 2, D2 x 2
+    static_assert(OFF_AHI % 1024 == 0 && OFF_BHI % 1024 == 0 && OFF_BLO % 1024 == 0 &&
+                      A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0,
+                  "128-byte-swizzled tiles need 1024-byte alignment");
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
-    return NMF_ERR_INVALID_ARG;
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait: false after ~2 s or once another thread has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort)
+{
+    const long long t0 = clock64();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity))
+            return true;
+        if ((it & 255u) == 0) {
+            if (*abort)
+                return false;
+            if (clock64() - t0 > TC_WAIT_CYCLES) {
+                *abort = 1;
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 A and B, FP32 D, both K-major.
+template <int N>
+__device__ __forceinline__ uint32_t idesc_bf16_f32()
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     bar)
+                 : "memory");
+}
+
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
+template <int C>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[C])
+{
+    if constexpr (C == 32)
+        tmem_ld32(taddr, v);
+    else if constexpr (C == 16)
+        tmem_ld16(taddr, v);
+    else
+        tmem_ld8(taddr, v);
+}
+
+// Split 8 FP32 values into packed BF16 hi and lo (16 bytes each).
+__device__ __forceinline__ void split8(const float (&v)[8], uint4 &hi, uint4 &lo)
+{
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 hb = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        const float2 hf = __bfloat1622float2(hb);
+        const __nv_bfloat162 lb = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
+        h[i] = *reinterpret_cast<const uint32_t *>(&hb);
+        l[i] = *reinterpret_cast<const uint32_t *>(&lb);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Byte offset of (row r, 16-byte chunk c) in a 128-byte-swizzled K-major tile.
+__device__ __forceinline__ uint32_t sw128_off(int r, int c)
+{
+    return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
+}
+
+// -------------------------------------------------------------------- kernel
+template <int N, int TRANS>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    mm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
+                 const __grid_constant__ CUtensorMap tmBlo, int64_t P, int64_t Q, int k, int col0,
+                 int kc, float *__restrict__ out, int *__restrict__ err)
+{
+    using L = TcLayout<N>;
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+    const uint32_t sbase = smem_u32(smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int *abort = reinterpret_cast<volatile int *>(smem + L::OFF_ABORT);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::OFF_TMEM);
+
+    const uint32_t bar0 = sbase + L::OFF_BAR;
+    auto f32_full = [&](int i) { return bar0 + 8u * i; };
+    auto f32_empty = [&](int i) { return bar0 + 8u * (TC_F32_STAGES + i); };
+    auto b_full = [&](int i) { return bar0 + 8u * (2 * TC_F32_STAGES + i); };
+    auto a_full = [&](int i) { return bar0 + 8u * (2 * TC_F32_STAGES + TC_BF_STAGES + i); };
+    auto bf_empty = [&](int i) { return bar0 + 8u * (2 * TC_F32_STAGES + 2 * TC_BF_STAGES + i); };
+    const uint32_t accb = bar0 + 8u * (2 * TC_F32_STAGES + 3 * TC_BF_STAGES);
+    auto acc1_full = [&](int i) { return accb + 8u * i; };
+    auto acc1_empty = [&](int i) { return accb + 8u * (2 + i); };
+    auto acc2_full = [&](int i) { return accb + 8u * (4 + i); };
+    auto acc2_empty = [&](int i) { return accb + 8u * (6 + i); };
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < TC_F32_STAGES; ++i) {
+            mbar_init(f32_full(i), 1);
+            mbar_init(f32_empty(i), 4);
+        }
+        for (int i = 0; i < TC_BF_STAGES; ++i) {
+            mbar_init(b_full(i), 1);
+            mbar_init(a_full(i), 4);
+            mbar_init(bf_empty(i), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(acc1_full(i), 1);
+            mbar_init(acc1_empty(i), TC_DRAIN_WARPS);
+            mbar_init(acc2_full(i), 1);
+            mbar_init(acc2_empty(i), TC_DRAIN_WARPS);
+        }
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"((uint32_t)L::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int64_t p0 = (int64_t)blockIdx.x * TC_BM;
+    const int nkb = (int)((Q + TC_BK - 1) / TC_BK);
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int fs = kb % TC_F32_STAGES, fr = kb / TC_F32_STAGES;
+                const int bs = kb % TC_BF_STAGES, br = kb / TC_BF_STAGES;
+                if (!mbar_wait(f32_empty(fs), (fr & 1) ^ 1, abort))
+                    break;
+                mbar_arrive_expect_tx(f32_full(fs), L::F32_BYTES);
+                const uint32_t dstA = sbase + L::OFF_F32 + fs * L::F32_BYTES;
+                if (TRANS == 0)
+                    tma_load_2d(dstA, &tmA, kb * TC_BK, (int)p0, f32_full(fs));
+                else
+                    tma_load_2d(dstA, &tmA, (int)p0, kb * TC_BK, f32_full(fs));
+                if (!mbar_wait(bf_empty(bs), (br & 1) ^ 1, abort))
+                    break;
+                mbar_arrive_expect_tx(b_full(bs), 2 * L::B_BYTES);
+                tma_load_2d(sbase + L::OFF_BHI + bs * L::B_BYTES, &tmBhi, kb * TC_BK, 0, b_full(bs));
+                tma_load_2d(sbase + L::OFF_BLO + bs * L::B_BYTES, &tmBlo, kb * TC_BK, 0, b_full(bs));
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        // TMEM columns: D1 buffers at [0, N) and [N, 2N) (hi*hi, one K-block
+        // each), D2 buffers at [2N, 3N) and [3N, 4N) (hi*lo + lo*hi, windows
+        // of TC_WIN2 K-blocks).
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16_f32<N>();
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int bs = kb % TC_BF_STAGES, br = kb / TC_BF_STAGES;
+                const int b1 = kb & 1, u1 = kb >> 1;
+                const int w2 = kb / TC_WIN2, b2 = w2 & 1, u2 = w2 >> 1;
+                const bool first2 = (kb % TC_WIN2) == 0;
+                if (!mbar_wait(acc1_empty(b1), (u1 & 1) ^ 1, abort))
+                    break;
+                if (first2 && !mbar_wait(acc2_empty(b2), (u2 & 1) ^ 1, abort))
+                    break;
+                if (!mbar_wait(a_full(bs), br & 1, abort) || !mbar_wait(b_full(bs), br & 1, abort))
+                    break;
+                tc_fence_after();
+                const uint32_t d1 = tmem + (uint32_t)(b1 * N);
+                const uint32_t d2 = tmem + (uint32_t)((2 + b2) * N);
+                const uint32_t ahi = sbase + L::OFF_AHI + bs * L::A_BYTES;
+                const uint32_t alo = sbase + L::OFF_ALO + bs * L::A_BYTES;
+                const uint32_t bhi = sbase + L::OFF_BHI + bs * L::B_BYTES;
+                const uint32_t blo = sbase + L::OFF_BLO + bs * L::B_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                    const uint32_t o = kk * 32;   // 16 BF16 elements along K
+                    mma_bf16(d1, sw128_desc(ahi + o), sw128_desc(bhi + o), idesc, kk ? 1u : 0u);
+                }
+                mma_commit(acc1_full(b1));
+#pragma unroll
+                for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                    const uint32_t o = kk * 32;
+                    mma_bf16(d2, sw128_desc(ahi + o), sw128_desc(blo + o), idesc,
+                             (first2 && kk == 0) ? 0u : 1u);
+                    mma_bf16(d2, sw128_desc(alo + o), sw128_desc(bhi + o), idesc, 1u);
+                }
+                mma_commit(bf_empty(bs));
+                if ((kb % TC_WIN2) == TC_WIN2 - 1 || kb == nkb - 1)
+                    mma_commit(acc2_full(b2));
+            }
+        }
+    } else if (warp < 6) {
+        // ---------------------------------------------------- split (warps 2-5)
+        const int ct = threadIdx.x - 64;        // 0..127
+        const int cw = ct >> 5;                 // converter warp 0..3
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int fs = kb % TC_F32_STAGES, fr = kb / TC_F32_STAGES;
+            const int bs = kb % TC_BF_STAGES, br = kb / TC_BF_STAGES;
+            if (!mbar_wait(f32_full(fs), fr & 1, abort) ||
+                !mbar_wait(bf_empty(bs), (br & 1) ^ 1, abort))
+                break;
+            const unsigned char *src = smem + L::OFF_F32 + fs * L::F32_BYTES;
+            unsigned char *ahi = smem + L::OFF_AHI + bs * L::A_BYTES;
+            unsigned char *alo = smem + L::OFF_ALO + bs * L::A_BYTES;
+            if (TRANS == 0) {
+                // src: 128 rows (p) x 64 floats (q), 256 bytes per row.
+#pragma unroll 2
+                for (int it = 0; it < TC_BM / 16; ++it) {
+                    const int r = it * 16 + cw * 4 + (lane >> 3);
+                    const int c = lane & 7;
+                    const float4 a = *reinterpret_cast<const float4 *>(src + r * 256 + c * 32);
+                    const float4 b = *reinterpret_cast<const float4 *>(src + r * 256 + c * 32 + 16);
+                    const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+                    uint4 hi, lo;
+                    split8(v, hi, lo);
+                    *reinterpret_cast<uint4 *>(ahi + sw128_off(r, c)) = hi;
+                    *reinterpret_cast<uint4 *>(alo + sw128_off(r, c)) = lo;
+                }
+            } else {
+                // src: 64 rows (q) x 128 floats (p), 512 bytes per row; row p = ct.
+                const float *sp = reinterpret_cast<const float *>(src);
+#pragma unroll 2
+                for (int c = 0; c < TC_BK / 8; ++c) {
+                    float v[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        v[j] = sp[(8 * c + j) * TC_BM + ct];
+                    uint4 hi, lo;
+                    split8(v, hi, lo);
+                    *reinterpret_cast<uint4 *>(ahi + sw128_off(ct, c)) = hi;
+                    *reinterpret_cast<uint4 *>(alo + sw128_off(ct, c)) = lo;
+                }
+            }
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(a_full(bs));
+                mbar_arrive(f32_empty(fs));
+            }
+        }
+    } else {
+        // ------------------------------------------------ drain (warps 6-13)
+        constexpr int NH = N / 2;               // columns owned by this warp
+        const int dw = warp - 6;
+        const int quarter = warp & 3;           // TMEM lane quarter of this warp
+        const int cbase = (dw >> 2) * NH;       // first owned column
+        float sum[NH], cmp[NH];
+#pragma unroll
+        for (int c = 0; c < NH; ++c) {
+            sum[c] = 0.0f;
+            cmp[c] = 0.0f;
+        }
+        auto add_tile = [&](uint32_t ta) {
+            float v[NH];
+            tmem_ld<NH>(ta, v);
+#pragma unroll
+            for (int i = 0; i < NH; ++i) {
+                const float y = v[i] - cmp[i];
+                const float t = sum[i] + y;
+                cmp[i] = (t - sum[i]) - y;
+                sum[i] = t;
+            }
+        };
+        const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cbase;
+        bool ok = true;
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+            const int b1 = kb & 1, u1 = kb >> 1;
+            if (!mbar_wait(acc1_full(b1), u1 & 1, abort)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            add_tile(tq + (uint32_t)(b1 * N));
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(acc1_empty(b1));
+            if ((kb % TC_WIN2) == TC_WIN2 - 1 || kb == nkb - 1) {
+                const int w2 = kb / TC_WIN2, b2 = w2 & 1, u2 = w2 >> 1;
+                if (!mbar_wait(acc2_full(b2), u2 & 1, abort)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                add_tile(tq + (uint32_t)((2 + b2) * N));
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(acc2_empty(b2));
+            }
+        }
+        if (ok) {
+            const int64_t p = p0 + quarter * 32 + lane;
+            if (p < P) {
+                float *o = out + p * k + col0 + cbase;
+#pragma unroll
+                for (int c = 0; c < NH; ++c)
+                    if (cbase + c < kc)
+                        o[c] = sum[c] - cmp[c];
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort)
+        atomicExch(err, 1);
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"((uint32_t)L::TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// F (Q x k, float32 row-major) columns [col0, col0 + kc) -> BF16 hi / lo
+// tiles laid out [N rows (r)][Qp cols (q)], zero-padded. 32 x 32 transposes.
+__global__ void mm_tc_split_kernel(const float *__restrict__ F, int64_t Q, int k, int col0,
+                                   int kc, int N, int64_t Qp, __nv_bfloat16 *__restrict__ hi,
+                                   __nv_bfloat16 *__restrict__ lo)
+{
+    __shared__ float t[32][33];
+    const int64_t q0 = (int64_t)blockIdx.x * 32;
+    const int r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t q = q0 + i;
+        const int r = r0 + threadIdx.x;
+        t[i][threadIdx.x] = (q < Q && r < kc) ? F[q * k + col0 + r] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i;
+        const int64_t q = q0 + threadIdx.x;
+        if (r < N && q < Qp) {
+            const float v = t[threadIdx.x][i];
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            hi[(int64_t)r * Qp + q] = h;
+            lo[(int64_t)r * Qp + q] = __float2bfloat16_rn(v - __bfloat162float(h));
+        }
+    }
+}
+
+// ------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+bool make_map_2d(CUtensorMap *map, CUtensorMapDataType dt, const void *base, uint64_t dim0,
+                 uint64_t dim1, uint64_t stride1_bytes, uint32_t box0, uint32_t box1,
+                 CUtensorMapSwizzle sw)
+{
+    auto fn = encode_fn();
+    if (!fn)
+        return false;
+    const cuuint64_t dims[2] = {dim0, dim1};
+    const cuuint64_t strides[1] = {stride1_bytes};
+    const cuuint32_t box[2] = {box0, box1};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+constexpr size_t TC_ERR_BYTES = 256;
+
+template <int N, int TRANS>
+nmf_status launch_tc(const CUtensorMap &tA, const CUtensorMap &tBh, const CUtensorMap &tBl,
+                     int64_t P, int64_t Q, int k, int col0, int kc, float *out, int *err,
+                     cudaStream_t s)
+{
+    using L = TcLayout<N>;
+    const int smem = L::BYTES + 1024;
+    static int configured = 0;
+    if (!configured) {
+        NMF_CUDA(cudaFuncSetAttribute(mm_tc_kernel<N, TRANS>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        configured = 1;
+    }
+    const unsigned grid = (unsigned)cdiv(P, TC_BM);
+    mm_tc_kernel<N, TRANS><<<grid, TC_THREADS, smem, s>>>(tA, tBh, tBl, P, Q, k, col0, kc, out,
+                                                          err);
+    NMF_LAUNCHED("mm_tc_kernel");
+    return NMF_OK;
+}
+
+}  // namespace
+
+size_t mm_tc_work_bytes(int64_t m, int64_t n, int k, int trans)
+{
+    const int64_t Q = trans ? m : n;
+    const int64_t Qp = cdiv(Q > 0 ? Q : 1, TC_BK) * TC_BK;
+    const int N = k <= 16 ? 16 : k <= 32 ? 32 : 64;
+    return TC_ERR_BYTES + 2 * sizeof(__nv_bfloat16) * (size_t)N * (size_t)Qp;
+}
+
+nmf_status launch_mm_tc(const float *A, int64_t m, int64_t n, int64_t lda, const float *F,
+                        int k, int trans, float *out, void *work, size_t work_bytes,
+                        cudaStream_t s)
+{
+    const int64_t P = trans ? n : m;
+    const int64_t Q = trans ? m : n;
+    if (P == 0)
+        return NMF_OK;
+    if (Q == 0)
+        return cudaMemsetAsync(out, 0, sizeof(float) * (size_t)P * k, s) == cudaSuccess
+                   ? NMF_OK
+                   : NMF_ERR_CUDA;
+    // TMA needs a 16-byte-aligned base and row pitch; coordinates must fit int32.
+    if ((reinterpret_cast<uintptr_t>(A) & 15) || (lda % 4) || P > INT32_MAX || Q > INT32_MAX)
+        return NMF_ERR_INVALID_ARG;
+    if (!work || work_bytes < mm_tc_work_bytes(m, n, k, trans))
+        return NMF_ERR_INVALID_ARG;
+    const int64_t Qp = cdiv(Q, TC_BK) * TC_BK;
+    int *err = static_cast<int *>(work);
+    NMF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    __nv_bfloat16 *bhi = reinterpret_cast<__nv_bfloat16 *>(static_cast<char *>(work) + TC_ERR_BYTES);
+    CUtensorMap tA;
+    bool ok = trans == 0
+                  ? make_map_2d(&tA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)Q, (uint64_t)P,
+                                (uint64_t)lda * 4, TC_BK, TC_BM, CU_TENSOR_MAP_SWIZZLE_NONE)
+                  : make_map_2d(&tA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)P, (uint64_t)Q,
+                                (uint64_t)lda * 4, TC_BM, TC_BK, CU_TENSOR_MAP_SWIZZLE_NONE);
+    if (!ok)
+        return NMF_ERR_CUDA;
+    for (int col0 = 0; col0 < k; col0 += 64) {
+        const int kc = k - col0 < 64 ? k - col0 : 64;
+        const int N = kc <= 16 ? 16 : kc <= 32 ? 32 : 64;
+        __nv_bfloat16 *blo = bhi + (size_t)N * Qp;
+        dim3 sg((unsigned)cdiv(Qp, 32), (unsigned)cdiv(N, 32));
+        mm_tc_split_kernel<<<sg, dim3(32, 8), 0, s>>>(F, Q, k, col0, kc, N, Qp, bhi, blo);
+        NMF_LAUNCHED("mm_tc_split_kernel");
+        CUtensorMap tBh, tBl;
+        if (!make_map_2d(&tBh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, bhi, (uint64_t)Qp, (uint64_t)N,
+                         (uint64_t)Qp * 2, TC_BK, (uint32_t)N, CU_TENSOR_MAP_SWIZZLE_128B) ||
+            !make_map_2d(&tBl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, blo, (uint64_t)Qp, (uint64_t)N,
+                         (uint64_t)Qp * 2, TC_BK, (uint32_t)N, CU_TENSOR_MAP_SWIZZLE_128B))
+            return NMF_ERR_CUDA;
+        nmf_status st;
+        if (N == 16)
+            st = trans ? launch_tc<16, 1>(tA, tBh, tBl, P, Q, k, col0, kc, out, err, s)
+                       : launch_tc<16, 0>(tA, tBh, tBl, P, Q, k, col0, kc, out, err, s);
+        else if (N == 32)
+            st = trans ? launch_tc<32, 1>(tA, tBh, tBl, P, Q, k, col0, kc, out, err, s)
+                       : launch_tc<32, 0>(tA, tBh, tBl, P, Q, k, col0, kc, out, err, s);
+        else
+            st = trans ? launch_tc<64, 1>(tA, tBh, tBl, P, Q, k, col0, kc, out, err, s)
+                       : launch_tc<64, 0>(tA, tBh, tBl, P, Q, k, col0, kc, out, err, s);
+        NMF_TRY(st);
+    }
+    return NMF_OK;
 }
 
 }  // namespace nmf

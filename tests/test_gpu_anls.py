@@ -61,25 +61,27 @@ def check(nmf, g, ref, ftol=1e-5, xtol=1e-4):
     assert (g["f"][1:] <= g["f"][:-1] * (1 + 1e-6)).all()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
 @pytest.mark.parametrize("start", ["cold", "warm"])
-def test_dense_small_config(nmf, start):
+def test_dense_small_config(nmf, start, precision):
     # A = W0 H0 + |N(0, 0.01^2)|, 2000 x 1000, k = 10, 10 iterations.
     m, n, k, T = 2000, 1000, 10, 10
     A = synth.dense_planted(m, n, k, 0.01)
     W0, Ht0 = synth.init_factors(m, n, k)
     ref = oracle.anls(A, W0, Ht0, iters=T)
-    g = run_gpu(nmf, A, W0, Ht0, T, start=start)
+    g = run_gpu(nmf, A, W0, Ht0, T, start=start, precision=precision)
     check(nmf, g, ref)
 
 
-def test_dense_large_config_crop(nmf):
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_dense_large_config_crop(nmf, precision):
     # The 96000 x 64000 recipe (k = 50, sigma = 0.05) on its 4000 x 2000 crop,
     # 30 iterations.
     m, n, k, T = 4000, 2000, 50, 30
     A = synth.dense_planted(m, n, k, 0.05, m_full=96000, n_full=64000)
     W0, Ht0 = synth.init_factors(m, n, k)
     ref = oracle.anls(A, W0, Ht0, iters=T)
-    g = run_gpu(nmf, A, W0, Ht0, T, start="warm")
+    g = run_gpu(nmf, A, W0, Ht0, T, start="warm", precision=precision)
     check(nmf, g, ref)
 
 

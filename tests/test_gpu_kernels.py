@@ -67,6 +67,37 @@ def test_mm_dense_fp32(nmf, shape, k, trans):
     assert np.sqrt(np.mean(rel ** 2)) <= 2e-7
 
 
+@pytest.mark.parametrize("shape", [(1, 4), (37, 24), (129, 256), (300, 1000), (1000, 300),
+                                   (2050, 20), (4099, 132)])
+@pytest.mark.parametrize("k", [1, 10, 16, 17, 33, 50, 64, 100, 128])
+@pytest.mark.parametrize("trans", [0, 1])
+def test_mm_dense_bf16x3(nmf, shape, k, trans):
+    # Tensor-core path: each product carries a relative error <= 2^-16 from
+    # the head/tail split (|err| <= 2e-5 (|A||F|) elementwise, random sign, so
+    # ~2^-17 / sqrt(terms) RMS); the tensor cores' truncating accumulation adds
+    # a bias of about half an ulp per MMA into an accumulator, bounded by the
+    # one-K-block drain of the head products to ~2e-7.
+    m, n = shape
+    rng = np.random.default_rng(m * 3 + n * 11 + k + 7 * trans)
+    A = rng.uniform(0, 1, (m, n)).astype(np.float32)
+    F = rng.uniform(0, 1, (n if trans == 0 else m, k)).astype(np.float32)
+    out = nmf.nmf_mm_dense(dev(A), dev(F), bool(trans), precision="bf16x3")
+    out = out.cpu().numpy().astype(np.float64)
+    ref = oracle.mm_dense(A, F.astype(np.float64), bool(trans))
+    assert np.all(np.abs(out - ref) <= 2e-5 * ref + 1e-30)
+    rel = (out - ref) / np.where(ref == 0, 1, ref)
+    q = m if trans else n
+    assert np.sqrt(np.mean(rel ** 2)) <= 1.2e-5 / np.sqrt(q) + 2e-7
+
+
+def test_mm_dense_bf16x3_needs_aligned_rows(nmf):
+    # The tensor-core path reads A with TMA: rows must start on 16 bytes.
+    A = torch.zeros((16, 17), dtype=torch.float32, device="cuda")
+    F = torch.zeros((17, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(nmf.NMFError):
+        nmf.nmf_mm_dense(A, F, False, precision="bf16x3")
+
+
 @pytest.mark.parametrize("trans", [0, 1])
 def test_mm_dense_strided_and_signed(nmf, trans):
     # Leading dimension > n and not a multiple of 4 (scalar-load path), signed data.
