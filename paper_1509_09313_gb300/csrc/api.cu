@@ -169,10 +169,22 @@ extern "C" nmf_status nmf_objective_dense(const float *A, int64_t m, int64_t n, 
         return NMF_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
     TempBuf part(s), f(s);
-    NMF_CUDA(part.alloc(sizeof(double) * (size_t)objective_partials_len()));
     NMF_CUDA(f.alloc(sizeof(double)));
-    NMF_TRY(launch_objective_dense(A, m, n, lda, W, Ht, k, precision,
-                                   static_cast<double *>(part.p), static_cast<double *>(f.p), s));
+    if (precision == NMF_PREC_BF16X3 && k <= 64 && m > 0 && n > 0) {
+        // Tensor cores: the objective rides on an A H^T pass whose product
+        // goes to scratch.
+        const size_t wb = mm_tc_work_bytes(m, n, k, 0);
+        TempBuf w(s), v(s);
+        NMF_CUDA(w.alloc(wb));
+        NMF_CUDA(v.alloc(sizeof(float) * (size_t)m * k));
+        NMF_TRY(launch_mm_tc_obj(A, m, n, lda, Ht, k, 0, static_cast<float *>(v.p), W, Ht,
+                                 static_cast<double *>(f.p), w.p, wb, s));
+    } else {
+        NMF_CUDA(part.alloc(sizeof(double) * (size_t)objective_partials_len()));
+        NMF_TRY(launch_objective_dense(A, m, n, lda, W, Ht, k, precision,
+                                       static_cast<double *>(part.p), static_cast<double *>(f.p),
+                                       s));
+    }
     NMF_CUDA(cudaMemcpyAsync(f_out, f.p, sizeof(double), cudaMemcpyDeviceToHost, s));
     NMF_CUDA(cudaStreamSynchronize(s));
     return NMF_OK;
@@ -205,6 +217,8 @@ struct nmf_handle {
     float *t_vals = nullptr;
     // Host state.
     bool passive_valid = false;
+    bool fused_obj = false;        // objective computed inside the next A H^T pass
+    bool obj_pending = false;      // f of the last iteration not yet computed
     int64_t f_count = 0;
     int64_t iterations = 0;
     BppStats reported{};                        // stats already turned into a status
@@ -291,6 +305,9 @@ nmf_status mm(nmf_handle *h, int trans, const float *F, float *out)
 nmf_status objective_into(nmf_handle *h, double *f_dev)
 {
     const nmf_config &c = h->cfg;
+    if (h->fused_obj)
+        return launch_mm_tc_obj(h->A.dense, c.m, c.n, h->A.lda, h->Ht, c.k, 0, h->V, h->W, h->Ht,
+                                f_dev, h->tc_work, h->tc_work_bytes, h->stream);
     if (c.input_kind == NMF_INPUT_CSR) {
         NMF_TRY(launch_gram(h->Ht, c.n, c.k, h->GH, h->gram_part, h->stream));
         NMF_TRY(launch_gram(h->W, c.m, c.k, h->GW, h->gram_part, h->stream));
@@ -312,7 +329,15 @@ nmf_status one_iteration(nmf_handle *h)
     }
     {
         PhaseTimer t(h, 1);
-        NMF_TRY(mm(h, 0, h->Ht, h->V));
+        if (h->obj_pending) {
+            // The previous iterate's f(W, H) rides on this A H^T pass.
+            double *slot = h->f_hist + ((h->f_count - 1) % F_HIST_CAP);
+            NMF_TRY(launch_mm_tc_obj(h->A.dense, c.m, c.n, h->A.lda, h->Ht, c.k, 0, h->V, h->W,
+                                     h->Ht, slot, h->tc_work, h->tc_work_bytes, h->stream));
+            h->obj_pending = false;
+        } else {
+            NMF_TRY(mm(h, 0, h->Ht, h->V));
+        }
     }
     {
         PhaseTimer t(h, 2);
@@ -335,12 +360,30 @@ nmf_status one_iteration(nmf_handle *h)
     }
     h->passive_valid = true;
     if (c.objective_every) {
-        PhaseTimer t(h, 3);
-        NMF_TRY(objective_into(h, h->f_hist + (h->f_count % F_HIST_CAP)));
+        if (h->fused_obj) {
+            h->obj_pending = true;   // computed by the next A H^T pass or a flush
+        } else {
+            PhaseTimer t(h, 3);
+            NMF_TRY(objective_into(h, h->f_hist + (h->f_count % F_HIST_CAP)));
+        }
         h->f_count += 1;
     }
     h->iterations += 1;
     return NMF_OK;
+}
+
+// Compute a pending objective (fused mode) into its history slot.
+nmf_status flush_objective(nmf_handle *h)
+{
+    if (!h->obj_pending)
+        return NMF_OK;
+    const unsigned long long before = launch_count;
+    PhaseTimer t(h, 3);
+    const nmf_status st = objective_into(h, h->f_hist + ((h->f_count - 1) % F_HIST_CAP));
+    h->launches += (int64_t)(launch_count - before);
+    if (st == NMF_OK)
+        h->obj_pending = false;
+    return st;
 }
 
 void free_handle(nmf_handle *h)
@@ -426,6 +469,7 @@ extern "C" nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nm
     chk(dalloc(&h->obj_part, (size_t)objective_partials_len()));
     chk(dalloc(&h->f_hist, (size_t)F_HIST_CAP));
     chk(dalloc(&h->f_now, 1));
+    h->fused_obj = c.input_kind == NMF_INPUT_DENSE && c.precision == NMF_PREC_BF16X3 && c.k <= 64;
     if (e == cudaSuccess && c.input_kind == NMF_INPUT_DENSE && c.precision == NMF_PREC_BF16X3) {
         h->tc_work_bytes = mm_tc_work_bytes(c.m, c.n, c.k, 0);
         const size_t b1 = mm_tc_work_bytes(c.m, c.n, c.k, 1);
@@ -489,6 +533,7 @@ extern "C" nmf_status nmf_sync(nmf_handle *h)
 {
     if (!h)
         return NMF_ERR_INVALID_ARG;
+    NMF_TRY(flush_objective(h));
     BppStats st;
     NMF_CUDA(cudaMemcpyAsync(&st, h->stats_dev, sizeof(BppStats), cudaMemcpyDeviceToHost,
                              h->stream));
@@ -505,6 +550,7 @@ extern "C" nmf_status nmf_objective(nmf_handle *h, double *f_out)
 {
     if (!h || !f_out)
         return NMF_ERR_INVALID_ARG;
+    NMF_TRY(flush_objective(h));
     const unsigned long long before = launch_count;
     const nmf_status st = objective_into(h, h->f_now);
     h->launches += (int64_t)(launch_count - before);
@@ -519,6 +565,7 @@ extern "C" nmf_status nmf_objective_history(nmf_handle *h, double *f_host, int64
 {
     if (!h || !count || cap < 0 || (cap > 0 && !f_host))
         return NMF_ERR_INVALID_ARG;
+    NMF_TRY(flush_objective(h));
     NMF_CUDA(cudaStreamSynchronize(h->stream));
     const int64_t avail = h->f_count < F_HIST_CAP ? h->f_count : F_HIST_CAP;
     const int64_t nout = avail < cap ? avail : cap;
@@ -550,6 +597,7 @@ extern "C" nmf_status nmf_set_factors(nmf_handle *h, const float *W, const float
 {
     if (!h)
         return NMF_ERR_INVALID_ARG;
+    NMF_TRY(flush_objective(h));
     const size_t k = (size_t)h->cfg.k;
     if (W)
         NMF_CUDA(cudaMemcpyAsync(h->W, W, sizeof(float) * (size_t)h->cfg.m * k,
@@ -578,6 +626,7 @@ extern "C" nmf_status nmf_get_stats(nmf_handle *h, nmf_stats *out)
 {
     if (!h || !out)
         return NMF_ERR_INVALID_ARG;
+    NMF_TRY(flush_objective(h));
     BppStats st;
     NMF_CUDA(cudaMemcpyAsync(&st, h->stats_dev, sizeof(BppStats), cudaMemcpyDeviceToHost,
                              h->stream));

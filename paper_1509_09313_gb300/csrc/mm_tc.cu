@@ -1,25 +1,27 @@
 // Dense products of Alg. 1 (the "MM" task) on the 5th-generation tensor cores,
-// with BF16 head/tail operand splitting:
+// with BF16 head/tail operand splitting, and the objective of Eq. 1 fused into
+// the A H^T pass:
 //   trans = 0: out (m x k) = A H^T   (contract over n)
 //   trans = 1: out (n x k) = A^T W   (contract over m)
 // i.e. out[p][r] = sum_q A(p, q) F[q][r] with A(p, q) = A[p][q] or A[q][p].
 //
 // Every FP32 value v is split as v = hi + lo + O(2^-17 |v|), hi = bf16(v),
-// lo = bf16(v - hi); the product uses hi*hi + hi*lo + lo*hi (each term exact
-// in the FP32 accumulator's input), so a product's relative error is about
-// 2^-17 and unbiased.
+// lo = bf16(v - hi); a product uses hi*hi + hi*lo + lo*hi (each term exact in
+// the FP32 accumulator's input), so its relative error is about 2^-17 and
+// unbiased.
 //
 // Kernel (one CTA per 128 output rows, 448 threads):
-//   warp 0     TMA producer: FP32 A tiles (128 x 64, or 64 x 128 for trans = 1)
-//              into a 3-stage staging ring; pre-split BF16 F tiles (N x 64,
-//              128-byte swizzle) into a 2-stage operand ring.
+//   warp 0     TMA producer: FP32 A tiles (128 x 64 as two 128-byte-swizzled
+//              halves, or 64 x 128 unswizzled for trans = 1) into a staging
+//              ring; pre-split BF16 F tiles (N x 64, 128-byte swizzle) into a
+//              2-stage operand ring.
 //   warp 1     allocates TMEM; one lane issues tcgen05.mma (M = 128, N = 16,
 //              32 or 64, K = 16; 3 MMAs per 16-element step) and commits to
 //              mbarriers.
 //   warps 2-5  split each FP32 A tile into BF16 hi/lo tiles in the canonical
 //              K-major 128-byte-swizzled layout (transposing when trans = 1).
 //   warps 6-13 drain the TMEM accumulators (tcgen05.ld) into registers; two
-//              warps per TMEM lane quarter, each owning half of the N columns.
+//              warps per TMEM lane quarter, each owning half of the columns.
 // Accuracy: the tensor cores' FP32 accumulation truncates, so every MMA that
 // adds into an accumulator biases it by about half an ulp of its value;
 // accumulating all n / 16 * 3 steps in one place would bias the result by
@@ -27,14 +29,26 @@
 // cond(G). The dominant hi*hi products therefore go to their own ping-pong
 // accumulator pair, drained after every K-block (4 MMAs), and the two cross
 // products (about 2^-8 smaller) to a second pair drained every 4 K-blocks;
-// warps 6-13 add each drained tile into registers with Kahan compensation.
-// Measured against FP64: bias and spread at the level of FP32 rounding.
+// the drain warps add each tile into registers with Kahan compensation.
+// Measured against FP64 at n = 64000: bias -4e-8, spread 3e-8 (plain FP32
+// rounding: spread 2.3e-8).
+//
+// Fused objective (trans = 0, k <= 64): with W and H^T given, every K-block
+// also forms the 128 x 64 tile of W H (W tile resident in shared memory,
+// K = k padded to 64, three split products) in a third ping-pong TMEM pair;
+// the drain warps subtract it from the staged FP32 A tile and add the squared
+// residuals in FP64. The A H^T pass of an ANLS iteration thereby yields
+// f(W, H) of the previous iterate without reading A again. A relative bias b
+// of W H shifts f by about S b with S = 2 mean(r) mean(WH) / mean(r^2)
+// (|S| <= 4 on the dense workloads), far inside the 1e-5 tolerance.
+//
 // F (H^T or W) is split once per call by mm_tc_split_kernel into a padded
 // N x Qp BF16 pair (the workspace); k > 64 is processed in 64-column chunks.
 // Every mbarrier wait is bounded (about 2 s); on timeout the kernel records
 // an error code in the workspace, leaves its loops, frees TMEM and returns.
 //
-// Roofline: HBM (A read once, 4 bytes per element; 2k flops per element).
+// Roofline: HBM (A read once, 4 bytes per element; 2k flops per element for
+// the product, 2k more for the fused objective).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -48,34 +62,47 @@ namespace {
 
 constexpr int TC_BM = 128;        // output rows per CTA (MMA M)
 constexpr int TC_BK = 64;         // contraction elements per K-block (128-byte BF16 row)
-constexpr int TC_F32_STAGES = 3;  // FP32 A staging ring
 constexpr int TC_BF_STAGES = 2;   // BF16 operand ring
 constexpr int TC_WIN2 = 4;        // K-blocks per cross-term accumulation window
 constexpr int TC_THREADS = 448;
 constexpr int TC_DRAIN_WARPS = 8;
 constexpr long long TC_WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
-template <int N>
+template <int N, int OBJ>
 struct TcLayout {
+    static constexpr int F32_STAGES = OBJ ? 2 : 3;         // FP32 A staging ring
     static constexpr int F32_BYTES = TC_BM * TC_BK * 4;   // 32 KB
     static constexpr int A_BYTES = TC_BM * TC_BK * 2;     // 16 KB
     static constexpr int B_BYTES = N * TC_BK * 2;
+    static constexpr int H_BYTES = OBJ ? 64 * TC_BK * 2 : 0;    // objective B (64 j x 64 r)
+    static constexpr int W_BYTES = OBJ ? TC_BM * TC_BK * 2 : 0; // objective A (128 i x 64 r)
     static constexpr int OFF_F32 = 0;
-    static constexpr int OFF_AHI = OFF_F32 + TC_F32_STAGES * F32_BYTES;
+    static constexpr int OFF_AHI = OFF_F32 + F32_STAGES * F32_BYTES;
     static constexpr int OFF_ALO = OFF_AHI + TC_BF_STAGES * A_BYTES;
     static constexpr int OFF_BHI = OFF_ALO + TC_BF_STAGES * A_BYTES;
     static constexpr int OFF_BLO = OFF_BHI + TC_BF_STAGES * B_BYTES;
-    static constexpr int OFF_BAR = (OFF_BLO + TC_BF_STAGES * B_BYTES + 1023) & ~1023;
-    // barriers: f32_full[3], f32_empty[3], b_full[2], a_full[2], bf_empty[2],
-    // acc1_full[2], acc1_empty[2], acc2_full[2], acc2_empty[2]
-    static constexpr int NBAR = 2 * TC_F32_STAGES + 3 * TC_BF_STAGES + 8;
+    static constexpr int OFF_HHI = OFF_BLO + TC_BF_STAGES * B_BYTES;
+    static constexpr int OFF_HLO = OFF_HHI + TC_BF_STAGES * H_BYTES;
+    static constexpr int OFF_WHI = OFF_HLO + TC_BF_STAGES * H_BYTES;
+    static constexpr int OFF_WLO = OFF_WHI + W_BYTES;
+    static constexpr int OFF_BAR = (OFF_WLO + W_BYTES + 1023) & ~1023;
+    // barriers: f32_full[S], f32_empty[S], b_full[2], a_full[2], bf_empty[2],
+    // acc1_full[2], acc1_empty[2], acc2_full[2], acc2_empty[2], obj_full[2],
+    // obj_empty[2], w_full
+    static constexpr int NBAR = 2 * F32_STAGES + 3 * TC_BF_STAGES + 13;
     static constexpr int OFF_TMEM = OFF_BAR + NBAR * 8;
     static constexpr int OFF_ABORT = OFF_TMEM + 4;
-    static constexpr int BYTES = OFF_ABORT + 4;
-    static constexpr int TMEM_COLS = 4 * N < 32 ? 32 : 4 * N;   // D1 x 2, D2 x 2
+    static constexpr int OFF_RED = (OFF_ABORT + 4 + 15) & ~15;    // 8 doubles
+    static constexpr int BYTES = OFF_RED + 16 * 8;
+    // TMEM: D1 x 2 (N), D2 x 2 (N), objective D3 x 2 (64).
+    static constexpr int COLS = 4 * N + (OBJ ? 128 : 0);
+    static constexpr int TMEM_COLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128
+                                   : COLS <= 256 ? 256 : 512;
     static_assert(OFF_AHI % 1024 == 0 && OFF_BHI % 1024 == 0 && OFF_BLO % 1024 == 0 &&
-                      A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0,
+                      OFF_HHI % 1024 == 0 && OFF_WHI % 1024 == 0 && A_BYTES % 1024 == 0 &&
+                      B_BYTES % 1024 == 0,
                   "128-byte-swizzled tiles need 1024-byte alignment");
+    static_assert(BYTES + 1024 <= 227 * 1024, "shared memory budget");
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -187,7 +214,7 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
                  : "memory");
 }
 
-// 32 consecutive FP32 columns of this warp's 32 TMEM lanes.
+// Consecutive FP32 columns of this warp's 32 TMEM lanes.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
 {
     uint32_t r[32];
@@ -264,20 +291,33 @@ __device__ __forceinline__ void split8(const float (&v)[8], uint4 &hi, uint4 &lo
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// Byte offset of (row r, 16-byte chunk c) in a 128-byte-swizzled K-major tile.
+// Byte offset of (row r, 16-byte chunk c) in a 128-byte-swizzled tile with
+// 128-byte rows (BF16 K-major operands, and each 32-float half of a staged
+// FP32 A tile when trans = 0).
 __device__ __forceinline__ uint32_t sw128_off(int r, int c)
 {
     return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
 }
 
+struct TcArgs {
+    int64_t P, Q;
+    int k, col0, kc;
+    float *out;
+    double *obj_partials;   // per-CTA sums of squared residuals (OBJ)
+    int *err;
+};
+
 // -------------------------------------------------------------------- kernel
-template <int N, int TRANS>
+template <int N, int TRANS, int OBJ>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     mm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
-                 const __grid_constant__ CUtensorMap tmBlo, int64_t P, int64_t Q, int k, int col0,
-                 int kc, float *__restrict__ out, int *__restrict__ err)
+                 const __grid_constant__ CUtensorMap tmBlo, const __grid_constant__ CUtensorMap tmWhi,
+                 const __grid_constant__ CUtensorMap tmWlo, const __grid_constant__ CUtensorMap tmHhi,
+                 const __grid_constant__ CUtensorMap tmHlo, const TcArgs args)
 {
-    using L = TcLayout<N>;
+    static_assert(!OBJ || TRANS == 0, "the objective rides on the A H^T pass");
+    using L = TcLayout<N, OBJ>;
+    constexpr int S = L::F32_STAGES;
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
@@ -285,23 +325,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     volatile int *abort = reinterpret_cast<volatile int *>(smem + L::OFF_ABORT);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::OFF_TMEM);
+    const int64_t P = args.P, Q = args.Q;
 
     const uint32_t bar0 = sbase + L::OFF_BAR;
     auto f32_full = [&](int i) { return bar0 + 8u * i; };
-    auto f32_empty = [&](int i) { return bar0 + 8u * (TC_F32_STAGES + i); };
-    auto b_full = [&](int i) { return bar0 + 8u * (2 * TC_F32_STAGES + i); };
-    auto a_full = [&](int i) { return bar0 + 8u * (2 * TC_F32_STAGES + TC_BF_STAGES + i); };
-    auto bf_empty = [&](int i) { return bar0 + 8u * (2 * TC_F32_STAGES + 2 * TC_BF_STAGES + i); };
-    const uint32_t accb = bar0 + 8u * (2 * TC_F32_STAGES + 3 * TC_BF_STAGES);
+    auto f32_empty = [&](int i) { return bar0 + 8u * (S + i); };
+    auto b_full = [&](int i) { return bar0 + 8u * (2 * S + i); };
+    auto a_full = [&](int i) { return bar0 + 8u * (2 * S + TC_BF_STAGES + i); };
+    auto bf_empty = [&](int i) { return bar0 + 8u * (2 * S + 2 * TC_BF_STAGES + i); };
+    const uint32_t accb = bar0 + 8u * (2 * S + 3 * TC_BF_STAGES);
     auto acc1_full = [&](int i) { return accb + 8u * i; };
     auto acc1_empty = [&](int i) { return accb + 8u * (2 + i); };
     auto acc2_full = [&](int i) { return accb + 8u * (4 + i); };
     auto acc2_empty = [&](int i) { return accb + 8u * (6 + i); };
+    auto obj_full = [&](int i) { return accb + 8u * (8 + i); };
+    auto obj_empty = [&](int i) { return accb + 8u * (10 + i); };
+    const uint32_t w_full = accb + 8u * 12;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < TC_F32_STAGES; ++i) {
+        for (int i = 0; i < S; ++i) {
             mbar_init(f32_full(i), 1);
-            mbar_init(f32_empty(i), 4);
+            mbar_init(f32_empty(i), 4 + (OBJ ? TC_DRAIN_WARPS : 0));
         }
         for (int i = 0; i < TC_BF_STAGES; ++i) {
             mbar_init(b_full(i), 1);
@@ -313,7 +357,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(acc1_empty(i), TC_DRAIN_WARPS);
             mbar_init(acc2_full(i), 1);
             mbar_init(acc2_empty(i), TC_DRAIN_WARPS);
+            mbar_init(obj_full(i), 1);
+            mbar_init(obj_empty(i), TC_DRAIN_WARPS);
         }
+        mbar_init(w_full, 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -335,32 +382,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
+            if (OBJ) {
+                mbar_arrive_expect_tx(w_full, 2 * L::W_BYTES);
+                tma_load_2d(sbase + L::OFF_WHI, &tmWhi, 0, (int)p0, w_full);
+                tma_load_2d(sbase + L::OFF_WLO, &tmWlo, 0, (int)p0, w_full);
+            }
             for (int kb = 0; kb < nkb; ++kb) {
-                const int fs = kb % TC_F32_STAGES, fr = kb / TC_F32_STAGES;
+                const int fs = kb % S, fr = kb / S;
                 const int bs = kb % TC_BF_STAGES, br = kb / TC_BF_STAGES;
                 if (!mbar_wait(f32_empty(fs), (fr & 1) ^ 1, abort))
                     break;
                 mbar_arrive_expect_tx(f32_full(fs), L::F32_BYTES);
                 const uint32_t dstA = sbase + L::OFF_F32 + fs * L::F32_BYTES;
-                if (TRANS == 0)
+                if (TRANS == 0) {
+                    // Two 128-byte-swizzled halves of 32 columns each.
                     tma_load_2d(dstA, &tmA, kb * TC_BK, (int)p0, f32_full(fs));
-                else
+                    tma_load_2d(dstA + L::F32_BYTES / 2, &tmA, kb * TC_BK + 32, (int)p0,
+                                f32_full(fs));
+                } else {
                     tma_load_2d(dstA, &tmA, (int)p0, kb * TC_BK, f32_full(fs));
+                }
                 if (!mbar_wait(bf_empty(bs), (br & 1) ^ 1, abort))
                     break;
-                mbar_arrive_expect_tx(b_full(bs), 2 * L::B_BYTES);
+                mbar_arrive_expect_tx(b_full(bs), 2 * L::B_BYTES + 2 * L::H_BYTES);
                 tma_load_2d(sbase + L::OFF_BHI + bs * L::B_BYTES, &tmBhi, kb * TC_BK, 0, b_full(bs));
                 tma_load_2d(sbase + L::OFF_BLO + bs * L::B_BYTES, &tmBlo, kb * TC_BK, 0, b_full(bs));
+                if (OBJ) {
+                    tma_load_2d(sbase + L::OFF_HHI + bs * L::H_BYTES, &tmHhi, 0, kb * TC_BK,
+                                b_full(bs));
+                    tma_load_2d(sbase + L::OFF_HLO + bs * L::H_BYTES, &tmHlo, 0, kb * TC_BK,
+                                b_full(bs));
+                }
             }
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         // TMEM columns: D1 buffers at [0, N) and [N, 2N) (hi*hi, one K-block
-        // each), D2 buffers at [2N, 3N) and [3N, 4N) (hi*lo + lo*hi, windows
-        // of TC_WIN2 K-blocks).
+        // each), D2 buffers at [2N, 4N) (cross terms, windows of TC_WIN2
+        // K-blocks), objective D3 buffers at [4N, 4N + 128) (64 columns each).
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_f32<N>();
-            for (int kb = 0; kb < nkb; ++kb) {
+            const uint32_t idesc_obj = idesc_bf16_f32<64>();
+            bool ok = !OBJ || mbar_wait(w_full, 0, abort);
+            for (int kb = 0; kb < nkb && ok; ++kb) {
                 const int bs = kb % TC_BF_STAGES, br = kb / TC_BF_STAGES;
                 const int b1 = kb & 1, u1 = kb >> 1;
                 const int w2 = kb / TC_WIN2, b2 = w2 & 1, u2 = w2 >> 1;
@@ -368,6 +432,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (!mbar_wait(acc1_empty(b1), (u1 & 1) ^ 1, abort))
                     break;
                 if (first2 && !mbar_wait(acc2_empty(b2), (u2 & 1) ^ 1, abort))
+                    break;
+                if (OBJ && !mbar_wait(obj_empty(b1), (u1 & 1) ^ 1, abort))
                     break;
                 if (!mbar_wait(a_full(bs), br & 1, abort) || !mbar_wait(b_full(bs), br & 1, abort))
                     break;
@@ -391,6 +457,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                              (first2 && kk == 0) ? 0u : 1u);
                     mma_bf16(d2, sw128_desc(alo + o), sw128_desc(bhi + o), idesc, 1u);
                 }
+                if (OBJ) {
+                    const uint32_t d3 = tmem + (uint32_t)(4 * N + b1 * 64);
+                    const uint32_t whi = sbase + L::OFF_WHI, wlo = sbase + L::OFF_WLO;
+                    const uint32_t hhi = sbase + L::OFF_HHI + bs * L::H_BYTES;
+                    const uint32_t hlo = sbase + L::OFF_HLO + bs * L::H_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                        const uint32_t o = kk * 32;
+                        mma_bf16(d3, sw128_desc(whi + o), sw128_desc(hhi + o), idesc_obj,
+                                 kk ? 1u : 0u);
+                        mma_bf16(d3, sw128_desc(whi + o), sw128_desc(hlo + o), idesc_obj, 1u);
+                        mma_bf16(d3, sw128_desc(wlo + o), sw128_desc(hhi + o), idesc_obj, 1u);
+                    }
+                    mma_commit(obj_full(b1));
+                }
                 mma_commit(bf_empty(bs));
                 if ((kb % TC_WIN2) == TC_WIN2 - 1 || kb == nkb - 1)
                     mma_commit(acc2_full(b2));
@@ -401,7 +482,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int ct = threadIdx.x - 64;        // 0..127
         const int cw = ct >> 5;                 // converter warp 0..3
         for (int kb = 0; kb < nkb; ++kb) {
-            const int fs = kb % TC_F32_STAGES, fr = kb / TC_F32_STAGES;
+            const int fs = kb % S, fr = kb / S;
             const int bs = kb % TC_BF_STAGES, br = kb / TC_BF_STAGES;
             if (!mbar_wait(f32_full(fs), fr & 1, abort) ||
                 !mbar_wait(bf_empty(bs), (br & 1) ^ 1, abort))
@@ -410,13 +491,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             unsigned char *ahi = smem + L::OFF_AHI + bs * L::A_BYTES;
             unsigned char *alo = smem + L::OFF_ALO + bs * L::A_BYTES;
             if (TRANS == 0) {
-                // src: 128 rows (p) x 64 floats (q), 256 bytes per row.
+                // src: two swizzled halves of 128 rows (p) x 32 floats (q).
 #pragma unroll 2
                 for (int it = 0; it < TC_BM / 16; ++it) {
                     const int r = it * 16 + cw * 4 + (lane >> 3);
-                    const int c = lane & 7;
-                    const float4 a = *reinterpret_cast<const float4 *>(src + r * 256 + c * 32);
-                    const float4 b = *reinterpret_cast<const float4 *>(src + r * 256 + c * 32 + 16);
+                    const int c = lane & 7;             // 8-float chunk of the row
+                    const unsigned char *hsrc = src + (c >> 2) * (L::F32_BYTES / 2);
+                    const int q16 = 2 * (c & 3);        // first 16-byte chunk in the half
+                    const float4 a = *reinterpret_cast<const float4 *>(hsrc + sw128_off(r, q16));
+                    const float4 b =
+                        *reinterpret_cast<const float4 *>(hsrc + sw128_off(r, q16 + 1));
                     const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
                     uint4 hi, lo;
                     split8(v, hi, lo);
@@ -447,16 +531,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else {
         // ------------------------------------------------ drain (warps 6-13)
-        constexpr int NH = N / 2;               // columns owned by this warp
+        constexpr int NH = N / 2;               // product columns owned by this warp
         const int dw = warp - 6;
         const int quarter = warp & 3;           // TMEM lane quarter of this warp
-        const int cbase = (dw >> 2) * NH;       // first owned column
+        const int half = dw >> 2;               // which half of the columns
+        const int cbase = half * NH;
         float sum[NH], cmp[NH];
 #pragma unroll
         for (int c = 0; c < NH; ++c) {
             sum[c] = 0.0f;
             cmp[c] = 0.0f;
         }
+        double fsum = 0.0;
         auto add_tile = [&](uint32_t ta) {
             float v[NH];
             tmem_ld<NH>(ta, v);
@@ -468,7 +554,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 sum[i] = t;
             }
         };
-        const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cbase;
+        const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16);
+        const int row = quarter * 32 + lane;    // row of the tile owned by this thread
         bool ok = true;
         for (int kb = 0; kb < nkb && ok; ++kb) {
             const int b1 = kb & 1, u1 = kb >> 1;
@@ -477,11 +564,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 break;
             }
             tc_fence_after();
-            add_tile(tq + (uint32_t)(b1 * N));
+            add_tile(tq + (uint32_t)(b1 * N + cbase));
             tc_fence_before();
             __syncwarp();
             if (lane == 0)
                 mbar_arrive(acc1_empty(b1));
+            if (OBJ) {
+                // Squared residuals of this thread's row over 32 columns.
+                const int fs = kb % S, fr = kb / S;
+                if (!mbar_wait(obj_full(b1), u1 & 1, abort) ||
+                    !mbar_wait(f32_full(fs), fr & 1, abort)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                float wh[32];
+                tmem_ld32(tq + (uint32_t)(4 * N + b1 * 64 + half * 32), wh);
+                const unsigned char *hsrc = smem + L::OFF_F32 + fs * L::F32_BYTES +
+                                            half * (L::F32_BYTES / 2);
+                float sq = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float4 a = *reinterpret_cast<const float4 *>(hsrc + sw128_off(row, c));
+                    const float e0 = a.x - wh[4 * c], e1 = a.y - wh[4 * c + 1];
+                    const float e2 = a.z - wh[4 * c + 2], e3 = a.w - wh[4 * c + 3];
+                    sq = fmaf(e0, e0, sq);
+                    sq = fmaf(e1, e1, sq);
+                    sq = fmaf(e2, e2, sq);
+                    sq = fmaf(e3, e3, sq);
+                }
+                fsum += (double)sq;
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(obj_empty(b1));
+                    mbar_arrive(f32_empty(fs));
+                }
+            }
             if ((kb % TC_WIN2) == TC_WIN2 - 1 || kb == nkb - 1) {
                 const int w2 = kb / TC_WIN2, b2 = w2 & 1, u2 = w2 >> 1;
                 if (!mbar_wait(acc2_full(b2), u2 & 1, abort)) {
@@ -489,7 +608,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     break;
                 }
                 tc_fence_after();
-                add_tile(tq + (uint32_t)((2 + b2) * N));
+                add_tile(tq + (uint32_t)((2 + b2) * N + cbase));
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0)
@@ -497,21 +616,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         }
         if (ok) {
-            const int64_t p = p0 + quarter * 32 + lane;
+            const int64_t p = p0 + row;
             if (p < P) {
-                float *o = out + p * k + col0 + cbase;
+                float *o = args.out + p * args.k + args.col0 + cbase;
 #pragma unroll
                 for (int c = 0; c < NH; ++c)
-                    if (cbase + c < kc)
+                    if (cbase + c < args.kc)
                         o[c] = sum[c] - cmp[c];
             }
+        }
+        if (OBJ) {
+            // Warp sums, then one value per warp into shared memory.
+            for (int o = 16; o > 0; o >>= 1)
+                fsum += __shfl_xor_sync(FULL, fsum, o);
+            if (lane == 0)
+                reinterpret_cast<double *>(smem + L::OFF_RED)[dw] = fsum;
         }
     }
 
     tc_fence_before();
     __syncthreads();
-    if (threadIdx.x == 0 && *abort)
-        atomicExch(err, 1);
+    if (threadIdx.x == 0) {
+        if (*abort)
+            atomicExch(args.err, 1);
+        if (OBJ) {
+            const double *red = reinterpret_cast<const double *>(smem + L::OFF_RED);
+            double s = 0.0;
+            for (int w = 0; w < TC_DRAIN_WARPS; ++w)
+                s += red[w];
+            args.obj_partials[blockIdx.x] = s;
+        }
+    }
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -544,6 +679,43 @@ __global__ void mm_tc_split_kernel(const float *__restrict__ F, int64_t Q, int k
             hi[(int64_t)r * Qp + q] = h;
             lo[(int64_t)r * Qp + q] = __float2bfloat16_rn(v - __bfloat162float(h));
         }
+    }
+}
+
+// X (rows x k, float32 row-major, k <= 64) -> BF16 hi / lo rows of 64
+// (zero-padded columns and rows up to rows_p): the objective's K-major
+// operands W [i][r] and H^T [j][r].
+__global__ void mm_tc_split_rows_kernel(const float *__restrict__ X, int64_t rows, int k,
+                                        int64_t rows_p, __nv_bfloat16 *__restrict__ hi,
+                                        __nv_bfloat16 *__restrict__ lo)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= rows_p * 64)
+        return;
+    const int64_t r = e >> 6;
+    const int c = (int)(e & 63);
+    const float v = (r < rows && c < k) ? X[r * k + c] : 0.0f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[e] = h;
+    lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+__global__ void obj_sum_kernel(const double *__restrict__ parts, int n, double *__restrict__ f)
+{
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        s += parts[i];
+    for (int o = 16; o > 0; o >>= 1)
+        s += __shfl_down_sync(FULL, s, o);
+    if ((threadIdx.x & 31) == 0)
+        red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            t += red[w];
+        *f = t;
     }
 }
 
@@ -581,65 +753,139 @@ bool make_map_2d(CUtensorMap *map, CUtensorMapDataType dt, const void *base, uin
 
 constexpr size_t TC_ERR_BYTES = 256;
 
-template <int N, int TRANS>
-nmf_status launch_tc(const CUtensorMap &tA, const CUtensorMap &tBh, const CUtensorMap &tBl,
-                     int64_t P, int64_t Q, int k, int col0, int kc, float *out, int *err,
-                     cudaStream_t s)
+template <int N, int TRANS, int OBJ>
+nmf_status launch_tc(const CUtensorMap (&maps)[7], const TcArgs &a, cudaStream_t s)
 {
-    using L = TcLayout<N>;
+    using L = TcLayout<N, OBJ>;
     const int smem = L::BYTES + 1024;
     static int configured = 0;
     if (!configured) {
-        NMF_CUDA(cudaFuncSetAttribute(mm_tc_kernel<N, TRANS>,
+        NMF_CUDA(cudaFuncSetAttribute(mm_tc_kernel<N, TRANS, OBJ>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         configured = 1;
     }
-    const unsigned grid = (unsigned)cdiv(P, TC_BM);
-    mm_tc_kernel<N, TRANS><<<grid, TC_THREADS, smem, s>>>(tA, tBh, tBl, P, Q, k, col0, kc, out,
-                                                          err);
+    const unsigned grid = (unsigned)cdiv(a.P, TC_BM);
+    mm_tc_kernel<N, TRANS, OBJ><<<grid, TC_THREADS, smem, s>>>(maps[0], maps[1], maps[2], maps[3],
+                                                               maps[4], maps[5], maps[6], a);
     NMF_LAUNCHED("mm_tc_kernel");
     return NMF_OK;
+}
+
+template <int TRANS, int OBJ>
+nmf_status launch_tc_n(int N, const CUtensorMap (&maps)[7], const TcArgs &a, cudaStream_t s)
+{
+    if (N == 16)
+        return launch_tc<16, TRANS, OBJ>(maps, a, s);
+    if (N == 32)
+        return launch_tc<32, TRANS, OBJ>(maps, a, s);
+    return launch_tc<64, TRANS, OBJ>(maps, a, s);
+}
+
+// Workspace: [err | product F split (2 x N x Qp BF16) | objective: W split
+// (2 x Pp x 64) | H^T split (2 x Qp x 64) | per-CTA partials].
+struct TcWork {
+    size_t f_off, w_off, h_off, part_off, total;
+};
+
+TcWork tc_work(int64_t m, int64_t n, int k, int trans, bool obj)
+{
+    const int64_t P = trans ? n : m;
+    const int64_t Q = trans ? m : n;
+    const int64_t Qp = cdiv(Q > 0 ? Q : 1, TC_BK) * TC_BK;
+    const int64_t Pp = cdiv(P > 0 ? P : 1, TC_BM) * TC_BM;
+    const int N = k <= 16 ? 16 : k <= 32 ? 32 : 64;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    TcWork w;
+    w.f_off = TC_ERR_BYTES;
+    size_t off = w.f_off + al(2 * sizeof(__nv_bfloat16) * (size_t)N * (size_t)Qp);
+    w.w_off = off;
+    if (obj)
+        off += al(2 * sizeof(__nv_bfloat16) * (size_t)Pp * 64);
+    w.h_off = off;
+    if (obj)
+        off += al(2 * sizeof(__nv_bfloat16) * (size_t)Qp * 64);
+    w.part_off = off;
+    if (obj)
+        off += al(sizeof(double) * (size_t)(Pp / TC_BM));
+    w.total = off;
+    return w;
 }
 
 }  // namespace
 
 size_t mm_tc_work_bytes(int64_t m, int64_t n, int k, int trans)
 {
-    const int64_t Q = trans ? m : n;
-    const int64_t Qp = cdiv(Q > 0 ? Q : 1, TC_BK) * TC_BK;
-    const int N = k <= 16 ? 16 : k <= 32 ? 32 : 64;
-    return TC_ERR_BYTES + 2 * sizeof(__nv_bfloat16) * (size_t)N * (size_t)Qp;
+    return tc_work(m, n, k, trans, trans == 0 && k <= 64).total;
 }
 
-nmf_status launch_mm_tc(const float *A, int64_t m, int64_t n, int64_t lda, const float *F,
-                        int k, int trans, float *out, void *work, size_t work_bytes,
-                        cudaStream_t s)
+// Products, and with W / Ht / f_dev given (trans = 0, k <= 64) the fused
+// objective f(W, H) written to *f_dev.
+nmf_status launch_mm_tc_obj(const float *A, int64_t m, int64_t n, int64_t lda, const float *F,
+                            int k, int trans, float *out, const float *W, const float *Ht,
+                            double *f_dev, void *work, size_t work_bytes, cudaStream_t s)
 {
     const int64_t P = trans ? n : m;
     const int64_t Q = trans ? m : n;
-    if (P == 0)
+    const bool obj = f_dev != nullptr;
+    if (obj && (trans != 0 || k > 64 || !W || !Ht))
+        return NMF_ERR_INVALID_ARG;
+    if (P == 0 || Q == 0) {
+        if (P > 0 && cudaMemsetAsync(out, 0, sizeof(float) * (size_t)P * k, s) != cudaSuccess)
+            return NMF_ERR_CUDA;
+        if (obj && cudaMemsetAsync(f_dev, 0, sizeof(double), s) != cudaSuccess)
+            return NMF_ERR_CUDA;
         return NMF_OK;
-    if (Q == 0)
-        return cudaMemsetAsync(out, 0, sizeof(float) * (size_t)P * k, s) == cudaSuccess
-                   ? NMF_OK
-                   : NMF_ERR_CUDA;
+    }
     // TMA needs a 16-byte-aligned base and row pitch; coordinates must fit int32.
     if ((reinterpret_cast<uintptr_t>(A) & 15) || (lda % 4) || P > INT32_MAX || Q > INT32_MAX)
         return NMF_ERR_INVALID_ARG;
-    if (!work || work_bytes < mm_tc_work_bytes(m, n, k, trans))
+    const TcWork wl = tc_work(m, n, k, trans, obj);
+    if (!work || work_bytes < wl.total)
         return NMF_ERR_INVALID_ARG;
     const int64_t Qp = cdiv(Q, TC_BK) * TC_BK;
-    int *err = static_cast<int *>(work);
+    const int64_t Pp = cdiv(P, TC_BM) * TC_BM;
+    char *wb = static_cast<char *>(work);
+    int *err = reinterpret_cast<int *>(wb);
     NMF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    __nv_bfloat16 *bhi = reinterpret_cast<__nv_bfloat16 *>(static_cast<char *>(work) + TC_ERR_BYTES);
-    CUtensorMap tA;
+    __nv_bfloat16 *bhi = reinterpret_cast<__nv_bfloat16 *>(wb + wl.f_off);
+    CUtensorMap maps[7];
     bool ok = trans == 0
-                  ? make_map_2d(&tA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)Q, (uint64_t)P,
-                                (uint64_t)lda * 4, TC_BK, TC_BM, CU_TENSOR_MAP_SWIZZLE_NONE)
-                  : make_map_2d(&tA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)P, (uint64_t)Q,
-                                (uint64_t)lda * 4, TC_BM, TC_BK, CU_TENSOR_MAP_SWIZZLE_NONE);
+                  ? make_map_2d(&maps[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)Q,
+                                (uint64_t)P, (uint64_t)lda * 4, 32, TC_BM,
+                                CU_TENSOR_MAP_SWIZZLE_128B)
+                  : make_map_2d(&maps[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)P,
+                                (uint64_t)Q, (uint64_t)lda * 4, TC_BM, TC_BK,
+                                CU_TENSOR_MAP_SWIZZLE_NONE);
     if (!ok)
         return NMF_ERR_CUDA;
+    TcArgs a;
+    a.P = P;
+    a.Q = Q;
+    a.k = k;
+    a.out = out;
+    a.err = err;
+    a.obj_partials = reinterpret_cast<double *>(wb + wl.part_off);
+    if (obj) {
+        __nv_bfloat16 *whi = reinterpret_cast<__nv_bfloat16 *>(wb + wl.w_off);
+        __nv_bfloat16 *wlo = whi + (size_t)Pp * 64;
+        __nv_bfloat16 *hhi = reinterpret_cast<__nv_bfloat16 *>(wb + wl.h_off);
+        __nv_bfloat16 *hlo = hhi + (size_t)Qp * 64;
+        mm_tc_split_rows_kernel<<<(unsigned)cdiv(Pp * 64, 256), 256, 0, s>>>(W, P, k, Pp, whi, wlo);
+        NMF_LAUNCHED("mm_tc_split_rows_kernel");
+        mm_tc_split_rows_kernel<<<(unsigned)cdiv(Qp * 64, 256), 256, 0, s>>>(Ht, Q, k, Qp, hhi, hlo);
+        NMF_LAUNCHED("mm_tc_split_rows_kernel");
+        if (!make_map_2d(&maps[3], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, whi, 64, (uint64_t)Pp, 128,
+                         64, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
+            !make_map_2d(&maps[4], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, wlo, 64, (uint64_t)Pp, 128,
+                         64, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
+            !make_map_2d(&maps[5], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, hhi, 64, (uint64_t)Qp, 128,
+                         64, 64, CU_TENSOR_MAP_SWIZZLE_128B) ||
+            !make_map_2d(&maps[6], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, hlo, 64, (uint64_t)Qp, 128,
+                         64, 64, CU_TENSOR_MAP_SWIZZLE_128B))
+            return NMF_ERR_CUDA;
+    } else {
+        maps[3] = maps[4] = maps[5] = maps[6] = maps[0];   // unused
+    }
     for (int col0 = 0; col0 < k; col0 += 64) {
         const int kc = k - col0 < 64 ? k - col0 : 64;
         const int N = kc <= 16 ? 16 : kc <= 32 ? 32 : 64;
@@ -647,25 +893,36 @@ nmf_status launch_mm_tc(const float *A, int64_t m, int64_t n, int64_t lda, const
         dim3 sg((unsigned)cdiv(Qp, 32), (unsigned)cdiv(N, 32));
         mm_tc_split_kernel<<<sg, dim3(32, 8), 0, s>>>(F, Q, k, col0, kc, N, Qp, bhi, blo);
         NMF_LAUNCHED("mm_tc_split_kernel");
-        CUtensorMap tBh, tBl;
-        if (!make_map_2d(&tBh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, bhi, (uint64_t)Qp, (uint64_t)N,
+        if (!make_map_2d(&maps[1], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, bhi, (uint64_t)Qp, (uint64_t)N,
                          (uint64_t)Qp * 2, TC_BK, (uint32_t)N, CU_TENSOR_MAP_SWIZZLE_128B) ||
-            !make_map_2d(&tBl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, blo, (uint64_t)Qp, (uint64_t)N,
+            !make_map_2d(&maps[2], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, blo, (uint64_t)Qp, (uint64_t)N,
                          (uint64_t)Qp * 2, TC_BK, (uint32_t)N, CU_TENSOR_MAP_SWIZZLE_128B))
             return NMF_ERR_CUDA;
+        a.col0 = col0;
+        a.kc = kc;
+        const bool fuse = obj && col0 == 0;
         nmf_status st;
-        if (N == 16)
-            st = trans ? launch_tc<16, 1>(tA, tBh, tBl, P, Q, k, col0, kc, out, err, s)
-                       : launch_tc<16, 0>(tA, tBh, tBl, P, Q, k, col0, kc, out, err, s);
-        else if (N == 32)
-            st = trans ? launch_tc<32, 1>(tA, tBh, tBl, P, Q, k, col0, kc, out, err, s)
-                       : launch_tc<32, 0>(tA, tBh, tBl, P, Q, k, col0, kc, out, err, s);
+        if (trans)
+            st = launch_tc_n<1, 0>(N, maps, a, s);
+        else if (fuse)
+            st = launch_tc_n<0, 1>(N, maps, a, s);
         else
-            st = trans ? launch_tc<64, 1>(tA, tBh, tBl, P, Q, k, col0, kc, out, err, s)
-                       : launch_tc<64, 0>(tA, tBh, tBl, P, Q, k, col0, kc, out, err, s);
+            st = launch_tc_n<0, 0>(N, maps, a, s);
         NMF_TRY(st);
+        if (fuse) {
+            obj_sum_kernel<<<1, 256, 0, s>>>(a.obj_partials, (int)(Pp / TC_BM), f_dev);
+            NMF_LAUNCHED("obj_sum_kernel");
+        }
     }
     return NMF_OK;
+}
+
+nmf_status launch_mm_tc(const float *A, int64_t m, int64_t n, int64_t lda, const float *F,
+                        int k, int trans, float *out, void *work, size_t work_bytes,
+                        cudaStream_t s)
+{
+    return launch_mm_tc_obj(A, m, n, lda, F, k, trans, out, nullptr, nullptr, nullptr, work,
+                            work_bytes, s);
 }
 
 }  // namespace nmf

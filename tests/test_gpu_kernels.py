@@ -304,14 +304,28 @@ def test_bpp_empty_batch(nmf):
 
 
 # ----------------------------------------------------------------------------- objective
-@pytest.mark.parametrize("shape,k", [((37, 23), 3), ((300, 1000), 10), ((1000, 300), 50),
-                                     ((129, 65), 100)])
-def test_objective_dense(nmf, shape, k):
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("shape,k", [((37, 24), 3), ((300, 1000), 10), ((1000, 300), 50),
+                                     ((129, 68), 100), ((4100, 2048), 64)])
+def test_objective_dense(nmf, shape, k, precision):
     m, n = shape
     A = synth.dense_planted(m, n, k, 0.05, seed=m + n)
     rng = np.random.default_rng(3)
     W = rng.uniform(0, 1, (m, k)).astype(np.float32)
     Ht = rng.uniform(0, 1, (n, k)).astype(np.float32)
-    f = nmf.nmf_objective_dense(dev(A), dev(W), dev(Ht))
+    f = nmf.nmf_objective_dense(dev(A), dev(W), dev(Ht), precision=precision)
     ref = oracle.objective_dense(A, W, Ht)
     assert abs(f - ref) <= 1e-5 * ref
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_objective_dense_good_fit(nmf, precision):
+    # W, H near the planted factors: the residual is ~1e-3 of A, so the sum is
+    # sensitive to any bias in W H.
+    m, n, k = 2000, 1024, 16
+    A, W0, H0 = synth.dense_planted(m, n, k, 0.05, seed=4, return_factors=True)
+    W = W0.astype(np.float32)
+    Ht = np.ascontiguousarray(H0.T).astype(np.float32)
+    f = nmf.nmf_objective_dense(dev(A), dev(W), dev(Ht), precision=precision)
+    ref = oracle.objective_dense(A, W, Ht)
+    assert abs(f - ref) <= 1e-5 * ref, (f, ref)
