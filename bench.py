@@ -314,7 +314,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "bf16x3"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "bf16x3"], default="bf16x3")
     ap.add_argument("--start", choices=["cold", "warm"], default="warm")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dense-large")
     ap.add_argument("--max-rounds", type=int, default=100)

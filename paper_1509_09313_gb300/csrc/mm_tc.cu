@@ -35,10 +35,12 @@
 //
 // Fused objective (trans = 0, k <= 64): with W and H^T given, every K-block
 // also forms the 128 x 64 tile of W H (W tile resident in shared memory,
-// K = k padded to 64, three split products) in a third ping-pong TMEM pair;
-// the drain warps subtract it from the staged FP32 A tile and add the squared
-// residuals in FP64. The A H^T pass of an ANLS iteration thereby yields
-// f(W, H) of the previous iterate without reading A again. A relative bias b
+// K = k padded to 64, three split products) in a third ping-pong TMEM pair,
+// issued one K-block ahead (it needs no A). The split warps, each owning 32
+// rows of the tile (their TMEM lane quarter), subtract it from the staged A
+// values they have just split and add the squared residuals in FP64. The
+// A H^T pass of an ANLS iteration thereby yields f(W, H) of the previous
+// iterate without reading A again. A relative bias b
 // of W H shifts f by about S b with S = 2 mean(r) mean(WH) / mean(r^2)
 // (|S| <= 4 on the dense workloads), far inside the 1e-5 tolerance.
 //
@@ -302,7 +304,8 @@ __device__ __forceinline__ uint32_t sw128_off(int r, int c)
 struct TcArgs {
     int64_t P, Q;
     int k, col0, kc;
-    float *out;
+    int kb_per_split;       // K-blocks per CTA along the contraction (grid.y splits)
+    float *out;             // grid.y == 1: the output; else partials [split][P][k]
     double *obj_partials;   // per-CTA sums of squared residuals (OBJ)
     int *err;
 };
@@ -345,7 +348,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int i = 0; i < S; ++i) {
             mbar_init(f32_full(i), 1);
-            mbar_init(f32_empty(i), 4 + (OBJ ? TC_DRAIN_WARPS : 0));
+            mbar_init(f32_empty(i), 4);
         }
         for (int i = 0; i < TC_BF_STAGES; ++i) {
             mbar_init(b_full(i), 1);
@@ -358,7 +361,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(acc2_full(i), 1);
             mbar_init(acc2_empty(i), TC_DRAIN_WARPS);
             mbar_init(obj_full(i), 1);
-            mbar_init(obj_empty(i), TC_DRAIN_WARPS);
+            mbar_init(obj_empty(i), 4);
         }
         mbar_init(w_full, 1);
         *abort = 0;
@@ -377,7 +380,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t tmem = *tmem_slot;
 
     const int64_t p0 = (int64_t)blockIdx.x * TC_BM;
-    const int nkb = (int)((Q + TC_BK - 1) / TC_BK);
+    const int nkb_all = (int)((Q + TC_BK - 1) / TC_BK);
+    const int kb0 = blockIdx.y * args.kb_per_split;   // first K-block of this CTA
+    const int nkb = min(args.kb_per_split, nkb_all - kb0);
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
@@ -396,21 +401,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const uint32_t dstA = sbase + L::OFF_F32 + fs * L::F32_BYTES;
                 if (TRANS == 0) {
                     // Two 128-byte-swizzled halves of 32 columns each.
-                    tma_load_2d(dstA, &tmA, kb * TC_BK, (int)p0, f32_full(fs));
-                    tma_load_2d(dstA + L::F32_BYTES / 2, &tmA, kb * TC_BK + 32, (int)p0,
+                    tma_load_2d(dstA, &tmA, (kb0 + kb) * TC_BK, (int)p0, f32_full(fs));
+                    tma_load_2d(dstA + L::F32_BYTES / 2, &tmA, (kb0 + kb) * TC_BK + 32, (int)p0,
                                 f32_full(fs));
                 } else {
-                    tma_load_2d(dstA, &tmA, (int)p0, kb * TC_BK, f32_full(fs));
+                    tma_load_2d(dstA, &tmA, (int)p0, (kb0 + kb) * TC_BK, f32_full(fs));
                 }
                 if (!mbar_wait(bf_empty(bs), (br & 1) ^ 1, abort))
                     break;
                 mbar_arrive_expect_tx(b_full(bs), 2 * L::B_BYTES + 2 * L::H_BYTES);
-                tma_load_2d(sbase + L::OFF_BHI + bs * L::B_BYTES, &tmBhi, kb * TC_BK, 0, b_full(bs));
-                tma_load_2d(sbase + L::OFF_BLO + bs * L::B_BYTES, &tmBlo, kb * TC_BK, 0, b_full(bs));
+                tma_load_2d(sbase + L::OFF_BHI + bs * L::B_BYTES, &tmBhi, (kb0 + kb) * TC_BK, 0,
+                            b_full(bs));
+                tma_load_2d(sbase + L::OFF_BLO + bs * L::B_BYTES, &tmBlo, (kb0 + kb) * TC_BK, 0,
+                            b_full(bs));
                 if (OBJ) {
-                    tma_load_2d(sbase + L::OFF_HHI + bs * L::H_BYTES, &tmHhi, 0, kb * TC_BK,
+                    tma_load_2d(sbase + L::OFF_HHI + bs * L::H_BYTES, &tmHhi, 0, (kb0 + kb) * TC_BK,
                                 b_full(bs));
-                    tma_load_2d(sbase + L::OFF_HLO + bs * L::H_BYTES, &tmHlo, 0, kb * TC_BK,
+                    tma_load_2d(sbase + L::OFF_HLO + bs * L::H_BYTES, &tmHlo, 0, (kb0 + kb) * TC_BK,
                                 b_full(bs));
                 }
             }
@@ -423,7 +430,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_f32<N>();
             const uint32_t idesc_obj = idesc_bf16_f32<64>();
-            bool ok = !OBJ || mbar_wait(w_full, 0, abort);
+            // Objective tile W H of K-block j (needs only W and the H^T tile).
+            auto issue_obj = [&](int j) -> bool {
+                const int bs = j % TC_BF_STAGES, br = j / TC_BF_STAGES;
+                const int b = j & 1, u = j >> 1;
+                if (!mbar_wait(obj_empty(b), (u & 1) ^ 1, abort) ||
+                    !mbar_wait(b_full(bs), br & 1, abort))
+                    return false;
+                tc_fence_after();
+                const uint32_t d3 = tmem + (uint32_t)(4 * N + b * 64);
+                const uint32_t whi = sbase + L::OFF_WHI, wlo = sbase + L::OFF_WLO;
+                const uint32_t hhi = sbase + L::OFF_HHI + bs * L::H_BYTES;
+                const uint32_t hlo = sbase + L::OFF_HLO + bs * L::H_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                    const uint32_t o = kk * 32;
+                    mma_bf16(d3, sw128_desc(whi + o), sw128_desc(hhi + o), idesc_obj, kk ? 1u : 0u);
+                    mma_bf16(d3, sw128_desc(whi + o), sw128_desc(hlo + o), idesc_obj, 1u);
+                    mma_bf16(d3, sw128_desc(wlo + o), sw128_desc(hhi + o), idesc_obj, 1u);
+                }
+                mma_commit(obj_full(b));
+                return true;
+            };
+            bool ok = true;
+            if (OBJ)
+                ok = mbar_wait(w_full, 0, abort) && issue_obj(0);
             for (int kb = 0; kb < nkb && ok; ++kb) {
                 const int bs = kb % TC_BF_STAGES, br = kb / TC_BF_STAGES;
                 const int b1 = kb & 1, u1 = kb >> 1;
@@ -432,8 +463,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (!mbar_wait(acc1_empty(b1), (u1 & 1) ^ 1, abort))
                     break;
                 if (first2 && !mbar_wait(acc2_empty(b2), (u2 & 1) ^ 1, abort))
-                    break;
-                if (OBJ && !mbar_wait(obj_empty(b1), (u1 & 1) ^ 1, abort))
                     break;
                 if (!mbar_wait(a_full(bs), br & 1, abort) || !mbar_wait(b_full(bs), br & 1, abort))
                     break;
@@ -457,30 +486,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                              (first2 && kk == 0) ? 0u : 1u);
                     mma_bf16(d2, sw128_desc(alo + o), sw128_desc(bhi + o), idesc, 1u);
                 }
-                if (OBJ) {
-                    const uint32_t d3 = tmem + (uint32_t)(4 * N + b1 * 64);
-                    const uint32_t whi = sbase + L::OFF_WHI, wlo = sbase + L::OFF_WLO;
-                    const uint32_t hhi = sbase + L::OFF_HHI + bs * L::H_BYTES;
-                    const uint32_t hlo = sbase + L::OFF_HLO + bs * L::H_BYTES;
-#pragma unroll
-                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                        const uint32_t o = kk * 32;
-                        mma_bf16(d3, sw128_desc(whi + o), sw128_desc(hhi + o), idesc_obj,
-                                 kk ? 1u : 0u);
-                        mma_bf16(d3, sw128_desc(whi + o), sw128_desc(hlo + o), idesc_obj, 1u);
-                        mma_bf16(d3, sw128_desc(wlo + o), sw128_desc(hhi + o), idesc_obj, 1u);
-                    }
-                    mma_commit(obj_full(b1));
-                }
                 mma_commit(bf_empty(bs));
                 if ((kb % TC_WIN2) == TC_WIN2 - 1 || kb == nkb - 1)
                     mma_commit(acc2_full(b2));
+                if (OBJ && kb + 1 < nkb && !issue_obj(kb + 1))
+                    break;
             }
         }
     } else if (warp < 6) {
         // ---------------------------------------------------- split (warps 2-5)
         const int ct = threadIdx.x - 64;        // 0..127
-        const int cw = ct >> 5;                 // converter warp 0..3
+        const int quarter = warp & 3;           // TMEM lane quarter of this warp
+        const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16);
+        double fsum = 0.0;
         for (int kb = 0; kb < nkb; ++kb) {
             const int fs = kb % S, fr = kb / S;
             const int bs = kb % TC_BF_STAGES, br = kb / TC_BF_STAGES;
@@ -491,21 +509,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             unsigned char *ahi = smem + L::OFF_AHI + bs * L::A_BYTES;
             unsigned char *alo = smem + L::OFF_ALO + bs * L::A_BYTES;
             if (TRANS == 0) {
-                // src: two swizzled halves of 128 rows (p) x 32 floats (q).
-#pragma unroll 2
-                for (int it = 0; it < TC_BM / 16; ++it) {
-                    const int r = it * 16 + cw * 4 + (lane >> 3);
-                    const int c = lane & 7;             // 8-float chunk of the row
-                    const unsigned char *hsrc = src + (c >> 2) * (L::F32_BYTES / 2);
-                    const int q16 = 2 * (c & 3);        // first 16-byte chunk in the half
-                    const float4 a = *reinterpret_cast<const float4 *>(hsrc + sw128_off(r, q16));
-                    const float4 b =
-                        *reinterpret_cast<const float4 *>(hsrc + sw128_off(r, q16 + 1));
-                    const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-                    uint4 hi, lo;
-                    split8(v, hi, lo);
-                    *reinterpret_cast<uint4 *>(ahi + sw128_off(r, c)) = hi;
-                    *reinterpret_cast<uint4 *>(alo + sw128_off(r, c)) = lo;
+                // src: two swizzled halves of 128 rows (p) x 32 floats (q). Each
+                // converter warp owns the 32 rows of its TMEM lane quarter
+                // (lane = row), so it can also read the objective tile W H.
+                const int r = quarter * 32 + lane;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const unsigned char *hsrc = src + h * (L::F32_BYTES / 2);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float4 a =
+                            *reinterpret_cast<const float4 *>(hsrc + sw128_off(r, 2 * c));
+                        const float4 b =
+                            *reinterpret_cast<const float4 *>(hsrc + sw128_off(r, 2 * c + 1));
+                        const float w8[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+                        uint4 hi, lo;
+                        split8(w8, hi, lo);
+                        *reinterpret_cast<uint4 *>(ahi + sw128_off(r, h * 4 + c)) = hi;
+                        *reinterpret_cast<uint4 *>(alo + sw128_off(r, h * 4 + c)) = lo;
+                    }
                 }
             } else {
                 // src: 64 rows (q) x 128 floats (p), 512 bytes per row; row p = ct.
@@ -524,10 +546,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             fence_proxy_async();
             __syncwarp();
-            if (lane == 0) {
+            if (lane == 0)
                 mbar_arrive(a_full(bs));
-                mbar_arrive(f32_empty(fs));
+            if (OBJ && TRANS == 0) {
+                // Squared residuals of this warp's 32 rows against the W H tile
+                // (issued a K-block ahead, so normally complete by now).
+                const int r = quarter * 32 + lane;
+                const int b1 = kb & 1, u1 = kb >> 1;
+                if (!mbar_wait(obj_full(b1), u1 & 1, abort))
+                    break;
+                tc_fence_after();
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const unsigned char *hsrc = src + h * (L::F32_BYTES / 2);
+                    float wh[32];
+                    tmem_ld32(tq + (uint32_t)(4 * N + b1 * 64 + h * 32), wh);
+                    float sq = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const float4 a = *reinterpret_cast<const float4 *>(hsrc + sw128_off(r, c));
+                        const float e0 = a.x - wh[4 * c], e1 = a.y - wh[4 * c + 1];
+                        const float e2 = a.z - wh[4 * c + 2], e3 = a.w - wh[4 * c + 3];
+                        sq = fmaf(e0, e0, sq);
+                        sq = fmaf(e1, e1, sq);
+                        sq = fmaf(e2, e2, sq);
+                        sq = fmaf(e3, e3, sq);
+                    }
+                    fsum += (double)sq;
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(obj_empty(b1));
             }
+            if (lane == 0)
+                mbar_arrive(f32_empty(fs));
+        }
+        if (OBJ) {
+            for (int o = 16; o > 0; o >>= 1)
+                fsum += __shfl_xor_sync(FULL, fsum, o);
+            if (lane == 0)
+                reinterpret_cast<double *>(smem + L::OFF_RED)[warp - 2] = fsum;
         }
     } else {
         // ------------------------------------------------ drain (warps 6-13)
@@ -542,7 +601,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             sum[c] = 0.0f;
             cmp[c] = 0.0f;
         }
-        double fsum = 0.0;
         auto add_tile = [&](uint32_t ta) {
             float v[NH];
             tmem_ld<NH>(ta, v);
@@ -569,38 +627,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             __syncwarp();
             if (lane == 0)
                 mbar_arrive(acc1_empty(b1));
-            if (OBJ) {
-                // Squared residuals of this thread's row over 32 columns.
-                const int fs = kb % S, fr = kb / S;
-                if (!mbar_wait(obj_full(b1), u1 & 1, abort) ||
-                    !mbar_wait(f32_full(fs), fr & 1, abort)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                float wh[32];
-                tmem_ld32(tq + (uint32_t)(4 * N + b1 * 64 + half * 32), wh);
-                const unsigned char *hsrc = smem + L::OFF_F32 + fs * L::F32_BYTES +
-                                            half * (L::F32_BYTES / 2);
-                float sq = 0.0f;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const float4 a = *reinterpret_cast<const float4 *>(hsrc + sw128_off(row, c));
-                    const float e0 = a.x - wh[4 * c], e1 = a.y - wh[4 * c + 1];
-                    const float e2 = a.z - wh[4 * c + 2], e3 = a.w - wh[4 * c + 3];
-                    sq = fmaf(e0, e0, sq);
-                    sq = fmaf(e1, e1, sq);
-                    sq = fmaf(e2, e2, sq);
-                    sq = fmaf(e3, e3, sq);
-                }
-                fsum += (double)sq;
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(obj_empty(b1));
-                    mbar_arrive(f32_empty(fs));
-                }
-            }
             if ((kb % TC_WIN2) == TC_WIN2 - 1 || kb == nkb - 1) {
                 const int w2 = kb / TC_WIN2, b2 = w2 & 1, u2 = w2 >> 1;
                 if (!mbar_wait(acc2_full(b2), u2 & 1, abort)) {
@@ -618,19 +644,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (ok) {
             const int64_t p = p0 + row;
             if (p < P) {
-                float *o = args.out + p * args.k + args.col0 + cbase;
+                float *o = args.out + (int64_t)blockIdx.y * P * args.k + p * args.k + args.col0 +
+                           cbase;
 #pragma unroll
                 for (int c = 0; c < NH; ++c)
                     if (cbase + c < args.kc)
                         o[c] = sum[c] - cmp[c];
             }
-        }
-        if (OBJ) {
-            // Warp sums, then one value per warp into shared memory.
-            for (int o = 16; o > 0; o >>= 1)
-                fsum += __shfl_xor_sync(FULL, fsum, o);
-            if (lane == 0)
-                reinterpret_cast<double *>(smem + L::OFF_RED)[dw] = fsum;
         }
     }
 
@@ -642,7 +662,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (OBJ) {
             const double *red = reinterpret_cast<const double *>(smem + L::OFF_RED);
             double s = 0.0;
-            for (int w = 0; w < TC_DRAIN_WARPS; ++w)
+            for (int w = 0; w < 4; ++w)
                 s += red[w];
             args.obj_partials[blockIdx.x] = s;
         }
@@ -698,6 +718,21 @@ __global__ void mm_tc_split_rows_kernel(const float *__restrict__ X, int64_t row
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     hi[e] = h;
     lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+// out[p][col0 + c] = sum over splits of part[s][p][col0 + c], in split order.
+__global__ void mm_tc_reduce_kernel(const float *__restrict__ part, int splits, int64_t P, int k,
+                                    int col0, int kc, float *__restrict__ out)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= P * kc)
+        return;
+    const int64_t p = e / kc;
+    const int c = col0 + (int)(e % kc);
+    double acc = 0.0;
+    for (int sp = 0; sp < splits; ++sp)
+        acc += (double)part[(int64_t)sp * P * k + p * k + c];
+    out[p * k + c] = (float)acc;
 }
 
 __global__ void obj_sum_kernel(const double *__restrict__ parts, int n, double *__restrict__ f)
@@ -764,7 +799,8 @@ nmf_status launch_tc(const CUtensorMap (&maps)[7], const TcArgs &a, cudaStream_t
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         configured = 1;
     }
-    const unsigned grid = (unsigned)cdiv(a.P, TC_BM);
+    const int nkb = (int)cdiv(a.Q, TC_BK);
+    const dim3 grid((unsigned)cdiv(a.P, TC_BM), (unsigned)cdiv(nkb, a.kb_per_split));
     mm_tc_kernel<N, TRANS, OBJ><<<grid, TC_THREADS, smem, s>>>(maps[0], maps[1], maps[2], maps[3],
                                                                maps[4], maps[5], maps[6], a);
     NMF_LAUNCHED("mm_tc_kernel");
@@ -784,8 +820,30 @@ nmf_status launch_tc_n(int N, const CUtensorMap (&maps)[7], const TcArgs &a, cud
 // Workspace: [err | product F split (2 x N x Qp BF16) | objective: W split
 // (2 x Pp x 64) | H^T split (2 x Qp x 64) | per-CTA partials].
 struct TcWork {
-    size_t f_off, w_off, h_off, part_off, total;
+    size_t f_off, w_off, h_off, part_off, split_off, total;
 };
+
+constexpr int TC_MAX_SPLITS = 4;
+
+// Contraction splits that fill the last wave of CTAs better (1 CTA per SM).
+int choose_splits(int64_t P, int64_t Q)
+{
+    const int64_t tiles = cdiv(P, TC_BM), nkb = cdiv(Q, TC_BK);
+    const int64_t sms = sm_count();
+    auto eff = [&](int64_t ctas) { return (double)ctas / (double)(cdiv(ctas, sms) * sms); };
+    int best = 1;
+    double best_eff = eff(tiles);
+    for (int sp = 2; sp <= TC_MAX_SPLITS; ++sp) {
+        if (nkb / sp < 16)
+            break;
+        const double e = eff(tiles * sp);
+        if (e > best_eff + 0.03) {
+            best = sp;
+            best_eff = e;
+        }
+    }
+    return best;
+}
 
 TcWork tc_work(int64_t m, int64_t n, int k, int trans, bool obj)
 {
@@ -807,6 +865,9 @@ TcWork tc_work(int64_t m, int64_t n, int k, int trans, bool obj)
     w.part_off = off;
     if (obj)
         off += al(sizeof(double) * (size_t)(Pp / TC_BM));
+    w.split_off = off;
+    if (!obj)
+        off += al(sizeof(float) * (size_t)TC_MAX_SPLITS * (size_t)(P > 0 ? P : 1) * (size_t)k);
     w.total = off;
     return w;
 }
@@ -815,7 +876,9 @@ TcWork tc_work(int64_t m, int64_t n, int k, int trans, bool obj)
 
 size_t mm_tc_work_bytes(int64_t m, int64_t n, int k, int trans)
 {
-    return tc_work(m, n, k, trans, trans == 0 && k <= 64).total;
+    const size_t a = tc_work(m, n, k, trans, false).total;
+    const size_t b = (trans == 0 && k <= 64) ? tc_work(m, n, k, trans, true).total : 0;
+    return a > b ? a : b;
 }
 
 // Products, and with W / Ht / f_dev given (trans = 0, k <= 64) the fused
@@ -901,6 +964,12 @@ nmf_status launch_mm_tc_obj(const float *A, int64_t m, int64_t n, int64_t lda, c
         a.col0 = col0;
         a.kc = kc;
         const bool fuse = obj && col0 == 0;
+        const int splits = fuse ? 1 : choose_splits(P, Q);
+        const int nkb = (int)cdiv(Q, TC_BK);
+        a.kb_per_split = (int)cdiv(nkb, splits);
+        const int grid_y = (int)cdiv(nkb, a.kb_per_split);
+        float *partial = reinterpret_cast<float *>(wb + wl.split_off);
+        a.out = grid_y > 1 ? partial : out;
         nmf_status st;
         if (trans)
             st = launch_tc_n<1, 0>(N, maps, a, s);
@@ -909,6 +978,11 @@ nmf_status launch_mm_tc_obj(const float *A, int64_t m, int64_t n, int64_t lda, c
         else
             st = launch_tc_n<0, 0>(N, maps, a, s);
         NMF_TRY(st);
+        if (grid_y > 1) {
+            mm_tc_reduce_kernel<<<(unsigned)cdiv(P * kc, 256), 256, 0, s>>>(partial, grid_y, P, k,
+                                                                            col0, kc, out);
+            NMF_LAUNCHED("mm_tc_reduce_kernel");
+        }
         if (fuse) {
             obj_sum_kernel<<<1, 256, 0, s>>>(a.obj_partials, (int)(Pp / TC_BM), f_dev);
             NMF_LAUNCHED("obj_sum_kernel");

@@ -68,7 +68,7 @@ def test_mm_dense_fp32(nmf, shape, k, trans):
 
 
 @pytest.mark.parametrize("shape", [(1, 4), (37, 24), (129, 256), (300, 1000), (1000, 300),
-                                   (2050, 20), (4099, 132)])
+                                   (2050, 20), (4099, 132), (512, 8192), (8192, 512)])
 @pytest.mark.parametrize("k", [1, 10, 16, 17, 33, 50, 64, 100, 128])
 @pytest.mark.parametrize("trans", [0, 1])
 def test_mm_dense_bf16x3(nmf, shape, k, trans):
