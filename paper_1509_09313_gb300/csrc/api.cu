@@ -177,7 +177,7 @@ extern "C" nmf_status nmf_objective_dense(const float *A, int64_t m, int64_t n, 
         TempBuf w(s), v(s);
         NMF_CUDA(w.alloc(wb));
         NMF_CUDA(v.alloc(sizeof(float) * (size_t)m * k));
-        NMF_TRY(launch_mm_tc_obj(A, m, n, lda, Ht, k, 0, static_cast<float *>(v.p), W, Ht,
+        NMF_TRY(launch_mm_tc_obj(A, m, n, lda, Ht, k, 0, static_cast<float *>(v.p), W,
                                  static_cast<double *>(f.p), w.p, wb, s));
     } else {
         NMF_CUDA(part.alloc(sizeof(double) * (size_t)objective_partials_len()));
@@ -306,7 +306,7 @@ nmf_status objective_into(nmf_handle *h, double *f_dev)
 {
     const nmf_config &c = h->cfg;
     if (h->fused_obj)
-        return launch_mm_tc_obj(h->A.dense, c.m, c.n, h->A.lda, h->Ht, c.k, 0, h->V, h->W, h->Ht,
+        return launch_mm_tc_obj(h->A.dense, c.m, c.n, h->A.lda, h->Ht, c.k, 0, h->V, h->W,
                                 f_dev, h->tc_work, h->tc_work_bytes, h->stream);
     if (c.input_kind == NMF_INPUT_CSR) {
         NMF_TRY(launch_gram(h->Ht, c.n, c.k, h->GH, h->gram_part, h->stream));
@@ -333,7 +333,7 @@ nmf_status one_iteration(nmf_handle *h)
             // The previous iterate's f(W, H) rides on this A H^T pass.
             double *slot = h->f_hist + ((h->f_count - 1) % F_HIST_CAP);
             NMF_TRY(launch_mm_tc_obj(h->A.dense, c.m, c.n, h->A.lda, h->Ht, c.k, 0, h->V, h->W,
-                                     h->Ht, slot, h->tc_work, h->tc_work_bytes, h->stream));
+                                     slot, h->tc_work, h->tc_work_bytes, h->stream));
             h->obj_pending = false;
         } else {
             NMF_TRY(mm(h, 0, h->Ht, h->V));

@@ -75,8 +75,8 @@ size_t mm_tc_work_bytes(int64_t m, int64_t n, int k, int trans);
 // Same, and with W, Ht, f_dev non-null (trans = 0, k <= 64) the objective
 // f(W, H) = ||A - W H||^2 fused into the pass, written to *f_dev.
 nmf_status launch_mm_tc_obj(const float *A, int64_t m, int64_t n, int64_t lda, const float *F,
-                            int k, int trans, float *out, const float *W, const float *Ht,
-                            double *f_dev, void *work, size_t work_bytes, cudaStream_t s);
+                            int k, int trans, float *out, const float *W, double *f_dev,
+                            void *work, size_t work_bytes, cudaStream_t s);
 
 // CSR SpMM: out (rows x k) = S F.
 nmf_status launch_spmm(const int64_t *rowptr, const int32_t *colidx, const float *vals,

@@ -10,39 +10,52 @@
 // the FP32 accumulator's input), so its relative error is about 2^-17 and
 // unbiased.
 //
-// Kernel (one CTA per 128 output rows, 448 threads):
-//   warp 0     TMA producer: FP32 A tiles (128 x 64 as two 128-byte-swizzled
-//              halves, or 64 x 128 unswizzled for trans = 1) into a staging
-//              ring; pre-split BF16 F tiles (N x 64, 128-byte swizzle) into a
-//              2-stage operand ring.
-//   warp 1     allocates TMEM; one lane issues tcgen05.mma (M = 128, N = 16,
-//              32 or 64, K = 16; 3 MMAs per 16-element step) and commits to
-//              mbarriers.
-//   warps 2-5  split each FP32 A tile into BF16 hi/lo tiles in the canonical
-//              K-major 128-byte-swizzled layout (transposing when trans = 1).
+// Kernel (one CTA per 128 output rows). Shared memory is one ring of stages,
+// each holding the FP32 A tile of a K-block (128 x 64, or 64 x 128 for
+// trans = 1) and the pre-split BF16 F tiles of the same K-block (N x 64 hi
+// and lo, 128-byte swizzle); 4 to 6 stages keep 100+ KB of A in flight per SM.
+//   warp 0     TMA producer: refills a stage once every MMA reading it is done.
+//   warp 1     allocates TMEM; one lane issues the product MMAs (M = 128,
+//              N = 16, 32 or 64, K = 16; 3 per 16-element step). This thread's
+//              instruction stream is the pass's critical path (issuing an MMA,
+//              a commit or a try_wait costs 30-45 cycles; an N = 64 MMA keeps
+//              the tensor core ~48), so its descriptors are precomputed and
+//              it waits on as few barriers as possible.
+//   warps 2-5  split the FP32 A tile into BF16 hi/lo IN PLACE, in the
+//              canonical K-major 128-byte-swizzled operand layout. trans = 0:
+//              each thread owns one row (its TMEM lane); the 32 floats of a
+//              128-byte row become [hi of the 32 | lo of the 32], so the MMA of
+//              each 16-element step reads hi at +32 s bytes and lo at +64 + 32 s
+//              of the row. trans = 1: the tile is transposed (thread = output
+//              row), so the four warps first read the whole tile into
+//              registers, meet at an mbarrier, then write hi and lo tiles.
 //   warps 6-13 drain the TMEM accumulators (tcgen05.ld) into registers; two
 //              warps per TMEM lane quarter, each owning half of the columns.
+//   warp 14    (objective only) issues the W H tile MMAs.
 // Accuracy: the tensor cores' FP32 accumulation truncates, so every MMA that
 // adds into an accumulator biases it by about half an ulp of its value;
 // accumulating all n / 16 * 3 steps in one place would bias the result by
 // ~1e-6 relative and spread it by as much, which the NLS solves amplify by
 // cond(G). The dominant hi*hi products therefore go to their own ping-pong
 // accumulator pair, drained after every K-block (4 MMAs), and the two cross
-// products (about 2^-8 smaller) to a second pair drained every 4 K-blocks;
-// the drain warps add each tile into registers with Kahan compensation.
-// Measured against FP64 at n = 64000: bias -4e-8, spread 3e-8 (plain FP32
-// rounding: spread 2.3e-8).
+// products (about 2^-8 smaller, so their truncation is 2^-8 as large) to a
+// second pair drained every TC_WIN2 K-blocks; the drain warps add each tile
+// into registers with Kahan compensation. Measured against FP64 at n = 64000:
+// bias -4e-8, spread 3e-8 (plain FP32 rounding: spread 2.3e-8).
 //
-// Fused objective (trans = 0, k <= 64): with W and H^T given, every K-block
-// also forms the 128 x 64 tile of W H (W tile resident in shared memory,
-// K = k padded to 64, three split products) in a third ping-pong TMEM pair,
-// issued one K-block ahead (it needs no A). The split warps, each owning 32
-// rows of the tile (their TMEM lane quarter), subtract it from the staged A
-// values they have just split and add the squared residuals in FP64. The
-// A H^T pass of an ANLS iteration thereby yields f(W, H) of the previous
-// iterate without reading A again. A relative bias b
-// of W H shifts f by about S b with S = 2 mean(r) mean(WH) / mean(r^2)
-// (|S| <= 4 on the dense workloads), far inside the 1e-5 tolerance.
+// Fused objective (trans = 0, k <= 64): with W given, every K-block also
+// forms the 128 x 64 tile of W H (W tile resident in shared memory, K = k
+// padded to 16/32/64, three split products) in a third ping-pong TMEM pair.
+// Its B operand is the stage's own F = H^T tile read MN-major (the 64 columns
+// of the K-block contiguous, k along K), so H costs no extra loads; a second
+// issuing thread (warp 14) runs these MMAs as soon as the stage lands. The
+// split warps, each owning 32 rows of the tile (their TMEM lane quarter),
+// subtract it from the FP32 A values they are about to split and add the
+// squared residuals (FP32 within a half row, FP64 across). The A H^T pass of
+// an ANLS iteration thereby yields f(W, H) of the previous iterate without
+// reading A again. A relative bias b of W H shifts f by about S b with
+// S = 2 mean(r) mean(WH) / mean(r^2) (|S| <= 4 on the dense workloads), far
+// inside the 1e-5 tolerance.
 //
 // F (H^T or W) is split once per call by mm_tc_split_kernel into a padded
 // N x Qp BF16 pair (the workspace); k > 64 is processed in 64-column chunks.
@@ -64,34 +77,28 @@ namespace {
 
 constexpr int TC_BM = 128;        // output rows per CTA (MMA M)
 constexpr int TC_BK = 64;         // contraction elements per K-block (128-byte BF16 row)
-constexpr int TC_BF_STAGES = 2;   // BF16 operand ring
-constexpr int TC_WIN2 = 4;        // K-blocks per cross-term accumulation window
-constexpr int TC_THREADS = 448;
+constexpr int TC_WIN2 = 8;        // K-blocks per cross-term accumulation window
 constexpr int TC_DRAIN_WARPS = 8;
+constexpr int TC_SMEM_MAX = 227 * 1024;
 constexpr long long TC_WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
 template <int N, int OBJ>
 struct TcLayout {
-    static constexpr int F32_STAGES = OBJ ? 2 : 3;         // FP32 A staging ring
-    static constexpr int F32_BYTES = TC_BM * TC_BK * 4;   // 32 KB
-    static constexpr int A_BYTES = TC_BM * TC_BK * 2;     // 16 KB
-    static constexpr int B_BYTES = N * TC_BK * 2;
-    static constexpr int H_BYTES = OBJ ? 64 * TC_BK * 2 : 0;    // objective B (64 j x 64 r)
+    // warps: 0 TMA, 1 product MMAs, 2-5 split, 6-13 drain, 14 objective MMAs.
+    static constexpr int THREADS = 448 + (OBJ ? 32 : 0);
+    static constexpr int F32_BYTES = TC_BM * TC_BK * 4;   // 32 KB FP32 A tile (split in place)
+    static constexpr int A_BYTES = TC_BM * TC_BK * 2;     // 16 KB: one BF16 A tile
+    static constexpr int B_BYTES = N * TC_BK * 2;         // one BF16 F tile (hi or lo)
+    static constexpr int STAGE_BYTES = F32_BYTES + 2 * B_BYTES;
     static constexpr int W_BYTES = OBJ ? TC_BM * TC_BK * 2 : 0; // objective A (128 i x 64 r)
-    static constexpr int OFF_F32 = 0;
-    static constexpr int OFF_AHI = OFF_F32 + F32_STAGES * F32_BYTES;
-    static constexpr int OFF_ALO = OFF_AHI + TC_BF_STAGES * A_BYTES;
-    static constexpr int OFF_BHI = OFF_ALO + TC_BF_STAGES * A_BYTES;
-    static constexpr int OFF_BLO = OFF_BHI + TC_BF_STAGES * B_BYTES;
-    static constexpr int OFF_HHI = OFF_BLO + TC_BF_STAGES * B_BYTES;
-    static constexpr int OFF_HLO = OFF_HHI + TC_BF_STAGES * H_BYTES;
-    static constexpr int OFF_WHI = OFF_HLO + TC_BF_STAGES * H_BYTES;
+    static constexpr int FIT = (TC_SMEM_MAX - 2048 - 2 * W_BYTES) / STAGE_BYTES;
+    static constexpr int STAGES = FIT > 6 ? 6 : FIT;
+    static constexpr int OFF_WHI = STAGES * STAGE_BYTES;
     static constexpr int OFF_WLO = OFF_WHI + W_BYTES;
-    static constexpr int OFF_BAR = (OFF_WLO + W_BYTES + 1023) & ~1023;
-    // barriers: f32_full[S], f32_empty[S], b_full[2], a_full[2], bf_empty[2],
-    // acc1_full[2], acc1_empty[2], acc2_full[2], acc2_empty[2], obj_full[2],
-    // obj_empty[2], w_full
-    static constexpr int NBAR = 2 * F32_STAGES + 3 * TC_BF_STAGES + 13;
+    static constexpr int OFF_BAR = OFF_WLO + W_BYTES;
+    // barriers: full[S], empty[S], a_full[S], readb[S], acc1_full[2],
+    // acc1_empty[2], acc2_full[2], acc2_empty[2], obj_full[2], obj_empty[2], w_full
+    static constexpr int NBAR = 4 * STAGES + 13;
     static constexpr int OFF_TMEM = OFF_BAR + NBAR * 8;
     static constexpr int OFF_ABORT = OFF_TMEM + 4;
     static constexpr int OFF_RED = (OFF_ABORT + 4 + 15) & ~15;    // 8 doubles
@@ -100,11 +107,11 @@ struct TcLayout {
     static constexpr int COLS = 4 * N + (OBJ ? 128 : 0);
     static constexpr int TMEM_COLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128
                                    : COLS <= 256 ? 256 : 512;
-    static_assert(OFF_AHI % 1024 == 0 && OFF_BHI % 1024 == 0 && OFF_BLO % 1024 == 0 &&
-                      OFF_HHI % 1024 == 0 && OFF_WHI % 1024 == 0 && A_BYTES % 1024 == 0 &&
-                      B_BYTES % 1024 == 0,
+    static_assert(STAGES >= 3, "at least three stages");
+    static_assert(STAGE_BYTES % 1024 == 0 && F32_BYTES % 1024 == 0 && B_BYTES % 1024 == 0 &&
+                      A_BYTES % 1024 == 0 && OFF_WHI % 1024 == 0 && W_BYTES % 1024 == 0,
                   "128-byte-swizzled tiles need 1024-byte alignment");
-    static_assert(BYTES + 1024 <= 227 * 1024, "shared memory budget");
+    static_assert(BYTES + 1024 <= TC_SMEM_MAX, "shared memory budget");
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -160,6 +167,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
+// The same wait for the MMA-issuing thread, whose instruction stream is the
+// critical path: a phase that has already completed costs one try_wait.
+__device__ __forceinline__ bool mbar_wait_fast(uint32_t bar, uint32_t parity, volatile int *abort)
+{
+    return mbar_try_wait(bar, parity) || mbar_wait(bar, parity, abort);
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
                                             uint32_t bar)
 {
@@ -168,11 +182,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
         : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -190,14 +199,36 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
     return d;
 }
 
-// Instruction descriptor, kind::f16: BF16 A and B, FP32 D, both K-major.
-template <int N>
-__device__ __forceinline__ uint32_t idesc_bf16_f32()
+// Shared-memory matrix descriptor for an MN-major operand with 128-byte
+// swizzle whose MN extent is one swizzle atom (64 BF16 values per 128-byte
+// row, K along the rows): 8-row groups along K are 1024 bytes apart. The
+// stride between atoms along MN is never used at this width; it gets the
+// same 1024 bytes.
+__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t saddr)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(TC_BM >> 4) << 24);
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(1024u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
 }
 
+// Instruction descriptor, kind::f16: BF16 A and B, FP32 D, A K-major; B
+// K-major, or MN-major when B_MN (bit 16).
+template <int N, int B_MN = 0>
+__device__ __forceinline__ uint32_t idesc_bf16_f32()
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)B_MN << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// A and B from shared memory.
 __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
                                          uint32_t idesc, uint32_t accumulate)
 {
@@ -277,25 +308,29 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[C])
         tmem_ld8(taddr, v);
 }
 
+// Split 2 FP32 values into packed BF16 pairs (low half = first value).
+__device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_t &lo)
+{
+    const __nv_bfloat162 hb = __floats2bfloat162_rn(v0, v1);
+    const float2 hf = __bfloat1622float2(hb);
+    const __nv_bfloat162 lb = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&hb);
+    lo = *reinterpret_cast<const uint32_t *>(&lb);
+}
+
 // Split 8 FP32 values into packed BF16 hi and lo (16 bytes each).
 __device__ __forceinline__ void split8(const float (&v)[8], uint4 &hi, uint4 &lo)
 {
     uint32_t h[4], l[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const __nv_bfloat162 hb = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-        const float2 hf = __bfloat1622float2(hb);
-        const __nv_bfloat162 lb = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
-        h[i] = *reinterpret_cast<const uint32_t *>(&hb);
-        l[i] = *reinterpret_cast<const uint32_t *>(&lb);
-    }
+    for (int i = 0; i < 4; ++i)
+        split2(v[2 * i], v[2 * i + 1], h[i], l[i]);
     hi = make_uint4(h[0], h[1], h[2], h[3]);
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // Byte offset of (row r, 16-byte chunk c) in a 128-byte-swizzled tile with
-// 128-byte rows (BF16 K-major operands, and each 32-float half of a staged
-// FP32 A tile when trans = 0).
+// 128-byte rows (each 32-float half of a staged FP32 A tile when trans = 0).
 __device__ __forceinline__ uint32_t sw128_off(int r, int c)
 {
     return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
@@ -312,15 +347,14 @@ struct TcArgs {
 
 // -------------------------------------------------------------------- kernel
 template <int N, int TRANS, int OBJ>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
     mm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
                  const __grid_constant__ CUtensorMap tmBlo, const __grid_constant__ CUtensorMap tmWhi,
-                 const __grid_constant__ CUtensorMap tmWlo, const __grid_constant__ CUtensorMap tmHhi,
-                 const __grid_constant__ CUtensorMap tmHlo, const TcArgs args)
+                 const __grid_constant__ CUtensorMap tmWlo, const TcArgs args)
 {
     static_assert(!OBJ || TRANS == 0, "the objective rides on the A H^T pass");
     using L = TcLayout<N, OBJ>;
-    constexpr int S = L::F32_STAGES;
+    constexpr int S = L::STAGES;
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
@@ -331,12 +365,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int64_t P = args.P, Q = args.Q;
 
     const uint32_t bar0 = sbase + L::OFF_BAR;
-    auto f32_full = [&](int i) { return bar0 + 8u * i; };
-    auto f32_empty = [&](int i) { return bar0 + 8u * (S + i); };
-    auto b_full = [&](int i) { return bar0 + 8u * (2 * S + i); };
-    auto a_full = [&](int i) { return bar0 + 8u * (2 * S + TC_BF_STAGES + i); };
-    auto bf_empty = [&](int i) { return bar0 + 8u * (2 * S + 2 * TC_BF_STAGES + i); };
-    const uint32_t accb = bar0 + 8u * (2 * S + 3 * TC_BF_STAGES);
+    auto full = [&](int i) { return bar0 + 8u * i; };              // TMA bytes landed
+    auto empty = [&](int i) { return bar0 + 8u * (S + i); };       // MMAs of the stage done
+    auto a_full = [&](int i) { return bar0 + 8u * (2 * S + i); };  // A split in place
+    auto readb = [&](int i) { return bar0 + 8u * (3 * S + i); };   // trans = 1: tile read
+    const uint32_t accb = bar0 + 8u * (4 * S);
     auto acc1_full = [&](int i) { return accb + 8u * i; };
     auto acc1_empty = [&](int i) { return accb + 8u * (2 + i); };
     auto acc2_full = [&](int i) { return accb + 8u * (4 + i); };
@@ -347,13 +380,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < S; ++i) {
-            mbar_init(f32_full(i), 1);
-            mbar_init(f32_empty(i), 4);
-        }
-        for (int i = 0; i < TC_BF_STAGES; ++i) {
-            mbar_init(b_full(i), 1);
+            mbar_init(full(i), 1);
+            mbar_init(empty(i), OBJ ? 2 : 1);   // product MMAs (+ objective MMAs)
             mbar_init(a_full(i), 4);
-            mbar_init(bf_empty(i), 1);
+            mbar_init(readb(i), 4);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(acc1_full(i), 1);
@@ -383,6 +413,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int nkb_all = (int)((Q + TC_BK - 1) / TC_BK);
     const int kb0 = blockIdx.y * args.kb_per_split;   // first K-block of this CTA
     const int nkb = min(args.kb_per_split, nkb_all - kb0);
+    auto stage = [&](int s) { return sbase + (uint32_t)(s * L::STAGE_BYTES); };
+    // Descriptors are formed once and advanced by constant adds: the start
+    // address field holds addr >> 4 in its low 14 bits, and every shared
+    // address here is below 256 KB, so no carry leaves the field.
+    constexpr uint64_t STAGE16 = (uint64_t)(L::STAGE_BYTES >> 4);
+    constexpr uint64_t F16 = (uint64_t)(L::F32_BYTES >> 4);
+    constexpr uint64_t BLO16 = (uint64_t)(L::B_BYTES >> 4);
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
@@ -393,194 +430,194 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tma_load_2d(sbase + L::OFF_WLO, &tmWlo, 0, (int)p0, w_full);
             }
             for (int kb = 0; kb < nkb; ++kb) {
-                const int fs = kb % S, fr = kb / S;
-                const int bs = kb % TC_BF_STAGES, br = kb / TC_BF_STAGES;
-                if (!mbar_wait(f32_empty(fs), (fr & 1) ^ 1, abort))
+                const int s = kb % S, u = kb / S;
+                if (!mbar_wait(empty(s), (u & 1) ^ 1, abort))
                     break;
-                mbar_arrive_expect_tx(f32_full(fs), L::F32_BYTES);
-                const uint32_t dstA = sbase + L::OFF_F32 + fs * L::F32_BYTES;
+                mbar_arrive_expect_tx(full(s), L::STAGE_BYTES);
+                const uint32_t dst = stage(s);
+                const int q0 = (kb0 + kb) * TC_BK;
                 if (TRANS == 0) {
                     // Two 128-byte-swizzled halves of 32 columns each.
-                    tma_load_2d(dstA, &tmA, (kb0 + kb) * TC_BK, (int)p0, f32_full(fs));
-                    tma_load_2d(dstA + L::F32_BYTES / 2, &tmA, (kb0 + kb) * TC_BK + 32, (int)p0,
-                                f32_full(fs));
+                    tma_load_2d(dst, &tmA, q0, (int)p0, full(s));
+                    tma_load_2d(dst + L::F32_BYTES / 2, &tmA, q0 + 32, (int)p0, full(s));
                 } else {
-                    tma_load_2d(dstA, &tmA, (int)p0, (kb0 + kb) * TC_BK, f32_full(fs));
+                    tma_load_2d(dst, &tmA, (int)p0, q0, full(s));
                 }
-                if (!mbar_wait(bf_empty(bs), (br & 1) ^ 1, abort))
-                    break;
-                mbar_arrive_expect_tx(b_full(bs), 2 * L::B_BYTES + 2 * L::H_BYTES);
-                tma_load_2d(sbase + L::OFF_BHI + bs * L::B_BYTES, &tmBhi, (kb0 + kb) * TC_BK, 0,
-                            b_full(bs));
-                tma_load_2d(sbase + L::OFF_BLO + bs * L::B_BYTES, &tmBlo, (kb0 + kb) * TC_BK, 0,
-                            b_full(bs));
-                if (OBJ) {
-                    tma_load_2d(sbase + L::OFF_HHI + bs * L::H_BYTES, &tmHhi, 0, (kb0 + kb) * TC_BK,
-                                b_full(bs));
-                    tma_load_2d(sbase + L::OFF_HLO + bs * L::H_BYTES, &tmHlo, 0, (kb0 + kb) * TC_BK,
-                                b_full(bs));
-                }
+                tma_load_2d(dst + L::F32_BYTES, &tmBhi, q0, 0, full(s));
+                tma_load_2d(dst + L::F32_BYTES + L::B_BYTES, &tmBlo, q0, 0, full(s));
             }
         }
     } else if (warp == 1) {
-        // ------------------------------------------------------------ MMA issuer
+        // ------------------------------------------------------ product MMAs
+        // One thread issues the 12 MMAs of a K-block; its instruction stream
+        // is on the critical path (each tcgen05.mma, commit or try_wait costs
+        // 30-45 cycles to issue; an N = 64 MMA occupies the tensor core ~48).
         // TMEM columns: D1 buffers at [0, N) and [N, 2N) (hi*hi, one K-block
         // each), D2 buffers at [2N, 4N) (cross terms, windows of TC_WIN2
-        // K-blocks), objective D3 buffers at [4N, 4N + 128) (64 columns each).
+        // K-blocks), objective D3 buffers at [4N, 4N + 128).
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_f32<N>();
-            const uint32_t idesc_obj = idesc_bf16_f32<64>();
-            // Objective tile W H of K-block j (needs only W and the H^T tile).
-            auto issue_obj = [&](int j) -> bool {
-                const int bs = j % TC_BF_STAGES, br = j / TC_BF_STAGES;
-                const int b = j & 1, u = j >> 1;
-                if (!mbar_wait(obj_empty(b), (u & 1) ^ 1, abort) ||
-                    !mbar_wait(b_full(bs), br & 1, abort))
-                    return false;
-                tc_fence_after();
-                const uint32_t d3 = tmem + (uint32_t)(4 * N + b * 64);
-                const uint32_t whi = sbase + L::OFF_WHI, wlo = sbase + L::OFF_WLO;
-                const uint32_t hhi = sbase + L::OFF_HHI + bs * L::H_BYTES;
-                const uint32_t hlo = sbase + L::OFF_HLO + bs * L::H_BYTES;
-#pragma unroll
-                for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                    const uint32_t o = kk * 32;
-                    mma_bf16(d3, sw128_desc(whi + o), sw128_desc(hhi + o), idesc_obj, kk ? 1u : 0u);
-                    mma_bf16(d3, sw128_desc(whi + o), sw128_desc(hlo + o), idesc_obj, 1u);
-                    mma_bf16(d3, sw128_desc(wlo + o), sw128_desc(hhi + o), idesc_obj, 1u);
-                }
-                mma_commit(obj_full(b));
-                return true;
-            };
-            bool ok = true;
-            if (OBJ)
-                ok = mbar_wait(w_full, 0, abort) && issue_obj(0);
-            for (int kb = 0; kb < nkb && ok; ++kb) {
-                const int bs = kb % TC_BF_STAGES, br = kb / TC_BF_STAGES;
+            const uint64_t a0 = sw128_desc(sbase), b0 = a0 + F16;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % S, u = kb / S;
                 const int b1 = kb & 1, u1 = kb >> 1;
                 const int w2 = kb / TC_WIN2, b2 = w2 & 1, u2 = w2 >> 1;
                 const bool first2 = (kb % TC_WIN2) == 0;
-                if (!mbar_wait(acc1_empty(b1), (u1 & 1) ^ 1, abort))
+                if (!mbar_wait_fast(acc1_empty(b1), (u1 & 1) ^ 1, abort))
                     break;
-                if (first2 && !mbar_wait(acc2_empty(b2), (u2 & 1) ^ 1, abort))
+                if (first2 && !mbar_wait_fast(acc2_empty(b2), (u2 & 1) ^ 1, abort))
                     break;
-                if (!mbar_wait(a_full(bs), br & 1, abort) || !mbar_wait(b_full(bs), br & 1, abort))
+                if (!mbar_wait_fast(a_full(s), u & 1, abort))
                     break;
                 tc_fence_after();
                 const uint32_t d1 = tmem + (uint32_t)(b1 * N);
                 const uint32_t d2 = tmem + (uint32_t)((2 + b2) * N);
-                const uint32_t ahi = sbase + L::OFF_AHI + bs * L::A_BYTES;
-                const uint32_t alo = sbase + L::OFF_ALO + bs * L::A_BYTES;
-                const uint32_t bhi = sbase + L::OFF_BHI + bs * L::B_BYTES;
-                const uint32_t blo = sbase + L::OFF_BLO + bs * L::B_BYTES;
+                const uint64_t as = a0 + (uint64_t)s * STAGE16;
+                const uint64_t bh = b0 + (uint64_t)s * STAGE16, bl = bh + BLO16;
 #pragma unroll
                 for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                    const uint32_t o = kk * 32;   // 16 BF16 elements along K
-                    mma_bf16(d1, sw128_desc(ahi + o), sw128_desc(bhi + o), idesc, kk ? 1u : 0u);
+                    // A hi / lo of this 16-element step (see the split warps).
+                    const uint64_t ah = TRANS == 0
+                                            ? as + (uint64_t)((kk >> 1) * (L::F32_BYTES / 32) + (kk & 1) * 2)
+                                            : as + (uint64_t)(kk * 2);
+                    const uint64_t al = TRANS == 0 ? ah + 4 : ah + (uint64_t)(L::A_BYTES >> 4);
+                    const uint64_t o = (uint64_t)(kk * 2);   // 16 BF16 = 32 bytes along K
+                    mma_bf16(d1, ah, bh + o, idesc, kk ? 1u : 0u);
+                    mma_bf16(d2, ah, bl + o, idesc, (first2 && kk == 0) ? 0u : 1u);
+                    mma_bf16(d2, al, bh + o, idesc, 1u);
                 }
                 mma_commit(acc1_full(b1));
-#pragma unroll
-                for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                    const uint32_t o = kk * 32;
-                    mma_bf16(d2, sw128_desc(ahi + o), sw128_desc(blo + o), idesc,
-                             (first2 && kk == 0) ? 0u : 1u);
-                    mma_bf16(d2, sw128_desc(alo + o), sw128_desc(bhi + o), idesc, 1u);
-                }
-                mma_commit(bf_empty(bs));
+                mma_commit(empty(s));
                 if ((kb % TC_WIN2) == TC_WIN2 - 1 || kb == nkb - 1)
                     mma_commit(acc2_full(b2));
-                if (OBJ && kb + 1 < nkb && !issue_obj(kb + 1))
-                    break;
             }
         }
-    } else if (warp < 6) {
+    } else if (OBJ && warp == 14) {
+        // ---------------------------------------------------- objective MMAs
+        // W H tile of every K-block: W (K-major, K = r, resident) times the
+        // stage's F = H^T tile read MN-major (N = the K-block's 64 columns),
+        // issued by its own thread so it never waits behind the products.
+        if (lane == 0) {
+            const uint32_t idesc_obj = idesc_bf16_f32<TC_BK, 1>();
+            const uint64_t wh = sw128_desc(sbase + L::OFF_WHI), wl = sw128_desc(sbase + L::OFF_WLO);
+            const uint64_t f0 = sw128_mn_desc(sbase + L::F32_BYTES);
+            bool ok = mbar_wait_fast(w_full, 0, abort);
+            for (int j = 0; j < nkb && ok; ++j) {
+                const int s = j % S, u = j / S;
+                const int b = j & 1, ub = j >> 1;
+                if (!mbar_wait_fast(obj_empty(b), (ub & 1) ^ 1, abort) ||
+                    !mbar_wait_fast(full(s), u & 1, abort))
+                    break;
+                tc_fence_after();
+                const uint32_t d3 = tmem + (uint32_t)(4 * N + b * 64);
+                const uint64_t fh = f0 + (uint64_t)s * STAGE16, fl = fh + BLO16;
+#pragma unroll
+                for (int kk = 0; kk < N / 16; ++kk) {
+                    const uint64_t o = (uint64_t)(kk * 2);            // 16 r along W's rows
+                    const uint64_t of = (uint64_t)(kk * (2048 >> 4)); // 16 r = two 8-row groups
+                    mma_bf16(d3, wh + o, fh + of, idesc_obj, kk ? 1u : 0u);
+                    mma_bf16(d3, wh + o, fl + of, idesc_obj, 1u);
+                    mma_bf16(d3, wl + o, fh + of, idesc_obj, 1u);
+                }
+                mma_commit(obj_full(b));
+                mma_commit(empty(s));
+            }
+        }
+    } else if (warp >= 2 && warp < 6) {
         // ---------------------------------------------------- split (warps 2-5)
         const int ct = threadIdx.x - 64;        // 0..127
         const int quarter = warp & 3;           // TMEM lane quarter of this warp
         const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16);
         double fsum = 0.0;
         for (int kb = 0; kb < nkb; ++kb) {
-            const int fs = kb % S, fr = kb / S;
-            const int bs = kb % TC_BF_STAGES, br = kb / TC_BF_STAGES;
-            if (!mbar_wait(f32_full(fs), fr & 1, abort) ||
-                !mbar_wait(bf_empty(bs), (br & 1) ^ 1, abort))
+            const int s = kb % S, u = kb / S;
+            if (!mbar_wait(full(s), u & 1, abort))
                 break;
-            const unsigned char *src = smem + L::OFF_F32 + fs * L::F32_BYTES;
-            unsigned char *ahi = smem + L::OFF_AHI + bs * L::A_BYTES;
-            unsigned char *alo = smem + L::OFF_ALO + bs * L::A_BYTES;
+            unsigned char *st = smem + s * L::STAGE_BYTES;
+            const int b1 = kb & 1, u1 = kb >> 1;
             if (TRANS == 0) {
-                // src: two swizzled halves of 128 rows (p) x 32 floats (q). Each
-                // converter warp owns the 32 rows of its TMEM lane quarter
-                // (lane = row), so it can also read the objective tile W H.
+                // Two swizzled halves of 128 rows (p) x 32 floats (q). Each
+                // thread owns row r (= its TMEM lane) and rewrites the 128
+                // bytes of its row in a half as [hi of the 32 | lo of the 32].
                 const int r = quarter * 32 + lane;
+                if (OBJ) {
+                    if (!mbar_wait(obj_full(b1), u1 & 1, abort))
+                        break;
+                    tc_fence_after();
+                }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const unsigned char *hsrc = src + h * (L::F32_BYTES / 2);
+                    unsigned char *hs = st + h * (L::F32_BYTES / 2);
+                    float a[32];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const float4 v = *reinterpret_cast<const float4 *>(hs + sw128_off(r, c));
+                        a[4 * c] = v.x;
+                        a[4 * c + 1] = v.y;
+                        a[4 * c + 2] = v.z;
+                        a[4 * c + 3] = v.w;
+                    }
+                    if (OBJ) {
+                        // Squared residuals against the W H tile of these columns.
+                        float wh[32];
+                        tmem_ld32(tq + (uint32_t)(4 * N + b1 * 64 + h * 32), wh);
+                        float sq = 0.0f;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const float e = a[i] - wh[i];
+                            sq = fmaf(e, e, sq);
+                        }
+                        fsum += (double)sq;
+                    }
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        const float4 a =
-                            *reinterpret_cast<const float4 *>(hsrc + sw128_off(r, 2 * c));
-                        const float4 b =
-                            *reinterpret_cast<const float4 *>(hsrc + sw128_off(r, 2 * c + 1));
-                        const float w8[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+                        float w8[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            w8[j] = a[8 * c + j];
                         uint4 hi, lo;
                         split8(w8, hi, lo);
-                        *reinterpret_cast<uint4 *>(ahi + sw128_off(r, h * 4 + c)) = hi;
-                        *reinterpret_cast<uint4 *>(alo + sw128_off(r, h * 4 + c)) = lo;
+                        *reinterpret_cast<uint4 *>(hs + sw128_off(r, c)) = hi;
+                        *reinterpret_cast<uint4 *>(hs + sw128_off(r, 4 + c)) = lo;
                     }
                 }
+                if (OBJ)
+                    tc_fence_before();
             } else {
-                // src: 64 rows (q) x 128 floats (p), 512 bytes per row; row p = ct.
-                const float *sp = reinterpret_cast<const float *>(src);
-#pragma unroll 2
+                // 64 rows (q) x 128 floats (p), 512 bytes per row; this thread
+                // produces output row p = ct. Read the whole column first (the
+                // hi / lo tiles overwrite other threads' columns).
+                const float *sp = reinterpret_cast<const float *>(st);
+                float v[TC_BK];
+#pragma unroll
+                for (int j = 0; j < TC_BK; ++j)
+                    v[j] = sp[j * TC_BM + ct];
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(readb(s));
+                if (!mbar_wait(readb(s), u & 1, abort))
+                    break;
+                unsigned char *ahi = st;
+                unsigned char *alo = st + L::A_BYTES;
+#pragma unroll
                 for (int c = 0; c < TC_BK / 8; ++c) {
-                    float v[8];
+                    float w8[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
-                        v[j] = sp[(8 * c + j) * TC_BM + ct];
+                        w8[j] = v[8 * c + j];
                     uint4 hi, lo;
-                    split8(v, hi, lo);
+                    split8(w8, hi, lo);
                     *reinterpret_cast<uint4 *>(ahi + sw128_off(ct, c)) = hi;
                     *reinterpret_cast<uint4 *>(alo + sw128_off(ct, c)) = lo;
                 }
             }
             fence_proxy_async();
             __syncwarp();
-            if (lane == 0)
-                mbar_arrive(a_full(bs));
-            if (OBJ && TRANS == 0) {
-                // Squared residuals of this warp's 32 rows against the W H tile
-                // (issued a K-block ahead, so normally complete by now).
-                const int r = quarter * 32 + lane;
-                const int b1 = kb & 1, u1 = kb >> 1;
-                if (!mbar_wait(obj_full(b1), u1 & 1, abort))
-                    break;
-                tc_fence_after();
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const unsigned char *hsrc = src + h * (L::F32_BYTES / 2);
-                    float wh[32];
-                    tmem_ld32(tq + (uint32_t)(4 * N + b1 * 64 + h * 32), wh);
-                    float sq = 0.0f;
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const float4 a = *reinterpret_cast<const float4 *>(hsrc + sw128_off(r, c));
-                        const float e0 = a.x - wh[4 * c], e1 = a.y - wh[4 * c + 1];
-                        const float e2 = a.z - wh[4 * c + 2], e3 = a.w - wh[4 * c + 3];
-                        sq = fmaf(e0, e0, sq);
-                        sq = fmaf(e1, e1, sq);
-                        sq = fmaf(e2, e2, sq);
-                        sq = fmaf(e3, e3, sq);
-                    }
-                    fsum += (double)sq;
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0)
+            if (lane == 0) {
+                if (OBJ)
                     mbar_arrive(obj_empty(b1));
+                mbar_arrive(a_full(s));
             }
-            if (lane == 0)
-                mbar_arrive(f32_empty(fs));
         }
         if (OBJ) {
             for (int o = 16; o > 0; o >>= 1)
@@ -588,7 +625,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (lane == 0)
                 reinterpret_cast<double *>(smem + L::OFF_RED)[warp - 2] = fsum;
         }
-    } else {
+    } else if (warp >= 6 && warp < 14) {
         // ------------------------------------------------ drain (warps 6-13)
         constexpr int NH = N / 2;               // product columns owned by this warp
         const int dw = warp - 6;
@@ -601,15 +638,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             sum[c] = 0.0f;
             cmp[c] = 0.0f;
         }
+        // Kahan-add a TMEM tile, CH columns per load to bound register use.
+        constexpr int CH = NH < 16 ? NH : 16;
         auto add_tile = [&](uint32_t ta) {
-            float v[NH];
-            tmem_ld<NH>(ta, v);
 #pragma unroll
-            for (int i = 0; i < NH; ++i) {
-                const float y = v[i] - cmp[i];
-                const float t = sum[i] + y;
-                cmp[i] = (t - sum[i]) - y;
-                sum[i] = t;
+            for (int c0 = 0; c0 < NH; c0 += CH) {
+                float v[CH];
+                tmem_ld<CH>(ta + (uint32_t)c0, v);
+#pragma unroll
+                for (int i = 0; i < CH; ++i) {
+                    const float y = v[i] - cmp[c0 + i];
+                    const float t = sum[c0 + i] + y;
+                    cmp[c0 + i] = (t - sum[c0 + i]) - y;
+                    sum[c0 + i] = t;
+                }
             }
         };
         const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16);
@@ -789,7 +831,7 @@ bool make_map_2d(CUtensorMap *map, CUtensorMapDataType dt, const void *base, uin
 constexpr size_t TC_ERR_BYTES = 256;
 
 template <int N, int TRANS, int OBJ>
-nmf_status launch_tc(const CUtensorMap (&maps)[7], const TcArgs &a, cudaStream_t s)
+nmf_status launch_tc(const CUtensorMap (&maps)[5], const TcArgs &a, cudaStream_t s)
 {
     using L = TcLayout<N, OBJ>;
     const int smem = L::BYTES + 1024;
@@ -801,14 +843,14 @@ nmf_status launch_tc(const CUtensorMap (&maps)[7], const TcArgs &a, cudaStream_t
     }
     const int nkb = (int)cdiv(a.Q, TC_BK);
     const dim3 grid((unsigned)cdiv(a.P, TC_BM), (unsigned)cdiv(nkb, a.kb_per_split));
-    mm_tc_kernel<N, TRANS, OBJ><<<grid, TC_THREADS, smem, s>>>(maps[0], maps[1], maps[2], maps[3],
-                                                               maps[4], maps[5], maps[6], a);
+    mm_tc_kernel<N, TRANS, OBJ><<<grid, L::THREADS, smem, s>>>(maps[0], maps[1], maps[2], maps[3],
+                                                               maps[4], a);
     NMF_LAUNCHED("mm_tc_kernel");
     return NMF_OK;
 }
 
 template <int TRANS, int OBJ>
-nmf_status launch_tc_n(int N, const CUtensorMap (&maps)[7], const TcArgs &a, cudaStream_t s)
+nmf_status launch_tc_n(int N, const CUtensorMap (&maps)[5], const TcArgs &a, cudaStream_t s)
 {
     if (N == 16)
         return launch_tc<16, TRANS, OBJ>(maps, a, s);
@@ -818,9 +860,9 @@ nmf_status launch_tc_n(int N, const CUtensorMap (&maps)[7], const TcArgs &a, cud
 }
 
 // Workspace: [err | product F split (2 x N x Qp BF16) | objective: W split
-// (2 x Pp x 64) | H^T split (2 x Qp x 64) | per-CTA partials].
+// (2 x Pp x 64) | per-CTA partials | contraction-split partials].
 struct TcWork {
-    size_t f_off, w_off, h_off, part_off, split_off, total;
+    size_t f_off, w_off, part_off, split_off, total;
 };
 
 constexpr int TC_MAX_SPLITS = 4;
@@ -859,9 +901,6 @@ TcWork tc_work(int64_t m, int64_t n, int k, int trans, bool obj)
     w.w_off = off;
     if (obj)
         off += al(2 * sizeof(__nv_bfloat16) * (size_t)Pp * 64);
-    w.h_off = off;
-    if (obj)
-        off += al(2 * sizeof(__nv_bfloat16) * (size_t)Qp * 64);
     w.part_off = off;
     if (obj)
         off += al(sizeof(double) * (size_t)(Pp / TC_BM));
@@ -881,16 +920,16 @@ size_t mm_tc_work_bytes(int64_t m, int64_t n, int k, int trans)
     return a > b ? a : b;
 }
 
-// Products, and with W / Ht / f_dev given (trans = 0, k <= 64) the fused
-// objective f(W, H) written to *f_dev.
+// Products, and with W / f_dev given (trans = 0, k <= 64) the fused
+// objective f(W, H) with H^T = F written to *f_dev.
 nmf_status launch_mm_tc_obj(const float *A, int64_t m, int64_t n, int64_t lda, const float *F,
-                            int k, int trans, float *out, const float *W, const float *Ht,
-                            double *f_dev, void *work, size_t work_bytes, cudaStream_t s)
+                            int k, int trans, float *out, const float *W, double *f_dev,
+                            void *work, size_t work_bytes, cudaStream_t s)
 {
     const int64_t P = trans ? n : m;
     const int64_t Q = trans ? m : n;
     const bool obj = f_dev != nullptr;
-    if (obj && (trans != 0 || k > 64 || !W || !Ht))
+    if (obj && (trans != 0 || k > 64 || !W))
         return NMF_ERR_INVALID_ARG;
     if (P == 0 || Q == 0) {
         if (P > 0 && cudaMemsetAsync(out, 0, sizeof(float) * (size_t)P * k, s) != cudaSuccess)
@@ -911,7 +950,7 @@ nmf_status launch_mm_tc_obj(const float *A, int64_t m, int64_t n, int64_t lda, c
     int *err = reinterpret_cast<int *>(wb);
     NMF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     __nv_bfloat16 *bhi = reinterpret_cast<__nv_bfloat16 *>(wb + wl.f_off);
-    CUtensorMap maps[7];
+    CUtensorMap maps[5];
     bool ok = trans == 0
                   ? make_map_2d(&maps[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)Q,
                                 (uint64_t)P, (uint64_t)lda * 4, 32, TC_BM,
@@ -931,23 +970,15 @@ nmf_status launch_mm_tc_obj(const float *A, int64_t m, int64_t n, int64_t lda, c
     if (obj) {
         __nv_bfloat16 *whi = reinterpret_cast<__nv_bfloat16 *>(wb + wl.w_off);
         __nv_bfloat16 *wlo = whi + (size_t)Pp * 64;
-        __nv_bfloat16 *hhi = reinterpret_cast<__nv_bfloat16 *>(wb + wl.h_off);
-        __nv_bfloat16 *hlo = hhi + (size_t)Qp * 64;
         mm_tc_split_rows_kernel<<<(unsigned)cdiv(Pp * 64, 256), 256, 0, s>>>(W, P, k, Pp, whi, wlo);
-        NMF_LAUNCHED("mm_tc_split_rows_kernel");
-        mm_tc_split_rows_kernel<<<(unsigned)cdiv(Qp * 64, 256), 256, 0, s>>>(Ht, Q, k, Qp, hhi, hlo);
         NMF_LAUNCHED("mm_tc_split_rows_kernel");
         if (!make_map_2d(&maps[3], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, whi, 64, (uint64_t)Pp, 128,
                          64, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
             !make_map_2d(&maps[4], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, wlo, 64, (uint64_t)Pp, 128,
-                         64, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
-            !make_map_2d(&maps[5], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, hhi, 64, (uint64_t)Qp, 128,
-                         64, 64, CU_TENSOR_MAP_SWIZZLE_128B) ||
-            !make_map_2d(&maps[6], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, hlo, 64, (uint64_t)Qp, 128,
-                         64, 64, CU_TENSOR_MAP_SWIZZLE_128B))
+                         64, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B))
             return NMF_ERR_CUDA;
     } else {
-        maps[3] = maps[4] = maps[5] = maps[6] = maps[0];   // unused
+        maps[3] = maps[4] = maps[0];   // unused
     }
     for (int col0 = 0; col0 < k; col0 += 64) {
         const int kc = k - col0 < 64 ? k - col0 : 64;
@@ -995,8 +1026,8 @@ nmf_status launch_mm_tc(const float *A, int64_t m, int64_t n, int64_t lda, const
                         int k, int trans, float *out, void *work, size_t work_bytes,
                         cudaStream_t s)
 {
-    return launch_mm_tc_obj(A, m, n, lda, F, k, trans, out, nullptr, nullptr, nullptr, work,
-                            work_bytes, s);
+    return launch_mm_tc_obj(A, m, n, lda, F, k, trans, out, nullptr, nullptr, work, work_bytes,
+                            s);
 }
 
 }  // namespace nmf
