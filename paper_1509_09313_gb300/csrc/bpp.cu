@@ -12,9 +12,15 @@
 // GPU design (differs from the paper's column grouping; same result):
 //  * bpp_prep_kernel (one CTA, FP64) factors the usable part of G once per
 //    half-step (G = L L^T; indices with G_ii <= 0 are never passive), forms
-//    M = G^{-1} and cond_1(G) = ||G||_1 ||M||_1, and picks the arithmetic of
-//    the solves: FP32 when cond_1(G) <= 1e4 (mode 0), FP64 otherwise (mode 1),
-//    FP64 without M when G is numerically singular (mode 2).
+//    M = G^{-1} and the condition number cond_1(S G S) = ||S G S||_1
+//    ||S^-1 M S^-1||_1 of G with its diagonal scaled to one (S = diag(G)^-1/2),
+//    and picks the arithmetic of the solves: FP32 when it is <= 1e4 (mode 0),
+//    FP64 otherwise (mode 1), FP64 without M when G is numerically singular
+//    (mode 2). The scaled number is the one that bounds the FP32 error: every
+//    FP32 step here (rounding G and M, Cholesky, the matrix-vector products)
+//    perturbs entry (i, j) relative to sqrt(G_ii G_jj), so a factor that is
+//    merely badly scaled (one row of H much smaller than the rest, common in
+//    early iterations) costs nothing.
 //  * bpp_solve_kernel: persistent, one warp per right-hand side, G and M in
 //    shared memory. Lane l holds indices l, l+32, ... of g, x, y and of the
 //    unconstrained solution u = M g. Each exchange round solves the smaller of
@@ -25,12 +31,15 @@
 //    by a warp-cooperative Cholesky in shared memory with shuffle-broadcast
 //    substitutions. In FP32 it then refines once (residual g_F - G_FF x_F
 //    solved through the same factor: the explicit inverse alone is not
-//    backward stable) and recomputes y from G; in FP64 neither is needed. Cost per round O(min(|F|,|A|)^3 + k |F|) instead of
-//    O(|F|^3). In FP32 a pivot below 1e-4 of its diagonal sends that system to
-//    FP64, and a sign test counts as violated only beyond 2^-20 of the
-//    problem's scale (max |x| on F, max |g| off F): values within FP32 noise
-//    of zero are degenerate ties that would otherwise make the exchange rules
-//    cycle. The final x is clamped at 0 there. FP64 modes use the strict test.
+//    backward stable) and recomputes y from G; in FP64 neither is needed.
+//    Cost per round O(min(|F|,|A|)^3 + k |F|) instead of O(|F|^3). In FP32 a
+//    pivot below 1e-4 of its diagonal sends that system to FP64, and a sign
+//    test counts as violated only beyond 2^-20 of the problem's scale in the
+//    diagonally scaled variables (x_i sqrt(G_ii) against max over F of
+//    |x_j| sqrt(G_jj); y_i / sqrt(G_ii) against max of |g_j| / sqrt(G_jj)):
+//    values within FP32 noise of zero are degenerate ties that would
+//    otherwise make the exchange rules cycle. The final x is clamped at 0
+//    there. FP64 modes use the strict test.
 //  * Every loop is bounded: a solve stops at max_rounds with status
 //    NOT_CONVERGED; there are no spin-waits.
 //
@@ -48,7 +57,7 @@ constexpr int BPP_THREADS = BPP_WARPS * 32;
 constexpr int RHS_CHUNK = 8;
 constexpr float PIVOT_TOL = 1e-4f;
 constexpr double PIVOT_TOL64 = 1e-13;
-constexpr double COND_FP32 = 1e4;          // cond_1(G) up to which solves run in FP32
+constexpr double COND_FP32 = 1e4;          // scaled cond_1(G) up to which solves run in FP32
 constexpr float FEAS_TOL32 = 9.5367431640625e-07f;   // 2^-20
 
 // Workspace layout (bytes, 256-aligned pieces).
@@ -72,7 +81,7 @@ WorkLayout layout(int k)
 }
 
 // ---------------------------------------------------------------------------
-// Prep: FP64 Cholesky of G_UU, its inverse and cond_1; one CTA.
+// Prep: FP64 Cholesky of G_UU, its inverse and the scaled cond_1; one CTA.
 // flags[0] = mode (0 FP32, 1 FP64 with M, 2 FP64 without M), flags[1] = |U|.
 // ---------------------------------------------------------------------------
 constexpr int PREP_THREADS = 256;
@@ -85,7 +94,8 @@ __global__ void __launch_bounds__(PREP_THREADS)
 {
     extern __shared__ double sm[];
     double *L = sm;                                   // u x u, later M (u x u)
-    int *uidx = reinterpret_cast<int *>(L + k * k);   // k
+    double *dsq = L + k * k;                          // sqrt(G_aa), a < u
+    int *uidx = reinterpret_cast<int *>(dsq + k);     // k
     __shared__ int s_u, s_ok;
     __shared__ unsigned long long s_norm[2];
     const int tid = threadIdx.x;
@@ -174,14 +184,20 @@ __global__ void __launch_bounds__(PREP_THREADS)
         L[a * u + b] = s;
     }
     __syncthreads();
-    // cond_1 = max column sum of |G_UU| times max column sum of |M|. Non-negative
-    // doubles order like their bit patterns, so an integer max reduces them.
+    // Scaled cond_1 = max column sum of |G_ac| / (d_a d_c) times max column
+    // sum of |M_ac| d_a d_c, d_a = sqrt(G_aa). Non-negative doubles order like
+    // their bit patterns, so an integer max reduces them.
+    for (int a = tid; a < u; a += PREP_THREADS)
+        dsq[a] = sqrt(G[uidx[a] * k + uidx[a]]);
+    __syncthreads();
     for (int c = tid; c < u; c += PREP_THREADS) {
         double sg = 0.0, sm2 = 0.0;
         for (int a = 0; a < u; ++a) {
-            sg += fabs(G[uidx[a] * k + uidx[c]]);
-            sm2 += fabs(L[a * u + c]);
+            sg += fabs(G[uidx[a] * k + uidx[c]]) / dsq[a];
+            sm2 += fabs(L[a * u + c]) * dsq[a];
         }
+        sg /= dsq[c];
+        sm2 *= dsq[c];
         atomicMax(&s_norm[0], (unsigned long long)__double_as_longlong(sg));
         atomicMax(&s_norm[1], (unsigned long long)__double_as_longlong(sm2));
     }
@@ -426,6 +442,16 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
         nU += __popc(w);
     }
     const T tolrel = MODE == 0 ? (T)FEAS_TOL32 : (T)0;
+    // sqrt(G_ii) of this lane's indices (1 where unusable): the scale of the
+    // FP32 sign tolerances.
+    T dsq[KW];
+#pragma unroll
+    for (int s = 0; s < KW; ++s) {
+        const int i = lane + 32 * s;
+        dsq[s] = (T)1;
+        if (MODE == 0 && usable[s] && i < k)
+            dsq[s] = sqrt(Gs[i * k + i]);
+    }
 
     unsigned long long st_rounds = 0, st_max = 0, st_fp64 = 0, st_nc = 0, st_sing = 0,
                        st_nf = 0, st_rhs = 0;
@@ -448,7 +474,7 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                 const int i = lane + 32 * s;
                 g[s] = i < k ? (T)P.B[j * k + i] : (T)0;
                 bad |= !isfinite(g[s]);
-                gmax = max(gmax, fabs(g[s]));
+                gmax = max(gmax, fabs(g[s]) / dsq[s]);
                 u[s] = 0;
                 x[s] = 0;
                 y[s] = -g[s];
@@ -651,7 +677,7 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                     T xm = 0;
 #pragma unroll
                     for (int s = 0; s < KW; ++s)
-                        xm = max(xm, inF[s] ? fabs(x[s]) : (T)0);
+                        xm = max(xm, inF[s] ? fabs(x[s]) * dsq[s] : (T)0);
                     if (MODE != 0 && comp) {
 #pragma unroll
                         for (int s = 0; s < KW; ++s)
@@ -666,7 +692,7 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                         for (int s = 0; s < KW; ++s)
                             y[s] = inF[s] ? (T)0 : w[s] - g[s];
                     }
-                    xtol = tolrel * warp_max(xm);
+                    xtol = tolrel * warp_max(xm);   // scaled: compares x_i * d_i
                     return NMF_OK;
                 };
 
@@ -683,7 +709,8 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                     int nV = 0;
 #pragma unroll
                     for (int s = 0; s < KW; ++s) {
-                        inf[s] = usable[s] && (inF[s] ? (x[s] < -xtol) : (y[s] < -ytol));
+                        inf[s] = usable[s] && (inF[s] ? (x[s] * dsq[s] < -xtol)
+                                                      : (y[s] < -ytol * dsq[s]));
                         vm[s] = __ballot_sync(FULL, inf[s]);
                         nV += __popc(vm[s]);
                     }
@@ -853,7 +880,7 @@ nmf_status launch_bpp(int k, int64_t nrhs, const double *G, const float *B, floa
     P.counter = reinterpret_cast<unsigned long long *>(w + L.counter);
     P.stats = stats_dev;
 
-    const size_t prep_smem = sizeof(double) * (size_t)k * k + sizeof(int) * (size_t)k;
+    const size_t prep_smem = sizeof(double) * ((size_t)k * k + k) + sizeof(int) * (size_t)k;
     static int prep_configured = 0;
     if ((int)prep_smem > 48 * 1024 && (int)prep_smem > prep_configured) {
         NMF_CUDA(cudaFuncSetAttribute(bpp_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
