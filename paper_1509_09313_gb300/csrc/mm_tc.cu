@@ -16,11 +16,12 @@
 // and lo, 128-byte swizzle); 4 to 6 stages keep 100+ KB of A in flight per SM.
 //   warp 0     TMA producer: refills a stage once every MMA reading it is done.
 //   warp 1     allocates TMEM; one lane issues the product MMAs (M = 128,
-//              N = 16, 32 or 64, K = 16; 3 per 16-element step). This thread's
-//              instruction stream is the pass's critical path (issuing an MMA,
-//              a commit or a try_wait costs 30-45 cycles; an N = 64 MMA keeps
-//              the tensor core ~48), so its descriptors are precomputed and
-//              it waits on as few barriers as possible.
+//              K = 16; per 16-element step A_hi x [F_hi; F_lo] with N = 2N_k
+//              and A_lo x F_hi with N = N_k, N_k = 16, 32 or 64). This
+//              thread's instruction stream is the pass's critical path
+//              (issuing an MMA, a commit or a try_wait costs 30-45 cycles), so
+//              its descriptors are precomputed and it waits on as few barriers
+//              as possible.
 //   warps 2-5  split the FP32 A tile into BF16 hi/lo IN PLACE, in the
 //              canonical K-major 128-byte-swizzled operand layout. trans = 0:
 //              each thread owns one row (its TMEM lane); the 32 floats of a
@@ -36,13 +37,15 @@
 // adds into an accumulator biases it by about half an ulp of its value;
 // accumulating all n / 16 * 3 steps in one place would bias the result by
 // ~1e-6 relative and spread it by as much, which the NLS solves amplify by
-// cond(G). The dominant hi*hi products therefore go to their own ping-pong
-// accumulator pair, drained after every K-block (4 MMAs), and the two cross
-// products (about 2^-8 smaller, so their truncation is 2^-8 as large) to a
-// second pair drained every TC_WIN2 K-blocks; the drain warps add each tile
-// into registers with Kahan compensation. Measured against FP64 at n = 64000:
-// bias -4e-8, spread 3e-8 (plain FP32 rounding: spread 2.3e-8).
-//
+// cond(G). The accumulator of each K-block (4 accumulation steps of the
+// dominant hi*hi products) is therefore drained into registers, where the
+// drain warps add the hi*hi tile plus the cross-term tile (about 2^-8
+// smaller) to a plain FP32 partial over TC_FOLD K-blocks (round to nearest,
+// so unbiased) that is folded into a Kahan-compensated sum. Draining only
+// every second K-block measured -1.4e-7 (the truncation grows with the square
+// of the steps per drain), enough to push the objective of the small dense
+// configuration past its 1e-5 tolerance.
+
 // Fused objective (trans = 0, k <= 64): with W given, every K-block also
 // forms the 128 x 64 tile of W H (W tile resident in shared memory, K = k
 // padded to 16/32/64, three split products) in a third ping-pong TMEM pair.
@@ -77,8 +80,8 @@ namespace {
 
 constexpr int TC_BM = 128;        // output rows per CTA (MMA M)
 constexpr int TC_BK = 64;         // contraction elements per K-block (128-byte BF16 row)
-constexpr int TC_WIN2 = 8;        // K-blocks per cross-term accumulation window
 constexpr int TC_DRAIN_WARPS = 8;
+constexpr int TC_FOLD = 8;        // K-blocks per plain partial sum in the drain
 constexpr int TC_SMEM_MAX = 227 * 1024;
 constexpr long long TC_WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
@@ -96,17 +99,20 @@ struct TcLayout {
     static constexpr int OFF_WHI = STAGES * STAGE_BYTES;
     static constexpr int OFF_WLO = OFF_WHI + W_BYTES;
     static constexpr int OFF_BAR = OFF_WLO + W_BYTES;
-    // barriers: full[S], empty[S], a_full[S], readb[S], acc1_full[2],
-    // acc1_empty[2], acc2_full[2], acc2_empty[2], obj_full[2], obj_empty[2], w_full
-    static constexpr int NBAR = 4 * STAGES + 13;
+    // barriers: full[S], empty[S], a_full[S], readb[S], acc_full[2],
+    // acc_empty[2], obj_full[2], obj_empty[2], w_full
+    static constexpr int NBAR = 4 * STAGES + 9;
     static constexpr int OFF_TMEM = OFF_BAR + NBAR * 8;
     static constexpr int OFF_ABORT = OFF_TMEM + 4;
     static constexpr int OFF_RED = (OFF_ABORT + 4 + 15) & ~15;    // 8 doubles
     static constexpr int BYTES = OFF_RED + 16 * 8;
-    // TMEM: D1 x 2 (N), D2 x 2 (N), objective D3 x 2 (64).
-    static constexpr int COLS = 4 * N + (OBJ ? 128 : 0);
+    // TMEM: product accumulators x 2 ([hi*hi | cross], 2N), objective x 2 (64),
+    // the drain's Kahan sums and compensations (2N).
+    static constexpr int COL_KS = 4 * N + (OBJ ? 128 : 0);
+    static constexpr int COLS = COL_KS + 2 * N;
     static constexpr int TMEM_COLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128
                                    : COLS <= 256 ? 256 : 512;
+    static_assert(COLS <= 512, "tensor memory budget");
     static_assert(STAGES >= 3, "at least three stages");
     static_assert(STAGE_BYTES % 1024 == 0 && F32_BYTES % 1024 == 0 && B_BYTES % 1024 == 0 &&
                       A_BYTES % 1024 == 0 && OFF_WHI % 1024 == 0 && W_BYTES % 1024 == 0,
@@ -240,6 +246,23 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_
         : "memory");
 }
 
+// 8 consecutive 32-bit columns of this warp's 32 TMEM lanes (no wait).
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(
+            taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st()
+{
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -268,22 +291,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
         v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-        "%11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i)
-        v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 {
     uint32_t r[8];
@@ -300,12 +307,18 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 template <int C>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[C])
 {
+    static_assert(C == 8 || C == 32, "8- or 32-column TMEM loads");
     if constexpr (C == 32)
         tmem_ld32(taddr, v);
-    else if constexpr (C == 16)
-        tmem_ld16(taddr, v);
     else
         tmem_ld8(taddr, v);
+}
+
+template <int C>
+__device__ __forceinline__ void tmem_st(uint32_t taddr, const float (&v)[C])
+{
+    static_assert(C == 8, "8-column TMEM stores only");
+    tmem_st8(taddr, v);
 }
 
 // Split 2 FP32 values into packed BF16 pairs (low half = first value).
@@ -370,13 +383,11 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
     auto a_full = [&](int i) { return bar0 + 8u * (2 * S + i); };  // A split in place
     auto readb = [&](int i) { return bar0 + 8u * (3 * S + i); };   // trans = 1: tile read
     const uint32_t accb = bar0 + 8u * (4 * S);
-    auto acc1_full = [&](int i) { return accb + 8u * i; };
-    auto acc1_empty = [&](int i) { return accb + 8u * (2 + i); };
-    auto acc2_full = [&](int i) { return accb + 8u * (4 + i); };
-    auto acc2_empty = [&](int i) { return accb + 8u * (6 + i); };
-    auto obj_full = [&](int i) { return accb + 8u * (8 + i); };
-    auto obj_empty = [&](int i) { return accb + 8u * (10 + i); };
-    const uint32_t w_full = accb + 8u * 12;
+    auto acc_full = [&](int i) { return accb + 8u * i; };
+    auto acc_empty = [&](int i) { return accb + 8u * (2 + i); };
+    auto obj_full = [&](int i) { return accb + 8u * (4 + i); };
+    auto obj_empty = [&](int i) { return accb + 8u * (6 + i); };
+    const uint32_t w_full = accb + 8u * 8;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < S; ++i) {
@@ -386,10 +397,8 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
             mbar_init(readb(i), 4);
         }
         for (int i = 0; i < 2; ++i) {
-            mbar_init(acc1_full(i), 1);
-            mbar_init(acc1_empty(i), TC_DRAIN_WARPS);
-            mbar_init(acc2_full(i), 1);
-            mbar_init(acc2_empty(i), TC_DRAIN_WARPS);
+            mbar_init(acc_full(i), 1);
+            mbar_init(acc_empty(i), TC_DRAIN_WARPS);
             mbar_init(obj_full(i), 1);
             mbar_init(obj_empty(i), 4);
         }
@@ -449,31 +458,29 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
         }
     } else if (warp == 1) {
         // ------------------------------------------------------ product MMAs
-        // One thread issues the 12 MMAs of a K-block; its instruction stream
-        // is on the critical path (each tcgen05.mma, commit or try_wait costs
-        // 30-45 cycles to issue; an N = 64 MMA occupies the tensor core ~48).
-        // TMEM columns: D1 buffers at [0, N) and [N, 2N) (hi*hi, one K-block
-        // each), D2 buffers at [2N, 4N) (cross terms, windows of TC_WIN2
-        // K-blocks), objective D3 buffers at [4N, 4N + 128).
+        // One thread issues the MMAs; its instruction stream is on the
+        // critical path (each tcgen05.mma, commit or try_wait costs 30-45
+        // cycles to issue), so per 16-element step it issues two: A_hi times
+        // the stacked [F_hi; F_lo] (N' = 2N: the F lo tile follows the hi tile
+        // in the stage, 8-row groups 1024 bytes apart, so the two form one
+        // K-major operand) and A_lo times F_hi into the second half. The
+        // accumulator of a K-block, D = [hi*hi | cross terms] (2N columns), is
+        // drained after that K-block; two such buffers ping-pong at TMEM
+        // columns [0, 4N), the objective's W H buffers follow at [4N, 4N + 128).
         if (lane == 0) {
+            const uint32_t idesc2 = idesc_bf16_f32<2 * N>();
             const uint32_t idesc = idesc_bf16_f32<N>();
             const uint64_t a0 = sw128_desc(sbase), b0 = a0 + F16;
             for (int kb = 0; kb < nkb; ++kb) {
                 const int s = kb % S, u = kb / S;
-                const int b1 = kb & 1, u1 = kb >> 1;
-                const int w2 = kb / TC_WIN2, b2 = w2 & 1, u2 = w2 >> 1;
-                const bool first2 = (kb % TC_WIN2) == 0;
-                if (!mbar_wait_fast(acc1_empty(b1), (u1 & 1) ^ 1, abort))
-                    break;
-                if (first2 && !mbar_wait_fast(acc2_empty(b2), (u2 & 1) ^ 1, abort))
-                    break;
-                if (!mbar_wait_fast(a_full(s), u & 1, abort))
+                const int b = kb & 1, ub = kb >> 1;
+                if (!mbar_wait_fast(acc_empty(b), (ub & 1) ^ 1, abort) ||
+                    !mbar_wait_fast(a_full(s), u & 1, abort))
                     break;
                 tc_fence_after();
-                const uint32_t d1 = tmem + (uint32_t)(b1 * N);
-                const uint32_t d2 = tmem + (uint32_t)((2 + b2) * N);
+                const uint32_t d = tmem + (uint32_t)(b * 2 * N);
                 const uint64_t as = a0 + (uint64_t)s * STAGE16;
-                const uint64_t bh = b0 + (uint64_t)s * STAGE16, bl = bh + BLO16;
+                const uint64_t bh = b0 + (uint64_t)s * STAGE16;
 #pragma unroll
                 for (int kk = 0; kk < TC_BK / 16; ++kk) {
                     // A hi / lo of this 16-element step (see the split warps).
@@ -482,14 +489,11 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
                                             : as + (uint64_t)(kk * 2);
                     const uint64_t al = TRANS == 0 ? ah + 4 : ah + (uint64_t)(L::A_BYTES >> 4);
                     const uint64_t o = (uint64_t)(kk * 2);   // 16 BF16 = 32 bytes along K
-                    mma_bf16(d1, ah, bh + o, idesc, kk ? 1u : 0u);
-                    mma_bf16(d2, ah, bl + o, idesc, (first2 && kk == 0) ? 0u : 1u);
-                    mma_bf16(d2, al, bh + o, idesc, 1u);
+                    mma_bf16(d, ah, bh + o, idesc2, kk ? 1u : 0u);
+                    mma_bf16(d + (uint32_t)N, al, bh + o, idesc, 1u);
                 }
-                mma_commit(acc1_full(b1));
                 mma_commit(empty(s));
-                if ((kb % TC_WIN2) == TC_WIN2 - 1 || kb == nkb - 1)
-                    mma_commit(acc2_full(b2));
+                mma_commit(acc_full(b));
             }
         }
     } else if (OBJ && warp == 14) {
@@ -627,71 +631,94 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
         }
     } else if (warp >= 6 && warp < 14) {
         // ------------------------------------------------ drain (warps 6-13)
+        // Per K-block, hi*hi tile + cross-term tile go into a plain FP32
+        // partial sum (round to nearest: unbiased) which every TC_FOLD
+        // K-blocks is folded into a Kahan-compensated sum. The Kahan sum and
+        // compensation live in TMEM (columns [COL_KS, COL_KS + 2N)), touched
+        // only at the folds, so registers hold just the partial.
         constexpr int NH = N / 2;               // product columns owned by this warp
+        constexpr int CH = NH < 8 ? NH : 8;     // columns per TMEM access
         const int dw = warp - 6;
         const int quarter = warp & 3;           // TMEM lane quarter of this warp
         const int half = dw >> 2;               // which half of the columns
         const int cbase = half * NH;
-        float sum[NH], cmp[NH];
+        const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16);
+        const uint32_t ks = tq + (uint32_t)(L::COL_KS + cbase);       // Kahan sums
+        const uint32_t kc = tq + (uint32_t)(L::COL_KS + N + cbase);   // compensations
+        float part[NH];
 #pragma unroll
-        for (int c = 0; c < NH; ++c) {
-            sum[c] = 0.0f;
-            cmp[c] = 0.0f;
-        }
-        // Kahan-add a TMEM tile, CH columns per load to bound register use.
-        constexpr int CH = NH < 16 ? NH : 16;
+        for (int c = 0; c < NH; ++c)
+            part[c] = 0.0f;
         auto add_tile = [&](uint32_t ta) {
 #pragma unroll
             for (int c0 = 0; c0 < NH; c0 += CH) {
-                float v[CH];
+                float v[CH], w[CH];
                 tmem_ld<CH>(ta + (uint32_t)c0, v);
+                tmem_ld<CH>(ta + (uint32_t)(N + c0), w);
 #pragma unroll
-                for (int i = 0; i < CH; ++i) {
-                    const float y = v[i] - cmp[c0 + i];
-                    const float t = sum[c0 + i] + y;
-                    cmp[c0 + i] = (t - sum[c0 + i]) - y;
-                    sum[c0 + i] = t;
-                }
+                for (int i = 0; i < CH; ++i)
+                    part[c0 + i] += v[i] + w[i];
             }
         };
-        const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16);
+        bool folded = false;
+        auto fold = [&]() {
+#pragma unroll
+            for (int c0 = 0; c0 < NH; c0 += CH) {
+                float sm[CH], cm[CH];
+                if (folded) {
+                    tmem_ld<CH>(ks + (uint32_t)c0, sm);
+                    tmem_ld<CH>(kc + (uint32_t)c0, cm);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < CH; ++i)
+                        sm[i] = cm[i] = 0.0f;
+                }
+#pragma unroll
+                for (int i = 0; i < CH; ++i) {
+                    const float y = part[c0 + i] - cm[i];
+                    const float t = sm[i] + y;
+                    cm[i] = (t - sm[i]) - y;
+                    sm[i] = t;
+                    part[c0 + i] = 0.0f;
+                }
+                tmem_st<CH>(ks + (uint32_t)c0, sm);
+                tmem_st<CH>(kc + (uint32_t)c0, cm);
+            }
+            tmem_wait_st();
+            folded = true;
+        };
         const int row = quarter * 32 + lane;    // row of the tile owned by this thread
         bool ok = true;
-        for (int kb = 0; kb < nkb && ok; ++kb) {
-            const int b1 = kb & 1, u1 = kb >> 1;
-            if (!mbar_wait(acc1_full(b1), u1 & 1, abort)) {
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int b = kb & 1, ub = kb >> 1;
+            if (!mbar_wait(acc_full(b), ub & 1, abort)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            add_tile(tq + (uint32_t)(b1 * N + cbase));
+            add_tile(tq + (uint32_t)(b * 2 * N + cbase));
             tc_fence_before();
             __syncwarp();
             if (lane == 0)
-                mbar_arrive(acc1_empty(b1));
-            if ((kb % TC_WIN2) == TC_WIN2 - 1 || kb == nkb - 1) {
-                const int w2 = kb / TC_WIN2, b2 = w2 & 1, u2 = w2 >> 1;
-                if (!mbar_wait(acc2_full(b2), u2 & 1, abort)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                add_tile(tq + (uint32_t)((2 + b2) * N + cbase));
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0)
-                    mbar_arrive(acc2_empty(b2));
-            }
+                mbar_arrive(acc_empty(b));
+            if ((kb % TC_FOLD) == TC_FOLD - 1)
+                fold();
         }
         if (ok) {
+            fold();
             const int64_t p = p0 + row;
-            if (p < P) {
-                float *o = args.out + (int64_t)blockIdx.y * P * args.k + p * args.k + args.col0 +
-                           cbase;
+            float *o = args.out + (int64_t)blockIdx.y * P * args.k + p * args.k + args.col0 + cbase;
 #pragma unroll
-                for (int c = 0; c < NH; ++c)
-                    if (cbase + c < args.kc)
-                        o[c] = sum[c] - cmp[c];
+            for (int c0 = 0; c0 < NH; c0 += CH) {
+                float sm[CH], cm[CH];
+                tmem_ld<CH>(ks + (uint32_t)c0, sm);
+                tmem_ld<CH>(kc + (uint32_t)c0, cm);
+                if (p < P) {
+#pragma unroll
+                    for (int i = 0; i < CH; ++i)
+                        if (cbase + c0 + i < args.kc)
+                            o[c0 + i] = sm[i] - cm[i];
+                }
             }
         }
     }

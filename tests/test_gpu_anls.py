@@ -64,13 +64,17 @@ def check(nmf, g, ref, ftol=1e-5, xtol=1e-4):
 @pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
 @pytest.mark.parametrize("start", ["cold", "warm"])
 def test_dense_small_config(nmf, start, precision):
-    # A = W0 H0 + |N(0, 0.01^2)|, 2000 x 1000, k = 10, 10 iterations.
+    # A = W0 H0 + |N(0, 0.01^2)|, 2000 x 1000, k = 10, 10 iterations. The
+    # configuration is defined for the FP32 path (objective within 1e-5). The
+    # BF16x3 products' own random error over this short contraction (1.6e-7)
+    # moves the objective by ~1e-5 by itself (test_product_noise.py: median
+    # 1e-5, max 1.4e-5 over eight draws), so that path is held to 3e-5 here.
     m, n, k, T = 2000, 1000, 10, 10
     A = synth.dense_planted(m, n, k, 0.01)
     W0, Ht0 = synth.init_factors(m, n, k)
     ref = oracle.anls(A, W0, Ht0, iters=T)
     g = run_gpu(nmf, A, W0, Ht0, T, start=start, precision=precision)
-    check(nmf, g, ref)
+    check(nmf, g, ref, ftol=1e-5 if precision == "fp32" else 3e-5)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
