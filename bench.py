@@ -45,8 +45,15 @@ FP32_LANES_PER_SM = 128
 
 # DRAM traffic per launch (read + write bytes) of the dominant kernel from one
 # ncu capture, keyed by (kernel, workload, precision); None until captured or
-# when the kernel changed since.
-NCU_TRAFFIC = {}
+# when the kernel changed since. dense-large: the two mm_tc_kernel launches of
+# an iteration captured on the 24000 x 16000 case (A H^T with the objective:
+# 1.5505 GB read + 7.1 MB written; A^T W: 1.5422 GB + 3.2 MB), scaled by the
+# element ratio 16 and averaged: 24.83 GB per launch against 24.61 GB of
+# algorithmic bytes (profiles/mm_tc_kernel_dense-medium.md).
+NCU_TRAFFIC = {
+    ("mm_tc_kernel", "dense-large", "bf16x3"): 24.83e9,
+    ("mm_tc_kernel", "dense-medium", "bf16x3"): 1.5516e9,
+}
 
 
 def env_int(name, default):
@@ -195,7 +202,12 @@ def run_ours(args, rank, world, local_rank):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    nvtx = getattr(torch.cuda, "nvtx", None)
+    if nvtx is not None:
+        nvtx.range_push("timed")    # lets ncu select exactly the timed launches
     h.nmf_iterate(args.steps)
+    if nvtx is not None:
+        nvtx.range_pop()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
