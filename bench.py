@@ -308,7 +308,10 @@ def run_ours(args, rank, world, local_rank):
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
-                "phase_ms_per_launch": {"mm": mm_ms, "nls": nls_ms, "gram": gram_ms,
+                # "gram_prep_side": Gram + BPP preparation on the handle's side
+                # stream, fork to finish; it overlaps the products (so it also
+                # counts time queued behind them) and is not part of the step sum.
+                "phase_ms_per_launch": {"mm": mm_ms, "nls": nls_ms, "gram_prep_side": gram_ms,
                                         "objective": obj_ms},
                 "bpp": {"rounds_per_rhs": rounds / max(rhs, 1),
                         "fp64_solves": st1["bpp_fp64_solves"] - st0["bpp_fp64_solves"],

@@ -198,6 +198,11 @@ struct nmf_handle {
     nmf_config cfg;
     nmf_matrix A;
     cudaStream_t stream;
+    // Side stream for each half-step's Gram and BPP preparation, which depend
+    // only on the other factor and so run beside the m x n x k product (in
+    // the SMs its last wave leaves idle); fork / join events order them.
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int nwords;
     // Owned device buffers.
     float *W = nullptr, *Ht = nullptr;          // factors (m x k, n x k)
@@ -258,19 +263,21 @@ cudaEvent_t take_event(nmf_handle *h)
 struct PhaseTimer {
     nmf_handle *h;
     int phase;
+    cudaStream_t s;
     cudaEvent_t a = nullptr;
-    PhaseTimer(nmf_handle *hh, int ph) : h(hh), phase(ph)
+    PhaseTimer(nmf_handle *hh, int ph, cudaStream_t st = nullptr)
+        : h(hh), phase(ph), s(st ? st : hh->stream)
     {
         if (h->timing) {
             a = take_event(h);
-            cudaEventRecord(a, h->stream);
+            cudaEventRecord(a, s);
         }
     }
     ~PhaseTimer()
     {
         if (h->timing) {
             cudaEvent_t b = take_event(h);
-            cudaEventRecord(b, h->stream);
+            cudaEventRecord(b, s);
             h->pending.push_back({phase, a, b});
         }
     }
@@ -322,11 +329,22 @@ nmf_status one_iteration(nmf_handle *h)
 {
     const nmf_config &c = h->cfg;
     const bool warm = c.start_mode == NMF_START_WARM && h->passive_valid;
+    // Side stream: Gram of the fixed factor, then the BPP preparation of that
+    // Gram (both need only the fixed factor, current on the main stream at the
+    // fork); the main stream runs the product meanwhile and joins before the
+    // solves. The BPP workspace is free again at each fork: the previous
+    // half-step's solves are on the main stream before it.
+    auto fork_prepare = [&](const float *F, int64_t rows, double *G) -> nmf_status {
+        NMF_CUDA(cudaEventRecord(h->ev_fork, h->stream));
+        NMF_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        PhaseTimer t(h, 0, h->side);
+        NMF_TRY(launch_gram(F, rows, c.k, G, h->gram_part, h->side));
+        NMF_TRY(launch_bpp_prep(c.k, G, h->bpp_work, h->stats_dev, h->side));
+        NMF_CUDA(cudaEventRecord(h->ev_join, h->side));
+        return NMF_OK;
+    };
     // W <- argmin_{W >= 0} ||A - W H||: Gram H H^T, right-hand sides A H^T.
-    {
-        PhaseTimer t(h, 0);
-        NMF_TRY(launch_gram(h->Ht, c.n, c.k, h->GH, h->gram_part, h->stream));
-    }
+    NMF_TRY(fork_prepare(h->Ht, c.n, h->GH));
     {
         PhaseTimer t(h, 1);
         if (h->obj_pending) {
@@ -341,22 +359,23 @@ nmf_status one_iteration(nmf_handle *h)
     }
     {
         PhaseTimer t(h, 2);
-        NMF_TRY(launch_bpp(c.k, c.m, h->GH, h->V, h->W, warm ? h->pW : nullptr, h->pW, nullptr,
-                           nullptr, c.max_bpp_rounds, h->bpp_work, h->stats_dev, h->stream));
+        NMF_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+        NMF_TRY(launch_bpp_solve(c.k, c.m, h->GH, h->V, h->W, warm ? h->pW : nullptr, h->pW,
+                                 nullptr, nullptr, c.max_bpp_rounds, h->bpp_work, h->stats_dev,
+                                 h->stream));
     }
     // H <- argmin_{H >= 0} ||A - W H||: Gram W^T W, right-hand sides (W^T A)^T.
-    {
-        PhaseTimer t(h, 0);
-        NMF_TRY(launch_gram(h->W, c.m, c.k, h->GW, h->gram_part, h->stream));
-    }
+    NMF_TRY(fork_prepare(h->W, c.m, h->GW));
     {
         PhaseTimer t(h, 1);
         NMF_TRY(mm(h, 1, h->W, h->Y));
     }
     {
         PhaseTimer t(h, 2);
-        NMF_TRY(launch_bpp(c.k, c.n, h->GW, h->Y, h->Ht, warm ? h->pH : nullptr, h->pH, nullptr,
-                           nullptr, c.max_bpp_rounds, h->bpp_work, h->stats_dev, h->stream));
+        NMF_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+        NMF_TRY(launch_bpp_solve(c.k, c.n, h->GW, h->Y, h->Ht, warm ? h->pH : nullptr, h->pH,
+                                 nullptr, nullptr, c.max_bpp_rounds, h->bpp_work, h->stats_dev,
+                                 h->stream));
     }
     h->passive_valid = true;
     if (c.objective_every) {
@@ -412,6 +431,12 @@ void free_handle(nmf_handle *h)
     }
     for (auto e : h->pool)
         cudaEventDestroy(e);
+    if (h->ev_fork)
+        cudaEventDestroy(h->ev_fork);
+    if (h->ev_join)
+        cudaEventDestroy(h->ev_join);
+    if (h->side)
+        cudaStreamDestroy(h->side);
     delete h;
 }
 
@@ -448,6 +473,12 @@ extern "C" nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nm
     h->A = *A;
     h->stream = as_stream(stream);
     h->nwords = (c.k + 63) / 64;
+    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        free_handle(h);
+        return NMF_ERR_CUDA;
+    }
     const size_t k = (size_t)c.k;
     const int64_t rmax = c.m > c.n ? c.m : c.n;
     cudaError_t e = cudaSuccess;

@@ -853,10 +853,11 @@ nmf_status launch_modes(const SolveParams &P, cudaStream_t s)
 
 size_t bpp_work_bytes(int k) { return layout(k).total; }
 
-nmf_status launch_bpp(int k, int64_t nrhs, const double *G, const float *B, float *X,
-                      const uint64_t *passive_in, uint64_t *passive_out, int32_t *rounds_out,
-                      int8_t *status_out, int max_rounds, void *work, BppStats *stats_dev,
-                      cudaStream_t s)
+namespace {
+
+SolveParams solve_params(int k, int64_t nrhs, const double *G, const float *B, float *X,
+                         const uint64_t *passive_in, uint64_t *passive_out, int32_t *rounds_out,
+                         int8_t *status_out, int max_rounds, void *work, BppStats *stats_dev)
 {
     const WorkLayout L = layout(k);
     unsigned char *w = static_cast<unsigned char *>(work);
@@ -879,7 +880,15 @@ nmf_status launch_bpp(int k, int64_t nrhs, const double *G, const float *B, floa
     P.status_out = status_out;
     P.counter = reinterpret_cast<unsigned long long *>(w + L.counter);
     P.stats = stats_dev;
+    return P;
+}
 
+}  // namespace
+
+nmf_status launch_bpp_prep(int k, const double *G, void *work, BppStats *stats_dev, cudaStream_t s)
+{
+    const SolveParams P = solve_params(k, 0, G, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                       nullptr, 0, work, stats_dev);
     const size_t prep_smem = sizeof(double) * ((size_t)k * k + k) + sizeof(int) * (size_t)k;
     static int prep_configured = 0;
     if ((int)prep_smem > 48 * 1024 && (int)prep_smem > prep_configured) {
@@ -892,8 +901,18 @@ nmf_status launch_bpp(int k, int64_t nrhs, const double *G, const float *B, floa
         const_cast<double *>(P.M64), const_cast<uint32_t *>(P.usable_words),
         const_cast<int *>(P.flags), P.counter, stats_dev);
     NMF_LAUNCHED("bpp_prep_kernel");
+    return NMF_OK;
+}
+
+nmf_status launch_bpp_solve(int k, int64_t nrhs, const double *G, const float *B, float *X,
+                            const uint64_t *passive_in, uint64_t *passive_out, int32_t *rounds_out,
+                            int8_t *status_out, int max_rounds, void *work, BppStats *stats_dev,
+                            cudaStream_t s)
+{
     if (nrhs == 0)
         return NMF_OK;
+    const SolveParams P = solve_params(k, nrhs, G, B, X, passive_in, passive_out, rounds_out,
+                                       status_out, max_rounds, work, stats_dev);
     if (k <= 32)
         return launch_modes<1>(P, s);
     if (k <= 64)
@@ -901,6 +920,16 @@ nmf_status launch_bpp(int k, int64_t nrhs, const double *G, const float *B, floa
     if (k <= 96)
         return launch_modes<3>(P, s);
     return launch_modes<4>(P, s);
+}
+
+nmf_status launch_bpp(int k, int64_t nrhs, const double *G, const float *B, float *X,
+                      const uint64_t *passive_in, uint64_t *passive_out, int32_t *rounds_out,
+                      int8_t *status_out, int max_rounds, void *work, BppStats *stats_dev,
+                      cudaStream_t s)
+{
+    NMF_TRY(launch_bpp_prep(k, G, work, stats_dev, s));
+    return launch_bpp_solve(k, nrhs, G, B, X, passive_in, passive_out, rounds_out, status_out,
+                            max_rounds, work, stats_dev, s);
 }
 
 }  // namespace nmf

@@ -104,5 +104,13 @@ nmf_status launch_bpp(int k, int64_t nrhs, const double *G, const float *B, floa
                       const uint64_t *passive_in, uint64_t *passive_out, int32_t *rounds_out,
                       int8_t *status_out, int max_rounds, void *work, BppStats *stats_dev,
                       cudaStream_t s);
+// The two halves of launch_bpp: the per-Gram preparation (factor, inverse,
+// arithmetic mode), then the solves. A prep must complete before its solves
+// and must not overlap another half-step's prep or solves on the same work.
+nmf_status launch_bpp_prep(int k, const double *G, void *work, BppStats *stats_dev, cudaStream_t s);
+nmf_status launch_bpp_solve(int k, int64_t nrhs, const double *G, const float *B, float *X,
+                            const uint64_t *passive_in, uint64_t *passive_out, int32_t *rounds_out,
+                            int8_t *status_out, int max_rounds, void *work, BppStats *stats_dev,
+                            cudaStream_t s);
 
 }  // namespace nmf
