@@ -206,26 +206,25 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
 }
 
 // Shared-memory matrix descriptor for an MN-major operand with 128-byte
-// swizzle whose MN extent is one swizzle atom (64 BF16 values per 128-byte
-// row, K along the rows): 8-row groups along K are 1024 bytes apart. The
-// stride between atoms along MN is never used at this width; it gets the
-// same 1024 bytes.
-__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t saddr)
+// swizzle: atoms of 64 BF16 values along MN (one 128-byte row) x 8 rows along
+// K; 8-row groups along K are 1024 bytes apart (stride field), atoms along MN
+// lbo bytes apart (leading-dimension field; unused when MN is one atom).
+__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t saddr, uint32_t lbo)
 {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(1024u >> 4) << 16;
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
     d |= (uint64_t)(1024u >> 4) << 32;
     d |= (uint64_t)1 << 46;
     d |= (uint64_t)2 << 61;
     return d;
 }
 
-// Instruction descriptor, kind::f16: BF16 A and B, FP32 D, A K-major; B
-// K-major, or MN-major when B_MN (bit 16).
-template <int N, int B_MN = 0>
+// Instruction descriptor, kind::f16: BF16 A and B, FP32 D; A MN-major when
+// A_MN (bit 15), B MN-major when B_MN (bit 16), K-major otherwise.
+template <int N, int B_MN = 0, int A_MN = 0>
 __device__ __forceinline__ uint32_t idesc_bf16_f32()
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)B_MN << 16) |
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)A_MN << 15) | ((uint32_t)B_MN << 16) |
            ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
 }
 
@@ -270,10 +269,10 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
                  : "memory");
 }
 
-// Consecutive FP32 columns of this warp's 32 TMEM lanes.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+// Consecutive FP32 columns of this warp's 32 TMEM lanes, without waiting:
+// the values are valid after tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[32])
 {
-    uint32_t r[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
         "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
@@ -285,10 +284,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
           "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
           "=r"(r[31])
         : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld()
+{
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-        v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
@@ -307,11 +307,8 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 template <int C>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[C])
 {
-    static_assert(C == 8 || C == 32, "8- or 32-column TMEM loads");
-    if constexpr (C == 32)
-        tmem_ld32(taddr, v);
-    else
-        tmem_ld8(taddr, v);
+    static_assert(C == 8, "8-column TMEM loads only");
+    tmem_ld8(taddr, v);
 }
 
 template <int C>
@@ -504,7 +501,7 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
         if (lane == 0) {
             const uint32_t idesc_obj = idesc_bf16_f32<TC_BK, 1>();
             const uint64_t wh = sw128_desc(sbase + L::OFF_WHI), wl = sw128_desc(sbase + L::OFF_WLO);
-            const uint64_t f0 = sw128_mn_desc(sbase + L::F32_BYTES);
+            const uint64_t f0 = sw128_mn_desc(sbase + L::F32_BYTES, 1024);
             bool ok = mbar_wait_fast(w_full, 0, abort);
             for (int j = 0; j < nkb && ok; ++j) {
                 const int s = j % S, u = j / S;
@@ -532,7 +529,10 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
         const int ct = threadIdx.x - 64;        // 0..127
         const int quarter = warp & 3;           // TMEM lane quarter of this warp
         const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16);
-        double fsum = 0.0;
+        // Sum of squared residuals: FP32 per half row, Kahan-compensated FP32
+        // across K-blocks (FP64 adds here would queue on GB300's narrow FP64
+        // pipe in the split warps' critical path), FP64 across threads.
+        float fs = 0.0f, fc = 0.0f;
         for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % S, u = kb / S;
             if (!mbar_wait(full(s), u & 1, abort))
@@ -552,6 +552,9 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     unsigned char *hs = st + h * (L::F32_BYTES / 2);
+                    uint32_t whr[32];
+                    if (OBJ)   // W H tile of these columns; consumed after the A loads
+                        tmem_ld32_nowait(tq + (uint32_t)(4 * N + b1 * 64 + h * 32), whr);
                     float a[32];
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
@@ -562,16 +565,17 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
                         a[4 * c + 3] = v.w;
                     }
                     if (OBJ) {
-                        // Squared residuals against the W H tile of these columns.
-                        float wh[32];
-                        tmem_ld32(tq + (uint32_t)(4 * N + b1 * 64 + h * 32), wh);
-                        float sq = 0.0f;
+                        tmem_wait_ld();
+                        float q4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
                         for (int i = 0; i < 32; ++i) {
-                            const float e = a[i] - wh[i];
-                            sq = fmaf(e, e, sq);
+                            const float e = a[i] - __uint_as_float(whr[i]);
+                            q4[i & 3] = fmaf(e, e, q4[i & 3]);
                         }
-                        fsum += (double)sq;
+                        const float y = ((q4[0] + q4[1]) + (q4[2] + q4[3])) - fc;
+                        const float t = fs + y;
+                        fc = (t - fs) - y;
+                        fs = t;
                     }
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
@@ -624,6 +628,7 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
             }
         }
         if (OBJ) {
+            double fsum = (double)fs - (double)fc;
             for (int o = 16; o > 0; o >>= 1)
                 fsum += __shfl_xor_sync(FULL, fsum, o);
             if (lane == 0)
