@@ -313,30 +313,53 @@ __device__ void warp_chol_subst(int p, const T *__restrict__ Lw, int LS,
     __syncwarp();
 }
 
-// out[s] += sum over set bits f of mask (one word per slot) of Mat[f][i] v_f,
-// i = lane + 32 s, v_f broadcast from lane f % 32 (Mat symmetric with rows
-// contiguous in i, so each step is a conflict-free row read).
 template <typename T, int KW>
-__device__ __forceinline__ void warp_matvec_masked(const T *__restrict__ Mat, int k,
-                                                   const unsigned (&mask)[KW], const T (&v)[KW],
-                                                   T (&out)[KW], int lane)
+__device__ __forceinline__ void warp_matvec(const T *__restrict__ Mat, int k, const T (&v)[KW],
+                                            T (&out)[KW], T *__restrict__ stage, int lane)
 {
 #pragma unroll
-    for (int s2 = 0; s2 < KW; ++s2) {
-        unsigned bits = mask[s2];
-        while (bits) {
-            const int l = __ffs(bits) - 1;
-            bits &= bits - 1;
-            const T vf = __shfl_sync(FULL, v[s2], l);
-            const T *row = Mat + (32 * s2 + l) * k;
+    for (int s = 0; s < KW; ++s)
+        stage[32 * s + lane] = v[s];
+    __syncwarp();
+    int j = 0;
+    for (; j + 4 <= k; j += 4) {
+        T vj[4];
+        if constexpr (sizeof(T) == 4) {
+            const float4 q = *reinterpret_cast<const float4 *>(stage + j);
+            vj[0] = q.x;
+            vj[1] = q.y;
+            vj[2] = q.z;
+            vj[3] = q.w;
+        } else {
+            const double2 q0 = *reinterpret_cast<const double2 *>(stage + j);
+            const double2 q1 = *reinterpret_cast<const double2 *>(stage + j + 2);
+            vj[0] = q0.x;
+            vj[1] = q0.y;
+            vj[2] = q1.x;
+            vj[3] = q1.y;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const T *row = Mat + (j + t) * k;
 #pragma unroll
             for (int s = 0; s < KW; ++s) {
                 const int i = lane + 32 * s;
                 if (i < k)
-                    out[s] = fma(row[i], vf, out[s]);
+                    out[s] = fma(row[i], vj[t], out[s]);
             }
         }
     }
+    for (; j < k; ++j) {
+        const T vj = stage[j];
+        const T *row = Mat + j * k;
+#pragma unroll
+        for (int s = 0; s < KW; ++s) {
+            const int i = lane + 32 * s;
+            if (i < k)
+                out[s] = fma(row[i], vj, out[s]);
+        }
+    }
+    __syncwarp();
 }
 
 template <typename T>
@@ -369,9 +392,13 @@ __device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) 
 template <int MODE> struct ModeType { using T = double; };
 template <> struct ModeType<0> { using T = float; };
 
+// Per warp: index list (128 ints), right-hand side and reciprocal pivots of
+// the compact system (128 doubles each), the matrix-vector staging vector
+// (128 doubles), the p x LS factor; rounded to 16 bytes.
 __host__ __device__ inline size_t per_warp_bytes(int pmax, int LS)
 {
-    return 128 * sizeof(int) + 256 * sizeof(double) + sizeof(double) * (size_t)pmax * LS;
+    const size_t b = 128 * sizeof(int) + 384 * sizeof(double) + sizeof(double) * (size_t)pmax * LS;
+    return (b + 15) & ~size_t(15);
 }
 
 // Shared-memory matrices of a mode: mode 0 G32 and M32, mode 1 G64 and M64,
@@ -427,7 +454,9 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
     int *widx = reinterpret_cast<int *>(wp);
     double *zbuf64 = reinterpret_cast<double *>(wp + 128 * sizeof(int));
     double *invd64 = zbuf64 + 128;
-    double *Lw64 = invd64 + 128;
+    double *stage64 = invd64 + 128;
+    double *Lw64 = stage64 + 128;
+    T *stage = reinterpret_cast<T *>(stage64);
     T *zbuf = reinterpret_cast<T *>(zbuf64);
     T *invd = reinterpret_cast<T *>(invd64);
     T *Lw = reinterpret_cast<T *>(Lw64);
@@ -493,24 +522,8 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                     x[s] = 0;
             } else {
                 // Unconstrained solution u = M g.
-                if (HAVE_M) {
-#pragma unroll
-                    for (int s2 = 0; s2 < KW; ++s2) {
-                        for (int l = 0; l < 32; ++l) {
-                            const int jj = 32 * s2 + l;
-                            const T gj = __shfl_sync(FULL, g[s2], l);
-                            if (jj >= k)
-                                break;
-                            const T *mrow = Ms + jj * k;
-#pragma unroll
-                            for (int s = 0; s < KW; ++s) {
-                                const int i = lane + 32 * s;
-                                if (i < k)
-                                    u[s] = fma(mrow[i], gj, u[s]);
-                            }
-                        }
-                    }
-                }
+                if (HAVE_M)
+                    warp_matvec<T, KW>(Ms, k, g, u, stage, lane);
                 // Starting partition: empty (cold) or the given bitmask (warm).
                 if (P.pin) {
 #pragma unroll
@@ -629,12 +642,12 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                             w[s] = 0;
                             up[s] = 0;
                         }
-                        warp_matvec_masked<T, KW>(Gs, k, fm, x, w, lane);
+                        warp_matvec<T, KW>(Gs, k, x, w, stage, lane);
 #pragma unroll
                         for (int s = 0; s < KW; ++s)
                             res[s] = inF[s] ? g[s] - w[s] : (T)0;
                         if (comp)
-                            warp_matvec_masked<T, KW>(Ms, k, fm, res, up, lane);
+                            warp_matvec<T, KW>(Ms, k, res, up, stage, lane);
 #pragma unroll
                         for (int s = 0; s < KW; ++s)
                             if (inS[s])
@@ -687,7 +700,7 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
 #pragma unroll
                         for (int s = 0; s < KW; ++s)
                             w[s] = 0;
-                        warp_matvec_masked<T, KW>(Gs, k, fm, x, w, lane);
+                        warp_matvec<T, KW>(Gs, k, x, w, stage, lane);
 #pragma unroll
                         for (int s = 0; s < KW; ++s)
                             y[s] = inF[s] ? (T)0 : w[s] - g[s];
