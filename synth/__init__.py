@@ -30,6 +30,10 @@ Workload recipes (the paper's synthetic sets, Section 6.1.1)
 * ``init_factors``: the non-negative starting point of Algorithm 1, uniform
   [0, 1) for both W (m x k) and H (stored as H^T, n x k). The same seed gives the
   same start on every path (Section 6.1.3).
+* ``mlp_init``: starting weights of the passive-set proposal network (3k -> h
+  -> h -> k), one flat FP32 array [W1 (h x 3k), b1, W2 (h x h), b2, W3 (k x h),
+  b3]; each weight matrix uniform in +-sqrt(6 / (fan_in + fan_out)) (Glorot and
+  Bengio 2010), biases zero.
 """
 from __future__ import annotations
 
@@ -54,6 +58,8 @@ TID_NLS_B = 11
 TID_STRESS_W = 12
 TID_STRESS_ZERO = 13
 TID_STRESS_A = 14
+TID_MLP_INIT = 15
+TID_MLP_BATCH = 16
 
 DEFAULT_SEED = 1509
 
@@ -183,3 +189,31 @@ def nls_batch(k: int, nrhs: int, rows_c: int | None = None, seed: int = DEFAULT_
     G = C.T @ C
     B = D @ C
     return np.ascontiguousarray(G), np.ascontiguousarray(B)
+
+
+def mlp_param_sizes(k: int, hidden: int) -> list[tuple[int, int]]:
+    """(rows, cols) of the proposal network's tensors in flat order; biases have
+    cols = 1."""
+    return [(hidden, 3 * k), (hidden, 1), (hidden, hidden), (hidden, 1), (k, hidden), (k, 1)]
+
+
+def mlp_init(k: int, hidden: int = 256, seed: int = DEFAULT_SEED) -> np.ndarray:
+    """Flat FP32 starting weights of the proposal network (see the module notes)."""
+    parts = []
+    off = 0
+    for rows, cols in mlp_param_sizes(k, hidden):
+        n = rows * cols
+        if cols == 1:
+            parts.append(np.zeros(n, dtype=np.float64))
+        else:
+            a = np.sqrt(6.0 / (rows + cols))
+            u = uniform01(seed, TID_MLP_INIT, np.arange(off, off + n, dtype=np.uint64))
+            parts.append((2.0 * u - 1.0) * a)
+        off += n
+    return np.concatenate(parts).astype(np.float32)
+
+
+def batch_order(n: int, epoch: int, seed: int = DEFAULT_SEED) -> np.ndarray:
+    """A seeded permutation of range(n) for one training epoch (sort of uniform keys)."""
+    u = uniform01(seed + epoch, TID_MLP_BATCH, np.arange(n, dtype=np.uint64))
+    return np.argsort(u, kind="stable").astype(np.int64)
