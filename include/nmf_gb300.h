@@ -207,6 +207,7 @@ typedef struct nmf_stats {
     int64_t bpp_singular;      /* solves left singular in FP64 */
     double ms_gram, ms_mm, ms_nls, ms_objective; /* GPU time per task (timing on) */
     int64_t kernel_launches;   /* CUDA kernels this handle has launched */
+    double ms_proposal;        /* features, proposal and training (timing on) */
 } nmf_stats;
 
 /* Create a handle. W0 (m x k) and Ht0 (n x k) are the device starting point
@@ -254,6 +255,70 @@ nmf_status nmf_set_timing(nmf_handle *h, int32_t timing);
 
 /* Release everything the handle owns. NULL is ignored. */
 void nmf_destroy(nmf_handle *h);
+
+/* ===================================================================== *
+ * Learned passive-set proposal (no counterpart in the paper).
+ * ===================================================================== *
+ * A small network proposes each BPP solve's starting passive set. The solve
+ * then runs to the KKT point of Eq. 4 as always, so every result is the same
+ * unique minimiser and a poor proposal only costs exchange rounds.
+ * Features of one right-hand side (G, g, the previous iterate x_p of that
+ * factor row; zeros when cold), with d_i = sqrt(G_ii) (1 where G_ii <= 0)
+ * and s = max_i |g_i| / d_i (1 if 0), 3k floats:
+ *   [ (G x_p - g)_i / (d_i s), log(G_ii / mean_j G_jj) (0 where G_ii <= 0),
+ *     x_p,i d_i / s ].
+ * Network 3k -> hidden -> hidden -> k, ReLU after the first two layers,
+ * BF16-rounded weights, FP32 arithmetic; proposal {i : logit_i > 0}.
+ * Parameters: one flat FP32 array [W1 (hidden x 3k), b1 (hidden), W2 (hidden
+ * x hidden), b2, W3 (k x hidden), b3 (k)], weight rows = outputs. Training
+ * minimises the mean binary cross-entropy against the solves' final passive
+ * sets with Adam (beta1 0.9, beta2 0.999, eps 1e-8) on FP32 master weights.
+ * All pointers are device pointers; calls are asynchronous on `stream`. */
+typedef struct nmf_mlp nmf_mlp;
+
+int64_t nmf_mlp_param_count(int32_t k, int32_t hidden);
+
+/* k in 1..NMF_MAX_K, hidden in 1..1024; `params` (nmf_mlp_param_count
+ * floats) is copied. */
+nmf_status nmf_mlp_create(nmf_mlp **out, int32_t k, int32_t hidden, const float *params,
+                          void *stream);
+/* Current FP32 master parameters into `params`. */
+nmf_status nmf_mlp_get_params(const nmf_mlp *h, float *params, void *stream);
+void nmf_mlp_destroy(nmf_mlp *h);
+
+/* F (nrhs x 3k) from G (k x k FP64), B (nrhs x k) and Xprev (nrhs x k, or
+ * NULL for zeros). */
+nmf_status nmf_mlp_features(const double *G, const float *B, const float *Xprev, int64_t nrhs,
+                            int32_t k, float *F, void *stream);
+/* Logits (nrhs x k) of features F. */
+nmf_status nmf_mlp_forward(nmf_mlp *h, const float *F, int64_t nrhs, float *logits, void *stream);
+/* Proposed passive sets, nrhs rows of ceil(k/64) words. */
+nmf_status nmf_mlp_propose(nmf_mlp *h, const float *F, int64_t nrhs, uint64_t *passive,
+                           void *stream);
+/* Gradient of the mean binary cross-entropy over the batch (labels: passive
+ * bitmasks) without updating; `grad` (nmf_mlp_param_count floats) and `loss`
+ * (one double) may each be NULL. */
+nmf_status nmf_mlp_gradient(nmf_mlp *h, const float *F, const uint64_t *passive, int64_t nrhs,
+                            float *grad, double *loss, void *stream);
+/* Adam steps over the nrhs samples in consecutive batches of `batch` rows;
+ * the last batch's loss to `loss` (one double, nullable). */
+nmf_status nmf_mlp_train(nmf_mlp *h, const float *F, const uint64_t *passive, int64_t nrhs,
+                         int64_t batch, float lr, double *loss, void *stream);
+
+/* Attach a network to an ANLS handle (NULL or NMF_PROPOSAL_OFF detaches).
+ *   NMF_PROPOSAL_TRAIN: each half-step computes the features of its solves,
+ *     solves as start_mode says, then trains the network on (features, final
+ *     passive sets): `epochs` passes in batches of `batch` rows at rate lr.
+ *   NMF_PROPOSAL_USE: each half-step's solves start from the proposal.
+ * The network must have the handle's k. The handle borrows it: keep it alive
+ * while attached. */
+typedef enum nmf_proposal_mode {
+    NMF_PROPOSAL_OFF = 0,
+    NMF_PROPOSAL_TRAIN = 1,
+    NMF_PROPOSAL_USE = 2
+} nmf_proposal_mode;
+nmf_status nmf_set_proposal(nmf_handle *h, nmf_mlp *mlp, int32_t mode, int32_t epochs,
+                            int64_t batch, float lr);
 
 #ifdef __cplusplus
 }

@@ -41,6 +41,9 @@ NMF_INPUT_CSR = 1
 NMF_START_COLD = 0
 NMF_START_WARM = 1
 NMF_MAX_K = 128
+NMF_PROPOSAL_OFF = 0
+NMF_PROPOSAL_TRAIN = 1
+NMF_PROPOSAL_USE = 2
 
 PRECISIONS = {"fp32": NMF_PREC_FP32, "bf16x3": NMF_PREC_BF16X3}
 
@@ -79,7 +82,7 @@ class nmf_stats(ctypes.Structure):
                 ("bpp_not_converged", _I64), ("bpp_singular", _I64),
                 ("ms_gram", ctypes.c_double), ("ms_mm", ctypes.c_double),
                 ("ms_nls", ctypes.c_double), ("ms_objective", ctypes.c_double),
-                ("kernel_launches", _I64)]
+                ("kernel_launches", _I64), ("ms_proposal", ctypes.c_double)]
 
 
 def _sig(name, args, res=ctypes.c_int):
@@ -113,11 +116,25 @@ _c_get_stats = _sig("nmf_get_stats", [_P, ctypes.POINTER(nmf_stats)])
 _c_set_timing = _sig("nmf_set_timing", [_P, _I32])
 _lib.nmf_destroy.argtypes = [_P]
 _lib.nmf_destroy.restype = None
+_c_mlp_param_count = _sig("nmf_mlp_param_count", [_I32, _I32], _I64)
+_c_mlp_create = _sig("nmf_mlp_create", [ctypes.POINTER(_P), _I32, _I32, _P, _P])
+_c_mlp_get_params = _sig("nmf_mlp_get_params", [_P, _P, _P])
+_lib.nmf_mlp_destroy.argtypes = [_P]
+_lib.nmf_mlp_destroy.restype = None
+_c_mlp_features = _sig("nmf_mlp_features", [_P, _P, _P, _I64, _I32, _P, _P])
+_c_mlp_forward = _sig("nmf_mlp_forward", [_P, _P, _I64, _P, _P])
+_c_mlp_propose = _sig("nmf_mlp_propose", [_P, _P, _I64, _P, _P])
+_c_mlp_gradient = _sig("nmf_mlp_gradient", [_P, _P, _P, _I64, _P, _P, _P])
+_c_mlp_train = _sig("nmf_mlp_train", [_P, _P, _P, _I64, _I64, ctypes.c_float, _P, _P])
+_c_set_proposal = _sig("nmf_set_proposal", [_P, _P, _I32, _I32, _I64, ctypes.c_float])
 
 EXPORTED = ["nmf_status_str", "nmf_gram", "nmf_mm_dense", "nmf_mm_csr", "nmf_csr_transpose",
             "nmf_nls_bpp", "nmf_nls_bpp_noalloc", "nmf_objective_dense", "nmf_init", "nmf_iterate", "nmf_sync",
             "nmf_objective", "nmf_objective_history", "nmf_get_factors", "nmf_set_factors",
-            "nmf_get_passive", "nmf_get_stats", "nmf_set_timing", "nmf_destroy"]
+            "nmf_get_passive", "nmf_get_stats", "nmf_set_timing", "nmf_destroy",
+            "nmf_mlp_param_count", "nmf_mlp_create", "nmf_mlp_get_params", "nmf_mlp_destroy",
+            "nmf_mlp_features", "nmf_mlp_forward", "nmf_mlp_propose", "nmf_mlp_gradient",
+            "nmf_mlp_train", "nmf_set_proposal"]
 
 
 def nmf_status_str(status: int) -> str:
@@ -365,6 +382,14 @@ class nmf_init:
     def nmf_set_timing(self, on: bool = True):
         _check(_c_set_timing(self._h, int(bool(on))), "nmf_set_timing")
 
+    def nmf_set_proposal(self, mlp, mode: str = "use", epochs: int = 1, batch: int = 8192,
+                         lr: float = 1e-3):
+        """Attach an nmf_mlp_create network: mode "train", "use" or "off"."""
+        modes = {"off": NMF_PROPOSAL_OFF, "train": NMF_PROPOSAL_TRAIN, "use": NMF_PROPOSAL_USE}
+        _check(_c_set_proposal(self._h, None if mlp is None else mlp._h, modes[mode], epochs,
+                               batch, lr), "nmf_set_proposal")
+        self._mlp = mlp   # the handle borrows the network
+
     def nmf_destroy(self):
         if getattr(self, "_h", None):
             _lib.nmf_destroy(self._h)
@@ -393,3 +418,89 @@ def bool_to_passive(P: torch.Tensor) -> torch.Tensor:
     pad[:, :k] = P.to(torch.int64)
     bits = torch.arange(64, device=P.device, dtype=torch.int64)
     return (pad.reshape(nrhs, nw, 64) << bits).sum(dim=-1)
+
+
+# ------------------------------------------------------------------ proposal
+def nmf_mlp_param_count(k: int, hidden: int) -> int:
+    return int(_c_mlp_param_count(k, hidden))
+
+
+def nmf_mlp_features(G: torch.Tensor, B: torch.Tensor, Xprev=None, out=None,
+                     stream=None) -> torch.Tensor:
+    """nrhs x 3k features of right-hand sides B (nrhs x k) with Gram G (k x k FP64)."""
+    _dev(G, torch.float64, "G")
+    _dev(B, torch.float32, "B")
+    if Xprev is not None:
+        _dev(Xprev, torch.float32, "Xprev")
+    nrhs, k = B.shape
+    if out is None:
+        out = torch.empty((nrhs, 3 * k), dtype=torch.float32, device=B.device)
+    _check(_c_mlp_features(_ptr(G), _ptr(B), _ptr(Xprev), nrhs, k, _ptr(out), _stream(stream)),
+           "nmf_mlp_features")
+    return out
+
+
+class nmf_mlp_create:
+    """The proposal network (C ABI nmf_mlp_*); `params` is the flat FP32 array."""
+
+    def __init__(self, k: int, hidden: int, params: torch.Tensor, stream=None):
+        _dev(params, torch.float32, "params")
+        if params.numel() != nmf_mlp_param_count(k, hidden):
+            raise ValueError("params has the wrong length")
+        self.k, self.hidden = k, hidden
+        self.device = params.device
+        h = _P()
+        _check(_c_mlp_create(ctypes.byref(h), k, hidden, _ptr(params), _stream(stream)),
+               "nmf_mlp_create")
+        self._h = h
+
+    def nmf_mlp_get_params(self, stream=None) -> torch.Tensor:
+        out = torch.empty(nmf_mlp_param_count(self.k, self.hidden), dtype=torch.float32,
+                          device=self.device)
+        _check(_c_mlp_get_params(self._h, _ptr(out), _stream(stream)), "nmf_mlp_get_params")
+        return out
+
+    def nmf_mlp_forward(self, F: torch.Tensor, stream=None) -> torch.Tensor:
+        _dev(F, torch.float32, "F")
+        out = torch.empty((F.shape[0], self.k), dtype=torch.float32, device=F.device)
+        _check(_c_mlp_forward(self._h, _ptr(F), F.shape[0], _ptr(out), _stream(stream)),
+               "nmf_mlp_forward")
+        return out
+
+    def nmf_mlp_propose(self, F: torch.Tensor, stream=None) -> torch.Tensor:
+        _dev(F, torch.float32, "F")
+        nw = (self.k + 63) // 64
+        out = torch.empty((F.shape[0], nw), dtype=torch.int64, device=F.device)
+        _check(_c_mlp_propose(self._h, _ptr(F), F.shape[0], _ptr(out), _stream(stream)),
+               "nmf_mlp_propose")
+        return out
+
+    def nmf_mlp_gradient(self, F: torch.Tensor, passive: torch.Tensor, stream=None):
+        _dev(F, torch.float32, "F")
+        _dev(passive, torch.int64, "passive")
+        g = torch.empty(nmf_mlp_param_count(self.k, self.hidden), dtype=torch.float32,
+                        device=F.device)
+        loss = torch.empty(1, dtype=torch.float64, device=F.device)
+        _check(_c_mlp_gradient(self._h, _ptr(F), _ptr(passive), F.shape[0], _ptr(g), _ptr(loss),
+                               _stream(stream)), "nmf_mlp_gradient")
+        return g, loss
+
+    def nmf_mlp_train(self, F: torch.Tensor, passive: torch.Tensor, batch: int = 8192,
+                      lr: float = 1e-3, stream=None) -> torch.Tensor:
+        _dev(F, torch.float32, "F")
+        _dev(passive, torch.int64, "passive")
+        loss = torch.empty(1, dtype=torch.float64, device=F.device)
+        _check(_c_mlp_train(self._h, _ptr(F), _ptr(passive), F.shape[0], batch, lr, _ptr(loss),
+                            _stream(stream)), "nmf_mlp_train")
+        return loss
+
+    def nmf_mlp_destroy(self):
+        if getattr(self, "_h", None):
+            _lib.nmf_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.nmf_mlp_destroy()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass

@@ -229,7 +229,14 @@ struct nmf_handle {
     BppStats reported{};                        // stats already turned into a status
     bool timing = false;
     int64_t launches = 0;                       // kernels launched by nmf_iterate / objective
-    double ms[4] = {0, 0, 0, 0};                // gram, mm, nls, objective
+    double ms[5] = {0, 0, 0, 0, 0};             // gram, mm, nls, objective, proposal
+    // Learned passive-set proposal (borrowed network; features buffer owned).
+    nmf::MlpNet *mlp = nullptr;
+    int32_t prop_mode = NMF_PROPOSAL_OFF;
+    int32_t prop_epochs = 1;
+    int64_t prop_batch = 8192;
+    float prop_lr = 1e-3f;
+    float *feat = nullptr;                      // max(m, n) x 3k
     struct Pending {
         int phase;
         cudaEvent_t a, b;
@@ -325,6 +332,38 @@ nmf_status objective_into(nmf_handle *h, double *f_dev)
                                   h->obj_part, f_dev, h->stream);
 }
 
+// The BPP solves of one half-step: X (rows x k, the factor, updated in place)
+// from Gram G and right-hand sides R; passive = that factor's bitmasks. With
+// a network attached, its features are formed from the rows of X before the
+// update; it proposes the starting partition (use) or learns from the final
+// one (train).
+nmf_status solve_half(nmf_handle *h, int64_t rows, const double *G, const float *R, float *X,
+                      uint64_t *passive, bool warm)
+{
+    const nmf_config &c = h->cfg;
+    const bool use = h->mlp && h->prop_mode == NMF_PROPOSAL_USE;
+    const bool train = h->mlp && h->prop_mode == NMF_PROPOSAL_TRAIN;
+    if (use || train) {
+        PhaseTimer t(h, 4);
+        NMF_TRY(mlp_features(G, R, X, rows, c.k, h->feat, h->stream));
+        if (use)
+            NMF_TRY(mlp_propose(h->mlp, h->feat, rows, passive, h->stream));
+    }
+    {
+        PhaseTimer t(h, 2);
+        NMF_TRY(launch_bpp_solve(c.k, rows, G, R, X, (use || warm) ? passive : nullptr, passive,
+                                 nullptr, nullptr, c.max_bpp_rounds, h->bpp_work, h->stats_dev,
+                                 h->stream));
+    }
+    if (train) {
+        PhaseTimer t(h, 4);
+        for (int e = 0; e < h->prop_epochs; ++e)
+            NMF_TRY(mlp_train(h->mlp, h->feat, passive, rows, h->prop_batch, h->prop_lr, nullptr,
+                              h->stream));
+    }
+    return NMF_OK;
+}
+
 nmf_status one_iteration(nmf_handle *h)
 {
     const nmf_config &c = h->cfg;
@@ -357,26 +396,16 @@ nmf_status one_iteration(nmf_handle *h)
             NMF_TRY(mm(h, 0, h->Ht, h->V));
         }
     }
-    {
-        PhaseTimer t(h, 2);
-        NMF_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-        NMF_TRY(launch_bpp_solve(c.k, c.m, h->GH, h->V, h->W, warm ? h->pW : nullptr, h->pW,
-                                 nullptr, nullptr, c.max_bpp_rounds, h->bpp_work, h->stats_dev,
-                                 h->stream));
-    }
+    NMF_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+    NMF_TRY(solve_half(h, c.m, h->GH, h->V, h->W, h->pW, warm));
     // H <- argmin_{H >= 0} ||A - W H||: Gram W^T W, right-hand sides (W^T A)^T.
     NMF_TRY(fork_prepare(h->W, c.m, h->GW));
     {
         PhaseTimer t(h, 1);
         NMF_TRY(mm(h, 1, h->W, h->Y));
     }
-    {
-        PhaseTimer t(h, 2);
-        NMF_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-        NMF_TRY(launch_bpp_solve(c.k, c.n, h->GW, h->Y, h->Ht, warm ? h->pH : nullptr, h->pH,
-                                 nullptr, nullptr, c.max_bpp_rounds, h->bpp_work, h->stats_dev,
-                                 h->stream));
-    }
+    NMF_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+    NMF_TRY(solve_half(h, c.n, h->GW, h->Y, h->Ht, h->pH, warm));
     h->passive_valid = true;
     if (c.objective_every) {
         if (h->fused_obj) {
@@ -425,6 +454,7 @@ void free_handle(nmf_handle *h)
     cudaFree(h->t_rowptr);
     cudaFree(h->t_colidx);
     cudaFree(h->t_vals);
+    cudaFree(h->feat);
     for (auto &p : h->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -677,6 +707,7 @@ extern "C" nmf_status nmf_get_stats(nmf_handle *h, nmf_stats *out)
     out->ms_nls = h->ms[2];
     out->ms_objective = h->ms[3];
     out->kernel_launches = h->launches;
+    out->ms_proposal = h->ms[4];
     return NMF_OK;
 }
 
@@ -694,4 +725,114 @@ extern "C" void nmf_destroy(nmf_handle *h)
         return;
     cudaStreamSynchronize(h->stream);
     free_handle(h);
+}
+
+// ===========================================================================
+// Learned passive-set proposal.
+// ===========================================================================
+
+struct nmf_mlp {
+    nmf::MlpNet *net;
+};
+
+extern "C" int64_t nmf_mlp_param_count(int32_t k, int32_t hidden)
+{
+    if (k < 1 || k > NMF_MAX_K || hidden < 1 || hidden > 1024)
+        return 0;
+    return mlp_param_count(k, hidden);
+}
+
+extern "C" nmf_status nmf_mlp_create(nmf_mlp **out, int32_t k, int32_t hidden,
+                                     const float *params, void *stream)
+{
+    if (!out || !params || k < 1 || k > NMF_MAX_K || hidden < 1 || hidden > 1024)
+        return NMF_ERR_INVALID_ARG;
+    *out = nullptr;
+    nmf::MlpNet *net = nullptr;
+    NMF_TRY(mlp_create(&net, k, hidden, params, as_stream(stream)));
+    *out = new nmf_mlp{net};
+    return NMF_OK;
+}
+
+extern "C" nmf_status nmf_mlp_get_params(const nmf_mlp *h, float *params, void *stream)
+{
+    if (!h || !params)
+        return NMF_ERR_INVALID_ARG;
+    NMF_CUDA(cudaMemcpyAsync(params, mlp_master(h->net), sizeof(float) * (size_t)mlp_nparams(h->net),
+                             cudaMemcpyDeviceToDevice, as_stream(stream)));
+    return NMF_OK;
+}
+
+extern "C" void nmf_mlp_destroy(nmf_mlp *h)
+{
+    if (!h)
+        return;
+    mlp_destroy(h->net);
+    delete h;
+}
+
+extern "C" nmf_status nmf_mlp_features(const double *G, const float *B, const float *Xprev,
+                                       int64_t nrhs, int32_t k, float *F, void *stream)
+{
+    if (!G || k < 1 || k > NMF_MAX_K || nrhs < 0 || (nrhs > 0 && (!B || !F)))
+        return NMF_ERR_INVALID_ARG;
+    return mlp_features(G, B, Xprev, nrhs, k, F, as_stream(stream));
+}
+
+extern "C" nmf_status nmf_mlp_forward(nmf_mlp *h, const float *F, int64_t nrhs, float *logits,
+                                      void *stream)
+{
+    if (!h || nrhs < 0 || nrhs > INT32_MAX || (nrhs > 0 && (!F || !logits)))
+        return NMF_ERR_INVALID_ARG;
+    return mlp_logits(h->net, F, nrhs, logits, as_stream(stream));
+}
+
+extern "C" nmf_status nmf_mlp_propose(nmf_mlp *h, const float *F, int64_t nrhs,
+                                      uint64_t *passive, void *stream)
+{
+    if (!h || nrhs < 0 || nrhs > INT32_MAX || (nrhs > 0 && (!F || !passive)))
+        return NMF_ERR_INVALID_ARG;
+    return mlp_propose(h->net, F, nrhs, passive, as_stream(stream));
+}
+
+extern "C" nmf_status nmf_mlp_gradient(nmf_mlp *h, const float *F, const uint64_t *passive,
+                                       int64_t nrhs, float *grad, double *loss, void *stream)
+{
+    if (!h || !F || !passive || nrhs < 1 || nrhs > INT32_MAX)
+        return NMF_ERR_INVALID_ARG;
+    return mlp_gradient(h->net, F, passive, nrhs, grad, loss, as_stream(stream));
+}
+
+extern "C" nmf_status nmf_mlp_train(nmf_mlp *h, const float *F, const uint64_t *passive,
+                                    int64_t nrhs, int64_t batch, float lr, double *loss,
+                                    void *stream)
+{
+    if (!h || !F || !passive || nrhs < 1 || batch < 1 || batch > INT32_MAX || !(lr > 0.0f))
+        return NMF_ERR_INVALID_ARG;
+    return mlp_train(h->net, F, passive, nrhs, batch, lr, loss, as_stream(stream));
+}
+
+extern "C" nmf_status nmf_set_proposal(nmf_handle *h, nmf_mlp *mlp, int32_t mode, int32_t epochs,
+                                       int64_t batch, float lr)
+{
+    if (!h || mode < NMF_PROPOSAL_OFF || mode > NMF_PROPOSAL_USE)
+        return NMF_ERR_INVALID_ARG;
+    if (!mlp || mode == NMF_PROPOSAL_OFF) {
+        h->mlp = nullptr;
+        h->prop_mode = NMF_PROPOSAL_OFF;
+        return NMF_OK;
+    }
+    if (mlp_k(mlp->net) != h->cfg.k || epochs < 0 || batch < 1 || batch > INT32_MAX ||
+        !(lr > 0.0f))
+        return NMF_ERR_INVALID_ARG;
+    if (!h->feat) {
+        const int64_t rows = h->cfg.m > h->cfg.n ? h->cfg.m : h->cfg.n;
+        NMF_CUDA(cudaMalloc(&h->feat, sizeof(float) * (size_t)rows * 3 * h->cfg.k));
+    }
+    h->mlp = mlp->net;
+    h->prop_mode = mode;
+    h->prop_epochs = epochs;
+    h->prop_batch = batch;
+    h->prop_lr = lr;
+    return NMF_OK;
 }

@@ -113,4 +113,22 @@ nmf_status launch_bpp_solve(int k, int64_t nrhs, const double *G, const float *B
                             int8_t *status_out, int max_rounds, void *work, BppStats *stats_dev,
                             cudaStream_t s);
 
+// Learned passive-set proposal (mlp.cu).
+struct MlpNet;
+int64_t mlp_param_count(int k, int h);
+nmf_status mlp_create(MlpNet **out, int k, int h, const float *params, cudaStream_t s);
+void mlp_destroy(MlpNet *net);
+int mlp_k(const MlpNet *net);
+int mlp_hidden(const MlpNet *net);
+int64_t mlp_nparams(const MlpNet *net);
+const float *mlp_master(const MlpNet *net);
+nmf_status mlp_features(const double *G, const float *B, const float *Xp, int64_t nrhs, int k,
+                        float *F, cudaStream_t s);
+nmf_status mlp_logits(MlpNet *net, const float *F, int64_t n, float *logits, cudaStream_t s);
+nmf_status mlp_propose(MlpNet *net, const float *F, int64_t n, uint64_t *passive, cudaStream_t s);
+nmf_status mlp_gradient(MlpNet *net, const float *F, const uint64_t *lab, int64_t n,
+                        float *grad_out, double *loss_dev, cudaStream_t s);
+nmf_status mlp_train(MlpNet *net, const float *F, const uint64_t *lab, int64_t n, int64_t batch,
+                     float lr, double *loss_dev, cudaStream_t s);
+
 }  // namespace nmf
