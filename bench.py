@@ -50,6 +50,8 @@ FP32_LANES_PER_SM = 128
 # 1.5505 GB read + 7.1 MB written; A^T W: 1.5422 GB + 3.2 MB), scaled by the
 # element ratio 16 and averaged: 24.83 GB per launch against 24.61 GB of
 # algorithmic bytes (profiles/mm_tc_kernel_dense-medium.md).
+MLP_HIDDEN = 256     # width of the proposal network (3k -> 256 -> 256 -> k)
+
 NCU_TRAFFIC = {
     ("mm_tc_kernel", "dense-large", "bf16x3"): 24.83e9,
     ("mm_tc_kernel", "dense-medium", "bf16x3"): 1.5516e9,
@@ -184,9 +186,21 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
 
-    h = nmf.nmf_init(A, W0, Ht0, precision=args.precision, start=args.start,
+    learned = args.start == "learned"
+    h = nmf.nmf_init(A, W0, Ht0, precision=args.precision,
+                     start="cold" if learned else args.start,
                      max_bpp_rounds=args.max_rounds, objective_every=True)
+    net = None
+    if learned:
+        # Learned starting partitions: the proposal network trains on every
+        # warm-up half-step's (features, final passive sets), then proposes
+        # the starting partition of every timed solve.
+        net = nmf.nmf_mlp_create(k, MLP_HIDDEN, torch.from_numpy(synth.mlp_init(k, MLP_HIDDEN,
+                                                                               seed=SEED)).to(dev))
+        h.nmf_set_proposal(net, "train", epochs=1, batch=8192, lr=1e-3)
     h.nmf_iterate(args.warmup)
+    if learned:
+        h.nmf_set_proposal(net, "use")
     warm_status = h.nmf_sync()
     st0 = h.nmf_get_stats()
     h.nmf_set_timing(True)
@@ -229,6 +243,7 @@ def run_ours(args, rank, world, local_rank):
     nls_ms = (st1["ms_nls"] - st0["ms_nls"]) / launches_mm
     gram_ms = (st1["ms_gram"] - st0["ms_gram"]) / launches_mm
     obj_ms = (st1["ms_objective"] - st0["ms_objective"]) / args.steps
+    prop_ms = (st1["ms_proposal"] - st0["ms_proposal"]) / launches_mm
     pk, pk_kind = peaks()
     bytes_mm = 4.0 * m * n + 4.0 * (m + n) * k     # A once + factor in + product out
     flops_mm = 2.0 * m * n * k
@@ -265,8 +280,11 @@ def run_ours(args, rank, world, local_rank):
         A.copy_(A_host, non_blocking=True)
         W0.copy_(W0_host, non_blocking=True)
         Ht0.copy_(Ht0_host, non_blocking=True)
-        h2 = nmf.nmf_init(A, W0, Ht0, precision=args.precision, start=args.start,
+        h2 = nmf.nmf_init(A, W0, Ht0, precision=args.precision,
+                          start="cold" if learned else args.start,
                           max_bpp_rounds=args.max_rounds, objective_every=True)
+        if learned:
+            h2.nmf_set_proposal(net, "use")    # the network trained above
         h2.nmf_iterate(args.steps)
         Wd, Htd = h2.nmf_get_factors()
         W_out.copy_(Wd, non_blocking=True)
@@ -312,7 +330,7 @@ def run_ours(args, rank, world, local_rank):
                 # stream, fork to finish; it overlaps the products (so it also
                 # counts time queued behind them) and is not part of the step sum.
                 "phase_ms_per_launch": {"mm": mm_ms, "nls": nls_ms, "gram_prep_side": gram_ms,
-                                        "objective": obj_ms},
+                                        "objective": obj_ms, "proposal": prop_ms},
                 "bpp": {"rounds_per_rhs": rounds / max(rhs, 1),
                         "fp64_solves": st1["bpp_fp64_solves"] - st0["bpp_fp64_solves"],
                         "fp64_halfsteps": st1["bpp_fp64_halfsteps"] - st0["bpp_fp64_halfsteps"],
@@ -330,7 +348,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "bf16x3"], default="bf16x3")
-    ap.add_argument("--start", choices=["cold", "warm"], default="warm")
+    ap.add_argument("--start", choices=["cold", "warm", "learned"], default="warm",
+                    help="BPP starting partitions: empty, the previous iteration's, or the "
+                         "proposal network's (trained during the warm-up iterations)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dense-large")
     ap.add_argument("--max-rounds", type=int, default=100)
     ap.add_argument("--cpu-steps", type=int, default=8)
