@@ -129,6 +129,16 @@ typedef struct nmf_nls_desc {
  * internal device workspace (stream-ordered allocation, freed on return). */
 nmf_status nmf_nls_bpp(const nmf_nls_desc *d, void *stream);
 
+/* Launch-shape autotuner for the batched solve (an interface of this library,
+ * no counterpart in the paper): times the solve kernel's candidate shapes
+ * (warps per CTA x right-hand sides per grab of the work counter) on this
+ * batch and keeps the fastest for d->k; every later solve of that k in the
+ * process (nmf_nls_bpp, handles) uses it. All shapes give bit-identical
+ * results. X receives the solution; passive_out, rounds_out and status_out
+ * are not written. Synchronises `stream`; *warps and *chunk (host, nullable)
+ * get the chosen shape. */
+nmf_status nmf_nls_bpp_tune(const nmf_nls_desc *d, void *stream, int32_t *warps, int32_t *chunk);
+
 /* Allocation-free variant of nmf_nls_bpp (no counterpart in the paper; an
  * interface of this library). Same arguments, computation and results as
  * nmf_nls_bpp, but it never allocates device memory, for callers that cannot
@@ -208,6 +218,7 @@ typedef struct nmf_stats {
     double ms_gram, ms_mm, ms_nls, ms_objective; /* GPU time per task (timing on) */
     int64_t kernel_launches;   /* CUDA kernels this handle has launched */
     double ms_proposal;        /* features, proposal and training (timing on) */
+    int64_t graph_launches;    /* nmf_iterate calls run as one CUDA graph */
 } nmf_stats;
 
 /* Create a handle. W0 (m x k) and Ht0 (n x k) are the device starting point
@@ -252,6 +263,11 @@ nmf_status nmf_get_passive(nmf_handle *h, uint64_t *pW, uint64_t *pH);
  * later iterations (adds event records, no host waits inside nmf_iterate). */
 nmf_status nmf_get_stats(nmf_handle *h, nmf_stats *out);
 nmf_status nmf_set_timing(nmf_handle *h, int32_t timing);
+
+/* on != 0: each nmf_iterate call captures its iterations into one CUDA graph
+ * and launches that (fewer launch gaps for small problems). Calls on the
+ * legacy default stream or with timing on run eagerly instead. */
+nmf_status nmf_set_graph(nmf_handle *h, int32_t on);
 
 /* Release everything the handle owns. NULL is ignored. */
 void nmf_destroy(nmf_handle *h);

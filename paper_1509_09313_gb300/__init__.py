@@ -82,7 +82,8 @@ class nmf_stats(ctypes.Structure):
                 ("bpp_not_converged", _I64), ("bpp_singular", _I64),
                 ("ms_gram", ctypes.c_double), ("ms_mm", ctypes.c_double),
                 ("ms_nls", ctypes.c_double), ("ms_objective", ctypes.c_double),
-                ("kernel_launches", _I64), ("ms_proposal", ctypes.c_double)]
+                ("kernel_launches", _I64), ("ms_proposal", ctypes.c_double),
+                ("graph_launches", _I64)]
 
 
 def _sig(name, args, res=ctypes.c_int):
@@ -100,6 +101,8 @@ _c_mm_csr = _sig("nmf_mm_csr", [_P, _P, _P, _I64, _I64, _P, _I32, _P, _P])
 _c_csr_transpose = _sig("nmf_csr_transpose", [_P, _P, _P, _I64, _I64, _I64, _P, _P, _P, _P])
 _c_nls_bpp = _sig("nmf_nls_bpp", [ctypes.POINTER(nmf_nls_desc), _P])
 _c_nls_bpp_noalloc = _sig("nmf_nls_bpp_noalloc", [ctypes.POINTER(nmf_nls_desc), _P])
+_c_nls_bpp_tune = _sig("nmf_nls_bpp_tune", [ctypes.POINTER(nmf_nls_desc), _P,
+                                            ctypes.POINTER(_I32), ctypes.POINTER(_I32)])
 _c_objective_dense = _sig("nmf_objective_dense",
                           [_P, _I64, _I64, _I64, _P, _P, _I32, _I32,
                            ctypes.POINTER(ctypes.c_double), _P])
@@ -114,6 +117,7 @@ _c_set_factors = _sig("nmf_set_factors", [_P, _P, _P])
 _c_get_passive = _sig("nmf_get_passive", [_P, _P, _P])
 _c_get_stats = _sig("nmf_get_stats", [_P, ctypes.POINTER(nmf_stats)])
 _c_set_timing = _sig("nmf_set_timing", [_P, _I32])
+_c_set_graph = _sig("nmf_set_graph", [_P, _I32])
 _lib.nmf_destroy.argtypes = [_P]
 _lib.nmf_destroy.restype = None
 _c_mlp_param_count = _sig("nmf_mlp_param_count", [_I32, _I32], _I64)
@@ -129,9 +133,9 @@ _c_mlp_train = _sig("nmf_mlp_train", [_P, _P, _P, _I64, _I64, ctypes.c_float, _P
 _c_set_proposal = _sig("nmf_set_proposal", [_P, _P, _I32, _I32, _I64, ctypes.c_float])
 
 EXPORTED = ["nmf_status_str", "nmf_gram", "nmf_mm_dense", "nmf_mm_csr", "nmf_csr_transpose",
-            "nmf_nls_bpp", "nmf_nls_bpp_noalloc", "nmf_objective_dense", "nmf_init", "nmf_iterate", "nmf_sync",
+            "nmf_nls_bpp", "nmf_nls_bpp_noalloc", "nmf_nls_bpp_tune", "nmf_objective_dense", "nmf_init", "nmf_iterate", "nmf_sync",
             "nmf_objective", "nmf_objective_history", "nmf_get_factors", "nmf_set_factors",
-            "nmf_get_passive", "nmf_get_stats", "nmf_set_timing", "nmf_destroy",
+            "nmf_get_passive", "nmf_get_stats", "nmf_set_timing", "nmf_set_graph", "nmf_destroy",
             "nmf_mlp_param_count", "nmf_mlp_create", "nmf_mlp_get_params", "nmf_mlp_destroy",
             "nmf_mlp_features", "nmf_mlp_forward", "nmf_mlp_propose", "nmf_mlp_gradient",
             "nmf_mlp_train", "nmf_set_proposal"]
@@ -244,6 +248,24 @@ def nmf_nls_bpp_noalloc(G: torch.Tensor, B: torch.Tensor, passive_in: torch.Tens
     caller's side, as for nmf_nls_bpp."""
     return _nls_bpp(_c_nls_bpp_noalloc, "nmf_nls_bpp_noalloc", G, B, passive_in, max_rounds,
                     outputs, stream)
+
+
+def nmf_nls_bpp_tune(G: torch.Tensor, B: torch.Tensor, passive_in: torch.Tensor | None = None,
+                     max_rounds: int = 100, stream=None):
+    """Autotune the solve kernel's launch shape for k on this batch (kept for
+    every later solve of that k). Returns (warps per CTA, RHS per grab, X)."""
+    _dev(G, torch.float64, "G")
+    _dev(B, torch.float32, "B")
+    nrhs, k = B.shape
+    X = torch.empty_like(B)
+    if passive_in is not None:
+        _dev(passive_in, torch.int64, "passive_in")
+    d = nmf_nls_desc(k, nrhs, _ptr(G), _ptr(B), _ptr(X), _ptr(passive_in), None, None, None,
+                     max_rounds)
+    w, c = _I32(0), _I32(0)
+    _check(_c_nls_bpp_tune(ctypes.byref(d), _stream(stream), ctypes.byref(w), ctypes.byref(c)),
+           "nmf_nls_bpp_tune")
+    return w.value, c.value, X
 
 
 def _nls_bpp(fn, name, G, B, passive_in, max_rounds, outputs, stream):
@@ -381,6 +403,9 @@ class nmf_init:
 
     def nmf_set_timing(self, on: bool = True):
         _check(_c_set_timing(self._h, int(bool(on))), "nmf_set_timing")
+
+    def nmf_set_graph(self, on: bool = True):
+        _check(_c_set_graph(self._h, int(bool(on))), "nmf_set_graph")
 
     def nmf_set_proposal(self, mlp, mode: str = "use", epochs: int = 1, batch: int = 8192,
                          lr: float = 1e-3):

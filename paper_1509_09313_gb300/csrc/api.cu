@@ -157,6 +157,27 @@ extern "C" nmf_status nmf_nls_bpp(const nmf_nls_desc *d, void *stream)
     return worst_from_stats(host);
 }
 
+extern "C" nmf_status nmf_nls_bpp_tune(const nmf_nls_desc *d, void *stream, int32_t *warps,
+                                       int32_t *chunk)
+{
+    if (!d || bad_k(d->k) || d->nrhs < 1 || d->max_rounds < 0 || !d->G || !d->B || !d->X)
+        return NMF_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    TempBuf w(s), st(s);
+    NMF_CUDA(w.alloc(bpp_work_bytes(d->k)));
+    NMF_CUDA(st.alloc(sizeof(BppStats)));
+    NMF_CUDA(cudaMemsetAsync(st.p, 0, sizeof(BppStats), s));
+    int wv = 0, cv = 0;
+    NMF_TRY(bpp_tune(d->k, d->nrhs, d->G, d->B, d->X, d->passive_in, d->max_rounds, w.p,
+                     static_cast<BppStats *>(st.p), s, &wv, &cv));
+    NMF_CUDA(cudaStreamSynchronize(s));
+    if (warps)
+        *warps = wv;
+    if (chunk)
+        *chunk = cv;
+    return NMF_OK;
+}
+
 extern "C" nmf_status nmf_objective_dense(const float *A, int64_t m, int64_t n, int64_t lda,
                                           const float *W, const float *Ht, int32_t k,
                                           int32_t precision, double *f_out, void *stream)
@@ -228,6 +249,10 @@ struct nmf_handle {
     int64_t iterations = 0;
     BppStats reported{};                        // stats already turned into a status
     bool timing = false;
+    bool use_graph = false;                     // nmf_iterate captures a CUDA graph
+    int64_t graph_launches = 0;                 // graphs launched by nmf_iterate
+    cudaGraphExec_t graph_exec = nullptr;       // last instantiated iteration graph
+    int32_t graph_iters = 0;                    // its iteration count
     int64_t launches = 0;                       // kernels launched by nmf_iterate / objective
     double ms[5] = {0, 0, 0, 0, 0};             // gram, mm, nls, objective, proposal
     // Learned passive-set proposal (borrowed network; features buffer owned).
@@ -467,6 +492,8 @@ void free_handle(nmf_handle *h)
         cudaEventDestroy(h->ev_join);
     if (h->side)
         cudaStreamDestroy(h->side);
+    if (h->graph_exec)
+        cudaGraphExecDestroy(h->graph_exec);
     delete h;
 }
 
@@ -578,16 +605,72 @@ extern "C" nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nm
     return NMF_OK;
 }
 
+// Graph mode: the call's iterations are captured from the handle's stream
+// (the side stream joins through the fork / join events) into one CUDA graph
+// and launched once. Kernel arguments that change between calls (objective
+// history slots) are captured per call. Not on the legacy default stream (it
+// cannot be captured) or with per-task timing on (its events would be graph
+// nodes): those calls run eagerly.
+nmf_status iterate_graph(nmf_handle *h, int32_t iters)
+{
+    NMF_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    nmf_status st = NMF_OK;
+    for (int32_t t = 0; t < iters && st == NMF_OK; ++t)
+        st = one_iteration(h);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (st != NMF_OK || e != cudaSuccess) {
+        if (g)
+            cudaGraphDestroy(g);
+        return st != NMF_OK ? st : from_cuda(e, "cudaStreamEndCapture");
+    }
+    // A call with the same iteration count and state captures the same graph
+    // shape with other arguments: update the instantiated graph in place
+    // (much cheaper than instantiating); instantiate only when that fails.
+    cudaError_t r = cudaErrorUnknown;
+    if (h->graph_exec && h->graph_iters == iters) {
+        cudaGraphExecUpdateResultInfo info;
+        r = cudaGraphExecUpdate(h->graph_exec, g, &info);
+        if (r != cudaSuccess)
+            cudaGetLastError();   // clear the update failure; instantiate below
+    }
+    if (r != cudaSuccess) {
+        if (h->graph_exec)
+            cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+        r = cudaGraphInstantiate(&h->graph_exec, g, 0);
+        h->graph_iters = iters;
+    }
+    if (r == cudaSuccess)
+        r = cudaGraphLaunch(h->graph_exec, h->stream);
+    cudaGraphDestroy(g);
+    NMF_CUDA(r);
+    return NMF_OK;
+}
+
 extern "C" nmf_status nmf_iterate(nmf_handle *h, int32_t iters)
 {
     if (!h || iters < 0)
         return NMF_ERR_INVALID_ARG;
     const unsigned long long before = launch_count;
     nmf_status st = NMF_OK;
-    for (int32_t t = 0; t < iters && st == NMF_OK; ++t)
-        st = one_iteration(h);
+    if (h->use_graph && iters > 0 && h->stream != nullptr && !h->timing) {
+        st = iterate_graph(h, iters);
+        h->graph_launches += 1;
+    } else {
+        for (int32_t t = 0; t < iters && st == NMF_OK; ++t)
+            st = one_iteration(h);
+    }
     h->launches += (int64_t)(launch_count - before);
     return st;
+}
+
+extern "C" nmf_status nmf_set_graph(nmf_handle *h, int32_t on)
+{
+    if (!h)
+        return NMF_ERR_INVALID_ARG;
+    h->use_graph = on != 0;
+    return NMF_OK;
 }
 
 extern "C" nmf_status nmf_sync(nmf_handle *h)
@@ -708,6 +791,7 @@ extern "C" nmf_status nmf_get_stats(nmf_handle *h, nmf_stats *out)
     out->ms_objective = h->ms[3];
     out->kernel_launches = h->launches;
     out->ms_proposal = h->ms[4];
+    out->graph_launches = h->graph_launches;
     return NMF_OK;
 }
 

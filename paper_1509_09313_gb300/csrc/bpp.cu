@@ -47,14 +47,15 @@
 // (right-hand sides in, solutions out) plus bitmasks.
 #include <math.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace nmf {
 namespace {
 
-constexpr int BPP_WARPS = 8;
+constexpr int BPP_WARPS = 8;               // most warps per CTA (launch bound)
 constexpr int BPP_THREADS = BPP_WARPS * 32;
-constexpr int RHS_CHUNK = 8;
 constexpr float PIVOT_TOL = 1e-4f;
 constexpr double PIVOT_TOL64 = 1e-13;
 constexpr double COND_FP32 = 1e4;          // scaled cond_1(G) up to which solves run in FP32
@@ -372,6 +373,7 @@ __device__ __forceinline__ T warp_max(T v)
 
 struct SolveParams {
     int k, nwords, max_rounds;
+    int warps, chunk;              // warps per CTA; right-hand sides per counter grab
     int64_t nrhs;
     const float *G32, *M32;
     const double *G64, *M64;
@@ -488,11 +490,11 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
     for (;;) {
         unsigned long long j0 = 0;
         if (lane == 0)
-            j0 = atomicAdd(P.counter, (unsigned long long)RHS_CHUNK);
+            j0 = atomicAdd(P.counter, (unsigned long long)P.chunk);
         j0 = __shfl_sync(FULL, j0, 0);
         if (j0 >= (unsigned long long)P.nrhs)
             break;
-        const int64_t jend = min((int64_t)j0 + RHS_CHUNK, P.nrhs);
+        const int64_t jend = min((int64_t)j0 + P.chunk, P.nrhs);
         for (int64_t j = (int64_t)j0; j < jend; ++j) {
             T g[KW], u[KW], x[KW], y[KW];
             bool inF[KW];
@@ -822,7 +824,7 @@ nmf_status launch_solve(const SolveParams &P, cudaStream_t s)
     if (pmax < 1)
         pmax = 1;
     const int LS = pmax | 1;   // odd row stride: conflict-free lane-per-row reads
-    int nwarps = BPP_WARPS;
+    int nwarps = P.warps;
     // Stage G (and M) in shared memory when they leave room for >= 2 warps.
     const int staged = MODE != 2 &&
                        mats_bytes(k, MODE) + 2 * per_warp_bytes(pmax, LS) <= SMEM_LIMIT;
@@ -845,7 +847,7 @@ nmf_status launch_solve(const SolveParams &P, cudaStream_t s)
     if (per_sm < 1)
         return NMF_ERR_INVALID_ARG;
     int64_t blocks = (int64_t)per_sm * sm_count();
-    const int64_t need = cdiv(cdiv(P.nrhs, RHS_CHUNK), nwarps);
+    const int64_t need = cdiv(cdiv(P.nrhs, (int64_t)P.chunk), nwarps);
     if (need < blocks)
         blocks = need < 1 ? 1 : need;
     bpp_solve_kernel<KW, PT, MODE><<<(unsigned)blocks, nwarps * 32, smem, s>>>(P, pmax, LS,
@@ -867,6 +869,21 @@ nmf_status launch_modes(const SolveParams &P, cudaStream_t s)
 size_t bpp_work_bytes(int k) { return layout(k).total; }
 
 namespace {
+
+// Launch shape of the solve kernel per k (warps per CTA, right-hand sides per
+// grab of the work counter): {8, 8} until bpp_tune has measured the batch.
+// Every shape computes the same results (each right-hand side is one warp's).
+struct BppShape {
+    int warps = BPP_WARPS, chunk = 8;
+};
+std::mutex g_shape_mu;
+BppShape g_shape[NMF_MAX_K + 1];
+
+BppShape shape_for(int k)
+{
+    std::lock_guard<std::mutex> lock(g_shape_mu);
+    return g_shape[k];
+}
 
 SolveParams solve_params(int k, int64_t nrhs, const double *G, const float *B, float *X,
                          const uint64_t *passive_in, uint64_t *passive_out, int32_t *rounds_out,
@@ -893,7 +910,21 @@ SolveParams solve_params(int k, int64_t nrhs, const double *G, const float *B, f
     P.status_out = status_out;
     P.counter = reinterpret_cast<unsigned long long *>(w + L.counter);
     P.stats = stats_dev;
+    const BppShape sh = shape_for(k);
+    P.warps = sh.warps;
+    P.chunk = sh.chunk;
     return P;
+}
+
+nmf_status launch_solves(const SolveParams &P, cudaStream_t s)
+{
+    if (P.k <= 32)
+        return launch_modes<1>(P, s);
+    if (P.k <= 64)
+        return launch_modes<2>(P, s);
+    if (P.k <= 96)
+        return launch_modes<3>(P, s);
+    return launch_modes<4>(P, s);
 }
 
 }  // namespace
@@ -926,13 +957,65 @@ nmf_status launch_bpp_solve(int k, int64_t nrhs, const double *G, const float *B
         return NMF_OK;
     const SolveParams P = solve_params(k, nrhs, G, B, X, passive_in, passive_out, rounds_out,
                                        status_out, max_rounds, work, stats_dev);
-    if (k <= 32)
-        return launch_modes<1>(P, s);
-    if (k <= 64)
-        return launch_modes<2>(P, s);
-    if (k <= 96)
-        return launch_modes<3>(P, s);
-    return launch_modes<4>(P, s);
+    return launch_solves(P, s);
+}
+
+// Times every candidate launch shape on this batch (after one warm-up each;
+// the passive-set, round and status outputs are left out so every candidate
+// starts from the same partitions) and keeps the fastest for k. X receives
+// the solution.
+nmf_status bpp_tune(int k, int64_t nrhs, const double *G, const float *B, float *X,
+                    const uint64_t *passive_in, int max_rounds, void *work, BppStats *stats_dev,
+                    cudaStream_t s, int *warps_out, int *chunk_out)
+{
+    static const BppShape cand[] = {{8, 1}, {8, 4}, {8, 8}, {8, 32}, {4, 4}, {4, 16}};
+    NMF_TRY(launch_bpp_prep(k, G, work, stats_dev, s));
+    SolveParams P = solve_params(k, nrhs, G, B, X, passive_in, nullptr, nullptr, nullptr,
+                                 max_rounds, work, stats_dev);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    NMF_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return NMF_ERR_CUDA;
+    }
+    BppShape best;
+    float best_ms = -1.0f;
+    nmf_status st = NMF_OK;
+    for (const BppShape &c : cand) {
+        P.warps = c.warps;
+        P.chunk = c.chunk;
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2 && st == NMF_OK; ++rep) {
+            // The prep kernel resets the work counter; re-run it per solve.
+            st = launch_bpp_prep(k, G, work, stats_dev, s);
+            if (st == NMF_OK && cudaEventRecord(e0, s) != cudaSuccess)
+                st = NMF_ERR_CUDA;
+            if (st == NMF_OK)
+                st = launch_solves(P, s);
+            if (st == NMF_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
+                                 cudaEventSynchronize(e1) != cudaSuccess ||
+                                 cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                st = NMF_ERR_CUDA;
+        }
+        if (st != NMF_OK)
+            break;
+        if (best_ms < 0.0f || ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    NMF_TRY(st);
+    {
+        std::lock_guard<std::mutex> lock(g_shape_mu);
+        g_shape[k] = best;
+    }
+    if (warps_out)
+        *warps_out = best.warps;
+    if (chunk_out)
+        *chunk_out = best.chunk;
+    return NMF_OK;
 }
 
 nmf_status launch_bpp(int k, int64_t nrhs, const double *G, const float *B, float *X,

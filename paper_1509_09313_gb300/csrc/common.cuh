@@ -108,6 +108,11 @@ nmf_status launch_bpp(int k, int64_t nrhs, const double *G, const float *B, floa
 // arithmetic mode), then the solves. A prep must complete before its solves
 // and must not overlap another half-step's prep or solves on the same work.
 nmf_status launch_bpp_prep(int k, const double *G, void *work, BppStats *stats_dev, cudaStream_t s);
+// Measures the solve kernel's launch shapes on this batch and keeps the fastest
+// for k (used by every later solve of that k); X receives the solution.
+nmf_status bpp_tune(int k, int64_t nrhs, const double *G, const float *B, float *X,
+                    const uint64_t *passive_in, int max_rounds, void *work, BppStats *stats_dev,
+                    cudaStream_t s, int *warps_out, int *chunk_out);
 nmf_status launch_bpp_solve(int k, int64_t nrhs, const double *G, const float *B, float *X,
                             const uint64_t *passive_in, uint64_t *passive_out, int32_t *rounds_out,
                             int8_t *status_out, int max_rounds, void *work, BppStats *stats_dev,

@@ -30,6 +30,9 @@ Workload recipes (the paper's synthetic sets, Section 6.1.1)
 * ``init_factors``: the non-negative starting point of Algorithm 1, uniform
   [0, 1) for both W (m x k) and H (stored as H^T, n x k). The same seed gives the
   same start on every path (Section 6.1.3).
+* ``stress_factor``: the factor of the batched-BPP stress recipe, uniform
+  [0, 1) with each entry zeroed with probability ``zero_frac`` (its own
+  stream), and ``normal_matrix`` for the right-hand-side draws of that recipe.
 * ``mlp_init``: starting weights of the passive-set proposal network (3k -> h
   -> h -> k), one flat FP32 array [W1 (h x 3k), b1, W2 (h x h), b2, W3 (k x h),
   b3]; each weight matrix uniform in +-sqrt(6 / (fan_in + fan_out)) (Glorot and
@@ -217,3 +220,19 @@ def batch_order(n: int, epoch: int, seed: int = DEFAULT_SEED) -> np.ndarray:
     """A seeded permutation of range(n) for one training epoch (sort of uniform keys)."""
     u = uniform01(seed + epoch, TID_MLP_BATCH, np.arange(n, dtype=np.uint64))
     return np.argsort(u, kind="stable").astype(np.int64)
+
+
+def stress_factor(rows: int, k: int, zero_frac: float = 0.3, seed: int = DEFAULT_SEED) -> np.ndarray:
+    """rows x k float32: uniform [0, 1), each entry zeroed with probability zero_frac."""
+    W = uniform_matrix(seed, TID_STRESS_W, rows, k)
+    Z = uniform_matrix(seed, TID_STRESS_ZERO, rows, k)
+    return np.where(Z < zero_frac, 0.0, W).astype(np.float32)
+
+
+def normal_matrix(seed: int, tensor_pair: tuple[int, int], rows: int, cols: int,
+                  row0: int = 0) -> np.ndarray:
+    """rows x cols standard normals (Box-Muller on the pair of streams), rows
+    row0.. of a matrix with `cols` columns."""
+    r = np.arange(row0, row0 + rows, dtype=np.uint64)[:, None]
+    c = np.arange(cols, dtype=np.uint64)[None, :]
+    return normal(seed, tensor_pair, r * np.uint64(cols) + c)

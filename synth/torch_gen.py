@@ -66,3 +66,14 @@ def dense_planted_device(m: int, n: int, k: int, sigma: float, seed: int,
         A[r0:r1] = blk.to(torch.float32)
         del blk
     return A
+
+
+def normal_device(seed: int, tensor_pair, rows: int, cols: int, device: torch.device,
+                  row0: int = 0) -> torch.Tensor:
+    """``synth.normal_matrix`` on the device (float64)."""
+    r = torch.arange(row0, row0 + rows, dtype=torch.int64, device=device)[:, None]
+    c = torch.arange(cols, dtype=torch.int64, device=device)[None, :]
+    idx = r * cols + c
+    u1 = _uniform(seed, tensor_pair[0], idx, True)
+    u2 = _uniform(seed, tensor_pair[1], idx, False)
+    return torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * np.pi * u2)

@@ -1,0 +1,98 @@
+"""The batched-BPP stress configuration: 10^6 right-hand sides with k = 100 in
+one launch (nmf_nls_bpp).
+
+The Gram is G = W^T W of W (200000 x 100, uniform [0, 1) with 30% of the
+entries zeroed). Right-hand sides b = W^T a with a uniform in [0, 1)^200000
+would cost 2e13 flops to form, so they are drawn from the distribution they
+follow by the central limit theorem: mean W^T 1 / 2, covariance G / 12, i.e.
+b = W^T 1 / 2 + L z / sqrt(12) with G = L L^T and z standard normal. G and the
+right-hand sides are formed with plain PyTorch FP64 ops (test inputs only).
+
+The launch is timed (printed); every status must be OK; a sample of 10^4
+right-hand sides is compared with the FP64 oracle: values within the FP32
+bound and passive sets equal wherever the KKT margin is clear."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from synth import torch_gen
+
+pytestmark = pytest.mark.gpu
+
+ROWS, K, NRHS = 200000, 100, 1000000
+
+
+@pytest.fixture(scope="module")
+def nmf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1509_09313_gb300 as lib
+    return lib
+
+
+def _stress_inputs(dev):
+    W = torch.from_numpy(synth.stress_factor(ROWS, K)).to(dev).double()
+    G = W.T @ W
+    mean = 0.5 * W.sum(dim=0)
+    L = torch.linalg.cholesky(G)
+    B = torch.empty((NRHS, K), dtype=torch.float32, device=dev)
+    pair = (synth.TID_STRESS_A, synth.TID_NOISE_U2)
+    for r0 in range(0, NRHS, 100000):
+        z = torch_gen.normal_device(synth.DEFAULT_SEED, pair, 100000, K, dev, row0=r0)
+        B[r0:r0 + 100000] = (mean + z @ L.T / np.sqrt(12.0)).float()
+        del z
+    return G.contiguous(), B
+
+
+def test_stress_one_launch_million_rhs(nmf):
+    dev = torch.device("cuda")
+    G, B = _stress_inputs(dev)
+    torch.cuda.synchronize()
+    nmf.nmf_nls_bpp(G, B)                      # warm-up (module load, attributes)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record()
+    r = nmf.nmf_nls_bpp(G, B)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    rounds = r["rounds"].double()
+    print(f"BPP stress: {NRHS} RHS, k={K}: {ms:.2f} ms ({NRHS / ms * 1e3:.3e} RHS/s), "
+          f"rounds mean {rounds.mean().item():.3f} max {int(rounds.max().item())}, "
+          f"host {1e3 * (time.perf_counter() - t0):.1f} ms")
+    assert r["worst"] == nmf.NMF_OK
+    assert (r["status"] == 0).all()
+    # FP64 oracle on every 100th right-hand side.
+    idx = torch.arange(0, NRHS, 100, device=dev)
+    Gh = G.cpu().numpy()
+    Bs = B[idx].double().cpu().numpy()
+    Xo, Po, Ro, So, wo = oracle.bpp(Gh, Bs)
+    X = r["X"][idx].double().cpu().numpy()
+    P = nmf.passive_to_bool(r["passive"][idx], K).cpu().numpy()
+    cond = np.linalg.cond(Gh)
+    err = np.linalg.norm(X - Xo) / np.linalg.norm(Xo)
+    print(f"cond(G) {cond:.3e}, sample rel err {err:.2e}")
+    assert err <= 20 * cond * 6e-8
+    Y = Xo @ Gh - Bs
+    xm = np.where(Po, Xo, np.inf).min(axis=1) / np.maximum(np.abs(Xo).max(axis=1), 1e-300)
+    ym = np.where(~Po.astype(bool), Y, np.inf).min(axis=1) / np.maximum(np.abs(Bs).max(axis=1), 1e-300)
+    ok = np.minimum(xm, ym) >= 1e-3
+    assert ok.mean() > 0.3
+    assert np.array_equal(P[ok], Po.astype(bool)[ok])
+    R = r["rounds"][idx].cpu().numpy()
+    assert (R[ok] == Ro[ok]).mean() >= 0.98
+    # Autotuned launch shape for k = 100: same bits, timed again.
+    warps, chunk, Xt = nmf.nmf_nls_bpp_tune(G, B)
+    assert torch.equal(Xt, r["X"])
+    e0.record()
+    r2 = nmf.nmf_nls_bpp(G, B)
+    e1.record()
+    torch.cuda.synchronize()
+    print(f"tuned shape: {warps} warps per CTA, {chunk} RHS per grab: "
+          f"{e0.elapsed_time(e1):.2f} ms")
+    assert torch.equal(r2["X"], r["X"]) and torch.equal(r2["passive"], r["passive"])
