@@ -35,7 +35,11 @@ WORKLOADS = {
                      "dense A=W0*H0+|N(0,0.05^2)| 24000x16000 k=50 fp32 (1.5 GB)"),
     "dense-small": (2000, 1000, 10, 0.01,
                     "dense A=W0*H0+|N(0,0.01^2)| 2000x1000 k=10 fp32"),
+    "sparse-large": (2000000, 1000000, 50, None,
+                     "sparse CSR 2000000x1000000, 20M uniform draws, values U(0,1], k=50"),
 }
+# Sparse workloads: number of uniform position draws (duplicates merged).
+SPARSE_DRAWS = {"sparse-large": 20000000}
 SEED = 1509
 METRIC = "ANLS-BPP iterations/s"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -145,6 +149,37 @@ def oracle_sample(m, n, k, sigma, steps, warm: bool):
     return 1.0 / (dt * scale), sample, orc.num_threads(), dt
 
 
+def oracle_sample_sparse(m, n, k, draws, steps, warm: bool, csr):
+    """Time the FP64 oracle on the top-left (m/20) x (n/20) block of the same
+    CSR matrix and scale by the row-plus-column ratio (the NLS work, one solve
+    per row and per column, dominates the sparse iteration)."""
+    import numpy as np
+    import oracle
+    import synth
+    rowptr, colidx, vals = csr
+    ms, ns = max(1, m // 20), max(1, n // 20)
+    keep_r = np.zeros(len(colidx), dtype=bool)
+    keep_r[:rowptr[ms]] = True
+    keep = keep_r & (colidx < ns)
+    rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(rowptr))
+    r_c, c_c, v_c = rows[keep], colidx[keep], vals[keep]
+    rp = np.zeros(ms + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(np.bincount(r_c, minlength=ms))
+    W0, Ht0 = synth.init_factors(ms, ns, k, seed=SEED)
+    orc = oracle.default()
+    crop = (rp, np.ascontiguousarray(c_c), np.ascontiguousarray(v_c))
+    r = orc.anls(None, W0, Ht0, iters=1, warm=warm, csr=crop, shape=(ms, ns))
+    t0 = time.perf_counter()
+    orc.anls(None, r["W"].astype("float32"), r["Ht"].astype("float32"), iters=steps, warm=warm,
+             csr=crop, shape=(ms, ns))
+    dt = (time.perf_counter() - t0) / steps
+    scale = (m + n) / (ms + ns)
+    sample = (f"oracle ANLS iterations on the top-left {ms}x{ns} block of the same CSR "
+              f"({len(c_c)} nonzeros, k={k}), {steps} iterations, time per iteration x "
+              f"{scale:.1f} (rows+columns ratio)")
+    return 1.0 / (dt * scale), sample, orc.num_threads(), dt
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -152,7 +187,13 @@ def run_reference(args, rank, world):
     import oracle
     oracle.build()
     steps = max(1, args.steps)
-    value, sample, cores, dt = oracle_sample(m, n, k, sigma, steps, args.start == "warm")
+    if args.workload in SPARSE_DRAWS:
+        import synth
+        csr = synth.csr_uniform(m, n, SPARSE_DRAWS[args.workload], seed=SEED)
+        value, sample, cores, dt = oracle_sample_sparse(m, n, k, SPARSE_DRAWS[args.workload],
+                                                        steps, args.start == "warm", csr)
+    else:
+        value, sample, cores, dt = oracle_sample(m, n, k, sigma, steps, args.start == "warm")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s",
             "n_gpus": world, "steps": steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
@@ -178,8 +219,17 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
 
+    sparse = args.workload in SPARSE_DRAWS
+    if sparse:
+        args.precision = "fp32"     # SpMM and the sparse objective have one precision
     t_gen = time.perf_counter()
-    A = torch_gen.dense_planted_device(m, n, k, sigma, SEED, dev)
+    csr_host = None
+    if sparse:
+        csr_host = synth.csr_uniform(m, n, SPARSE_DRAWS[args.workload], seed=SEED)
+        A = tuple(torch.from_numpy(x).to(dev) for x in csr_host)
+        nnz = int(csr_host[1].size)
+    else:
+        A = torch_gen.dense_planted_device(m, n, k, sigma, SEED, dev)
     W0h, Ht0h = synth.init_factors(m, n, k, seed=SEED)
     W0 = torch.from_numpy(W0h).to(dev)
     Ht0 = torch.from_numpy(Ht0h).to(dev)
@@ -189,7 +239,8 @@ def run_ours(args, rank, world, local_rank):
     learned = args.start == "learned"
     h = nmf.nmf_init(A, W0, Ht0, precision=args.precision,
                      start="cold" if learned else args.start,
-                     max_bpp_rounds=args.max_rounds, objective_every=True)
+                     max_bpp_rounds=args.max_rounds, objective_every=True,
+                     shape=(m, n) if sparse else None)
     net = None
     if learned:
         # Learned starting partitions: the proposal network trains on every
@@ -247,7 +298,18 @@ def run_ours(args, rank, world, local_rank):
     pk, pk_kind = peaks()
     bytes_mm = 4.0 * m * n + 4.0 * (m + n) * k     # A once + factor in + product out
     flops_mm = 2.0 * m * n * k
-    if args.precision == "fp32":
+    if sparse:
+        # Compulsory bytes of one SpMM, averaged over A H^T and A^T W: CSR
+        # (4-byte index + 4-byte value per nonzero, 8-byte row pointers), the
+        # dense operand read once, the product written once.
+        bytes_mm = 8.0 * nnz + 4.0 * (m + n) + 4.0 * (m + n) * k
+        flops_mm = 2.0 * nnz * k
+        achieved = bytes_mm / (mm_ms / 1000.0) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "kernel": "spmm_kernel",
+                "peak_source": f"{pk_kind} hbm_gbs", "bytes": "compulsory",
+                "achieved_with_gathers_gbs": (bytes_mm + 4.0 * nnz * k) / (mm_ms / 1000.0) / 1e9}
+    elif args.precision == "fp32":
         fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         achieved = flops_mm / (mm_ms / 1000.0) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
@@ -267,8 +329,11 @@ def run_ours(args, rank, world, local_rank):
     # starting point, nmf_init, K iterations, download W, H^T and the objective.
     e2e = None
     if not args.no_e2e:
-        A_host = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
-        A_host.copy_(A)
+        if sparse:
+            A_host = tuple(torch.from_numpy(x).pin_memory() for x in csr_host)
+        else:
+            A_host = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
+            A_host.copy_(A)
         W0_host = torch.from_numpy(W0h).pin_memory()
         Ht0_host = torch.from_numpy(Ht0h).pin_memory()
         W_out = torch.empty((m, k), dtype=torch.float32, pin_memory=True)
@@ -277,12 +342,17 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        A.copy_(A_host, non_blocking=True)
+        if sparse:
+            for dst, src in zip(A, A_host):
+                dst.copy_(src, non_blocking=True)
+        else:
+            A.copy_(A_host, non_blocking=True)
         W0.copy_(W0_host, non_blocking=True)
         Ht0.copy_(Ht0_host, non_blocking=True)
         h2 = nmf.nmf_init(A, W0, Ht0, precision=args.precision,
                           start="cold" if learned else args.start,
-                          max_bpp_rounds=args.max_rounds, objective_every=True)
+                          max_bpp_rounds=args.max_rounds, objective_every=True,
+                          shape=(m, n) if sparse else None)
         if learned:
             h2.nmf_set_proposal(net, "use")    # the network trained above
         h2.nmf_iterate(args.steps)
@@ -298,7 +368,8 @@ def run_ours(args, rank, world, local_rank):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
         h2.nmf_destroy()
-        h2d = 4 * (m * n + (m + n) * k)
+        h2d = (sum(x.numel() * x.element_size() for x in A_host) if sparse else 4 * m * n) + \
+            4 * (m + n) * k
         d2h = 4 * (m + n) * k + 8 * len(f_e2e)
         e2e = {"value": world * args.steps / dt, "unit": "iter/s",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
@@ -308,7 +379,13 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, sample, cores, _ = oracle_sample(m, n, k, sigma, args.cpu_steps, args.start == "warm")
+        if sparse:   # ~7 s per crop iteration on 16 cores: keep the sample near 20 s
+            v, sample, cores, _ = oracle_sample_sparse(m, n, k, SPARSE_DRAWS[args.workload],
+                                                       min(args.cpu_steps, 3),
+                                                       args.start == "warm", csr_host)
+        else:
+            v, sample, cores, _ = oracle_sample(m, n, k, sigma, args.cpu_steps,
+                                                args.start == "warm")
         cpu = {"value": v, "unit": "iter/s", "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
@@ -322,7 +399,9 @@ def run_ours(args, rank, world, local_rank):
                 "config": {"workload": desc, "precision": args.precision, "start": args.start,
                            "seed": SEED,
                            "l2": "small input (L2-resident)" if args.workload == "dense-small"
-                           else f"inputs larger than L2 (A = {4 * m * n / 1e9:.1f} GB)",
+                           else (f"CSR {8 * nnz / 1e9:.2f} GB + factors {8 * (m + n) * k / 1e9:.2f} GB, "
+                                 "larger than L2" if sparse
+                                 else f"inputs larger than L2 (A = {4 * m * n / 1e9:.1f} GB)"),
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],

@@ -159,8 +159,7 @@ def csr_uniform(m: int, n: int, nnz_draws: int, seed: int = DEFAULT_SEED):
     c = (ukey % n).astype(np.int32)
     v = vals[first]
     rowptr = np.zeros(m + 1, dtype=np.int64)
-    np.add.at(rowptr, r + 1, 1)
-    rowptr = np.cumsum(rowptr)
+    rowptr[1:] = np.cumsum(np.bincount(r, minlength=m))
     return rowptr, np.ascontiguousarray(c), np.ascontiguousarray(v)
 
 
