@@ -21,7 +21,7 @@
 //    perturbs entry (i, j) relative to sqrt(G_ii G_jj), so a factor that is
 //    merely badly scaled (one row of H much smaller than the rest, common in
 //    early iterations) costs nothing.
-//  * bpp_solve_kernel: persistent, one warp per right-hand side, G and M in
+//  * solve kernels: persistent, one warp per right-hand side, G and M in
 //    shared memory. Lane l holds indices l, l+32, ... of g, x, y and of the
 //    unconstrained solution u = M g. Each exchange round solves the smaller of
 //    two equivalent systems:
@@ -29,17 +29,19 @@
 //      complement  M_AA y_A = -u_A,  x_F = u_F + M_FA y_A  (|A| x |A|)
 //    (the second follows from G x = g + y with y supported on A and x_A = 0),
 //    by a warp-cooperative Cholesky in shared memory with shuffle-broadcast
-//    substitutions. In FP32 it then refines once (residual g_F - G_FF x_F
-//    solved through the same factor: the explicit inverse alone is not
-//    backward stable) and recomputes y from G; in FP64 neither is needed.
-//    Cost per round O(min(|F|,|A|)^3 + k |F|) instead of O(|F|^3). In FP32 a
-//    pivot below 1e-4 of its diagonal sends that system to FP64, and a sign
-//    test counts as violated only beyond 2^-20 of the problem's scale in the
+//    substitutions. Cost per round O(min(|F|,|A|)^3 + k |F|) instead of
+//    O(|F|^3). bpp_solve32_kernel (bpp32.cu) runs mode 0: it refines once
+//    (residual g_F - G_FF x_F solved through the same factor: the explicit
+//    inverse alone is not backward stable), recomputes y from G, and counts a
+//    sign test as violated only beyond 2^-20 of the problem's scale in the
 //    diagonally scaled variables (x_i sqrt(G_ii) against max over F of
 //    |x_j| sqrt(G_jj); y_i / sqrt(G_ii) against max of |g_j| / sqrt(G_jj)):
 //    values within FP32 noise of zero are degenerate ties that would
 //    otherwise make the exchange rules cycle. The final x is clamped at 0
-//    there. FP64 modes use the strict test.
+//    there. A system whose FP32 pivot falls below 1e-4 of its diagonal
+//    defers its right-hand side to a second pass of bpp_solve_kernel in FP64.
+//    bpp_solve_kernel (here) runs modes 1 and 2 in FP64 with the strict sign
+//    test and no refinement.
 //  * Every loop is bounded: a solve stops at max_rounds with status
 //    NOT_CONVERGED; there are no spin-waits.
 //
@@ -49,21 +51,19 @@
 
 #include <mutex>
 
-#include "common.cuh"
+#include "bpp_internal.cuh"
 
 namespace nmf {
 namespace {
 
+using namespace bpp;
+
 constexpr int BPP_WARPS = 8;               // most warps per CTA (launch bound)
 constexpr int BPP_THREADS = BPP_WARPS * 32;
-constexpr float PIVOT_TOL = 1e-4f;
-constexpr double PIVOT_TOL64 = 1e-13;
-constexpr double COND_FP32 = 1e4;          // scaled cond_1(G) up to which solves run in FP32
-constexpr float FEAS_TOL32 = 9.5367431640625e-07f;   // 2^-20
 
 // Workspace layout (bytes, 256-aligned pieces).
 struct WorkLayout {
-    size_t g32, m32, m64, usable, flags, counter, total;
+    size_t g32, m32, m64, usable, flags, counters, defer, total;
 };
 
 WorkLayout layout(int k)
@@ -76,7 +76,8 @@ WorkLayout layout(int k)
     w.m64 = off; off += al(sizeof(double) * k * k);
     w.usable = off; off += al(sizeof(uint32_t) * 4);
     w.flags = off; off += al(sizeof(int) * 4);
-    w.counter = off; off += al(sizeof(unsigned long long));
+    w.counters = off; off += al(sizeof(unsigned long long) * CNT_WORDS);
+    w.defer = off; off += al(sizeof(int64_t) * DEFER_CAP);
     w.total = off;
     return w;
 }
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(PREP_THREADS)
     bpp_prep_kernel(const double *__restrict__ G, int k, float *__restrict__ G32,
                     float *__restrict__ M32, double *__restrict__ M64,
                     uint32_t *__restrict__ usable_words, int *__restrict__ flags,
-                    unsigned long long *__restrict__ counter, BppStats *__restrict__ stats)
+                    unsigned long long *__restrict__ counters, BppStats *__restrict__ stats)
 {
     extern __shared__ double sm[];
     double *L = sm;                                   // u x u, later M (u x u)
@@ -119,7 +120,8 @@ __global__ void __launch_bounds__(PREP_THREADS)
         s_u = u;
         s_ok = u > 0;
         s_norm[0] = s_norm[1] = 0ull;
-        *counter = 0ull;
+        for (int c = 0; c < CNT_WORDS; ++c)
+            counters[c] = 0ull;
     }
     __syncthreads();
     const int u = s_u;
@@ -363,37 +365,6 @@ __device__ __forceinline__ void warp_matvec(const T *__restrict__ Mat, int k, co
     __syncwarp();
 }
 
-template <typename T>
-__device__ __forceinline__ T warp_max(T v)
-{
-    for (int o = 16; o > 0; o >>= 1)
-        v = max(v, __shfl_xor_sync(FULL, v, o));
-    return v;
-}
-
-struct SolveParams {
-    int k, nwords, max_rounds;
-    int warps, chunk;              // warps per CTA; right-hand sides per counter grab
-    int64_t nrhs;
-    const float *G32, *M32;
-    const double *G64, *M64;
-    const uint32_t *usable_words;
-    const int *flags;
-    const float *B;
-    float *X;
-    const uint64_t *pin;
-    uint64_t *pout;
-    int32_t *rounds_out;
-    int8_t *status_out;
-    unsigned long long *counter;
-    BppStats *stats;
-};
-
-__device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
-
-template <int MODE> struct ModeType { using T = double; };
-template <> struct ModeType<0> { using T = float; };
-
 // Per warp: index list (128 ints), right-hand side and reciprocal pivots of
 // the compact system (128 doubles each), the matrix-vector staging vector
 // (128 doubles), the p x LS factor; rounded to 16 bytes.
@@ -403,27 +374,42 @@ __host__ __device__ inline size_t per_warp_bytes(int pmax, int LS)
     return (b + 15) & ~size_t(15);
 }
 
-// Shared-memory matrices of a mode: mode 0 G32 and M32, mode 1 G64 and M64,
-// mode 2 none (no M; G64 read through L1/L2).
+// Shared-memory matrices of a mode: mode 1 G64 and M64, mode 2 none (no M;
+// G64 read through L1/L2).
 __host__ __device__ inline size_t mats_bytes(int k, int mode)
 {
-    const size_t b = mode == 0 ? 2 * sizeof(float) * (size_t)k * k
-                     : mode == 1 ? 2 * sizeof(double) * (size_t)k * k
-                                 : 0;
+    const size_t b = mode == 1 ? 2 * sizeof(double) * (size_t)k * k : 0;
     return (b + 15) & ~size_t(15);
 }
 
-// KW = index slots per lane (k <= 32 KW); PT = compact-system rows per lane
-// (pmax <= 32 PT). The kernel of each MODE returns at once unless the prep
-// kernel chose that mode, so the host never waits for the verdict.
+// FP64 solves. KW = index slots per lane (k <= 32 KW); PT = compact-system
+// rows per lane (pmax <= 32 PT). The kernel of each MODE returns at once
+// unless the prep kernel chose that mode, so the host never waits for the
+// verdict. With list_pass set (MODE 1 only) it is the second pass of mode 0:
+// it re-solves, from their starting partitions, the right-hand sides that the
+// FP32 kernel deferred (all of them if more than DEFER_CAP were).
 template <int KW, int PT, int MODE>
 __global__ void __launch_bounds__(BPP_THREADS, 2)
-    bpp_solve_kernel(const SolveParams P, int pmax, int LS, int staged)
+    bpp_solve_kernel(const SolveParams P, int pmax, int LS, int staged, int list_pass)
 {
-    using T = typename ModeType<MODE>::T;
+    using T = double;
     constexpr bool HAVE_M = MODE != 2;
-    if (P.flags[0] != MODE)
+    int64_t nwork = P.nrhs;
+    bool use_list = false;
+    unsigned long long *counter = &P.counters[CNT_WORK];
+    if (list_pass) {
+        if (P.flags[0] != 0)
+            return;
+        // Written by the FP32 kernel earlier in the same stream.
+        const unsigned long long nd = P.counters[CNT_DEFERRED];
+        if (nd == 0)
+            return;
+        use_list = nd <= (unsigned long long)DEFER_CAP;
+        nwork = use_list ? (int64_t)nd : P.nrhs;
+        counter = &P.counters[CNT_DEFER_WORK];
+    } else if (P.flags[0] != MODE) {
         return;
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int k = P.k;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -432,21 +418,15 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
     if (!staged) {
         // Matrices too large for shared memory next to the per-warp space:
         // read them through L1/L2 (mode 1 at k > ~100, mode 2 always).
-        Gs = reinterpret_cast<const T *>(MODE == 0 ? (const void *)P.G32 : (const void *)P.G64);
+        Gs = P.G64;
         if (HAVE_M)
-            Ms = reinterpret_cast<const T *>(MODE == 0 ? (const void *)P.M32
-                                                       : (const void *)P.M64);
+            Ms = P.M64;
     } else {
         T *gsh = reinterpret_cast<T *>(smem_raw);
         T *msh = gsh + k * k;
         for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-            if (MODE == 0) {
-                gsh[e] = (T)P.G32[e];
-                msh[e] = (T)P.M32[e];
-            } else {
-                gsh[e] = (T)P.G64[e];
-                msh[e] = (T)P.M64[e];
-            }
+            gsh[e] = P.G64[e];
+            msh[e] = P.M64[e];
         }
         Gs = gsh;
         Ms = msh;
@@ -454,14 +434,10 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
     unsigned char *wp =
         smem_raw + (staged ? mats_bytes(k, MODE) : 0) + warp * per_warp_bytes(pmax, LS);
     int *widx = reinterpret_cast<int *>(wp);
-    double *zbuf64 = reinterpret_cast<double *>(wp + 128 * sizeof(int));
-    double *invd64 = zbuf64 + 128;
-    double *stage64 = invd64 + 128;
-    double *Lw64 = stage64 + 128;
-    T *stage = reinterpret_cast<T *>(stage64);
-    T *zbuf = reinterpret_cast<T *>(zbuf64);
-    T *invd = reinterpret_cast<T *>(invd64);
-    T *Lw = reinterpret_cast<T *>(Lw64);
+    T *zbuf = reinterpret_cast<T *>(wp + 128 * sizeof(int));
+    T *invd = zbuf + 128;
+    T *stage = invd + 128;
+    T *Lw = stage + 128;
     __syncthreads();
 
     bool usable[KW];
@@ -472,49 +448,33 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
         usable[s] = (w >> lane) & 1u;
         nU += __popc(w);
     }
-    const T tolrel = MODE == 0 ? (T)FEAS_TOL32 : (T)0;
-    // sqrt(G_ii) of this lane's indices (1 where unusable): the scale of the
-    // FP32 sign tolerances.
-    T dsq[KW];
-#pragma unroll
-    for (int s = 0; s < KW; ++s) {
-        const int i = lane + 32 * s;
-        dsq[s] = (T)1;
-        if (MODE == 0 && usable[s] && i < k)
-            dsq[s] = sqrt(Gs[i * k + i]);
-    }
 
-    unsigned long long st_rounds = 0, st_max = 0, st_fp64 = 0, st_nc = 0, st_sing = 0,
-                       st_nf = 0, st_rhs = 0;
+    unsigned long long st_rounds = 0, st_max = 0, st_nc = 0, st_sing = 0, st_nf = 0, st_rhs = 0;
 
     for (;;) {
         unsigned long long j0 = 0;
         if (lane == 0)
-            j0 = atomicAdd(P.counter, (unsigned long long)P.chunk);
+            j0 = atomicAdd(counter, (unsigned long long)P.chunk);
         j0 = __shfl_sync(FULL, j0, 0);
-        if (j0 >= (unsigned long long)P.nrhs)
+        if (j0 >= (unsigned long long)nwork)
             break;
-        const int64_t jend = min((int64_t)j0 + P.chunk, P.nrhs);
-        for (int64_t j = (int64_t)j0; j < jend; ++j) {
+        const int64_t jend = min((int64_t)j0 + P.chunk, nwork);
+        for (int64_t jj = (int64_t)j0; jj < jend; ++jj) {
+            const int64_t j = use_list ? P.defer[jj] : jj;
             T g[KW], u[KW], x[KW], y[KW];
             bool inF[KW];
             bool bad = false;
-            T gmax = 0;
 #pragma unroll
             for (int s = 0; s < KW; ++s) {
                 const int i = lane + 32 * s;
                 g[s] = i < k ? (T)P.B[j * k + i] : (T)0;
                 bad |= !isfinite(g[s]);
-                gmax = max(gmax, fabs(g[s]) / dsq[s]);
                 u[s] = 0;
                 x[s] = 0;
                 y[s] = -g[s];
                 inF[s] = false;
             }
             bad = __any_sync(FULL, bad);
-            gmax = warp_max(gmax);
-            const T ytol = tolrel * gmax;
-            T xtol = 0;
             int status = NMF_OK;
             int rounds = 0;
             if (bad) {
@@ -567,60 +527,25 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                     }
                     const int p = pos;
                     __syncwarp();
-                    bool ok = true, refine = true;
                     if (p > 0) {
-                        ok = warp_chol_factor<T, T, PT>(comp ? Ms : Gs, k, widx, p, Lw, LS, invd,
-                                                        MODE == 0 ? (T)PIVOT_TOL
-                                                                  : (T)PIVOT_TOL64,
-                                                        lane);
-                        if (ok) {
-                            T r[PT];
+                        if (!warp_chol_factor<T, T, PT>(comp ? Ms : Gs, k, widx, p, Lw, LS, invd,
+                                                        (T)PIVOT_TOL64, lane))
+                            return NMF_ERR_SINGULAR_GRAM;
+                        T r[PT];
 #pragma unroll
-                            for (int t = 0; t < PT; ++t) {
-                                const int a = lane + 32 * t;
-                                r[t] = a < p ? zbuf[a] : (T)0;
-                            }
-                            warp_chol_subst<T, PT>(p, Lw, LS, invd, r, lane);
+                        for (int t = 0; t < PT; ++t) {
+                            const int a = lane + 32 * t;
+                            r[t] = a < p ? zbuf[a] : (T)0;
+                        }
+                        warp_chol_subst<T, PT>(p, Lw, LS, invd, r, lane);
 #pragma unroll
-                            for (int t = 0; t < PT; ++t) {
-                                const int a = lane + 32 * t;
-                                if (a < p)
-                                    zbuf[a] = r[t];
-                            }
-                        } else if (MODE == 0) {
-                            // Ill-conditioned in FP32: factor and solve in FP64.
-                            refine = false;
-                            st_fp64 += (lane == 0);
-                            __syncwarp();
-#pragma unroll
-                            for (int s = 0; s < KW; ++s)
-                                if (inS[s])
-                                    zbuf64[rank[s]] = (double)(comp ? -u[s] : g[s]);
-                            __syncwarp();
-                            double r64[PT];
-#pragma unroll
-                            for (int t = 0; t < PT; ++t) {
-                                const int a = lane + 32 * t;
-                                r64[t] = a < p ? zbuf64[a] : 0.0;
-                            }
-                            __syncwarp();
-                            ok = warp_chol_factor<double, double, PT>(
-                                comp ? P.M64 : P.G64, k, widx, p, Lw64, LS, invd64, PIVOT_TOL64,
-                                lane);
-                            if (ok) {
-                                warp_chol_subst<double, PT>(p, Lw64, LS, invd64, r64, lane);
-#pragma unroll
-                                for (int t = 0; t < PT; ++t) {
-                                    const int a = lane + 32 * t;
-                                    if (a < p)
-                                        zbuf[a] = (T)r64[t];
-                                }
-                            }
+                        for (int t = 0; t < PT; ++t) {
+                            const int a = lane + 32 * t;
+                            if (a < p)
+                                zbuf[a] = r[t];
                         }
                         __syncwarp();
                     }
-                    if (!ok)
-                        return NMF_ERR_SINGULAR_GRAM;
 #pragma unroll
                     for (int s = 0; s < KW; ++s) {
                         const int i = lane + 32 * s;
@@ -635,65 +560,9 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                         }
                     }
                     __syncwarp();
-                    // One refinement step through the same factor (FP32 only:
-                    // in FP64 the explicit inverse is accurate to cond * 1e-16).
-                    if (MODE == 0 && refine && nF > 0) {
-                        T w[KW], res[KW], up[KW];
-#pragma unroll
-                        for (int s = 0; s < KW; ++s) {
-                            w[s] = 0;
-                            up[s] = 0;
-                        }
-                        warp_matvec<T, KW>(Gs, k, x, w, stage, lane);
-#pragma unroll
-                        for (int s = 0; s < KW; ++s)
-                            res[s] = inF[s] ? g[s] - w[s] : (T)0;
-                        if (comp)
-                            warp_matvec<T, KW>(Ms, k, res, up, stage, lane);
-#pragma unroll
-                        for (int s = 0; s < KW; ++s)
-                            if (inS[s])
-                                zbuf[rank[s]] = comp ? -up[s] : res[s];
-                        __syncwarp();
-                        T r[PT];
-#pragma unroll
-                        for (int t = 0; t < PT; ++t) {
-                            const int a = lane + 32 * t;
-                            r[t] = a < p ? zbuf[a] : (T)0;
-                        }
-                        __syncwarp();
-                        warp_chol_subst<T, PT>(p, Lw, LS, invd, r, lane);
-#pragma unroll
-                        for (int t = 0; t < PT; ++t) {
-                            const int a = lane + 32 * t;
-                            if (a < p)
-                                zbuf[a] = r[t];
-                        }
-                        __syncwarp();
-#pragma unroll
-                        for (int s = 0; s < KW; ++s) {
-                            const int i = lane + 32 * s;
-                            T dx;
-                            if (!comp) {
-                                dx = inF[s] ? zbuf[rank[s]] : (T)0;
-                            } else {
-                                T acc = up[s];
-                                if (inF[s])
-                                    for (int a = 0; a < p; ++a)
-                                        acc = fma(Ms[widx[a] * k + i], zbuf[a], acc);
-                                dx = inF[s] ? acc : (T)0;
-                            }
-                            x[s] += dx;
-                        }
-                        __syncwarp();
-                    }
-                    // y = G x - g off F, 0 on F: recomputed from G in FP32; in
-                    // FP64 the complement solve's y_A is used as it stands.
-                    T xm = 0;
-#pragma unroll
-                    for (int s = 0; s < KW; ++s)
-                        xm = max(xm, inF[s] ? fabs(x[s]) * dsq[s] : (T)0);
-                    if (MODE != 0 && comp) {
+                    // y = G x - g off F, 0 on F: the complement solve gives y_A
+                    // directly (accurate in FP64); the direct one recomputes it.
+                    if (comp) {
 #pragma unroll
                         for (int s = 0; s < KW; ++s)
                             y[s] = inS[s] ? zbuf[rank[s]] : (inF[s] ? (T)0 : -g[s]);
@@ -707,7 +576,6 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                         for (int s = 0; s < KW; ++s)
                             y[s] = inF[s] ? (T)0 : w[s] - g[s];
                     }
-                    xtol = tolrel * warp_max(xm);   // scaled: compares x_i * d_i
                     return NMF_OK;
                 };
 
@@ -724,8 +592,7 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                     int nV = 0;
 #pragma unroll
                     for (int s = 0; s < KW; ++s) {
-                        inf[s] = usable[s] && (inF[s] ? (x[s] * dsq[s] < -xtol)
-                                                      : (y[s] < -ytol * dsq[s]));
+                        inf[s] = usable[s] && (inF[s] ? (x[s] < (T)0) : (y[s] < (T)0));
                         vm[s] = __ballot_sync(FULL, inf[s]);
                         nV += __popc(vm[s]);
                     }
@@ -763,7 +630,7 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                 bool nf = false;
 #pragma unroll
                 for (int s = 0; s < KW; ++s) {
-                    x[s] = x[s] > (T)0 ? x[s] : (T)0;   // within-tolerance negatives -> 0
+                    x[s] = x[s] > (T)0 ? x[s] : (T)0;
                     nf |= !isfinite(x[s]);
                 }
                 if (__any_sync(FULL, nf) && status == NMF_OK)
@@ -803,11 +670,13 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
             }
         }
     }
+    // (After an overflow of the deferral list the second pass re-solves the
+    // whole batch, and the right-hand-side and round counts include both
+    // passes.)
     if (lane == 0 && st_rhs) {
         atomicAdd(&P.stats->rhs, st_rhs);
         atomicAdd(&P.stats->rounds, st_rounds);
         atomicMax(&P.stats->max_rounds, st_max);
-        if (st_fp64) atomicAdd(&P.stats->fp64_solves, st_fp64);
         if (st_nc) atomicAdd(&P.stats->not_converged, st_nc);
         if (st_sing) atomicAdd(&P.stats->singular, st_sing);
         if (st_nf) atomicAdd(&P.stats->nonfinite, st_nf);
@@ -817,15 +686,15 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 
 template <int KW, int PT, int MODE>
-nmf_status launch_solve(const SolveParams &P, cudaStream_t s)
+nmf_status launch_solve(const SolveParams &P, int list_pass, cudaStream_t s)
 {
     const int k = P.k;
     int pmax = MODE == 2 ? k : k / 2;
     if (pmax < 1)
         pmax = 1;
     const int LS = pmax | 1;   // odd row stride: conflict-free lane-per-row reads
-    int nwarps = P.warps;
-    // Stage G (and M) in shared memory when they leave room for >= 2 warps.
+    int nwarps = P.warps < BPP_WARPS ? P.warps : BPP_WARPS;
+    // Stage G and M in shared memory when they leave room for >= 2 warps.
     const int staged = MODE != 2 &&
                        mats_bytes(k, MODE) + 2 * per_warp_bytes(pmax, LS) <= SMEM_LIMIT;
     const size_t mats = staged ? mats_bytes(k, MODE) : 0;
@@ -847,11 +716,13 @@ nmf_status launch_solve(const SolveParams &P, cudaStream_t s)
     if (per_sm < 1)
         return NMF_ERR_INVALID_ARG;
     int64_t blocks = (int64_t)per_sm * sm_count();
-    const int64_t need = cdiv(cdiv(P.nrhs, (int64_t)P.chunk), nwarps);
+    // The second pass's size is known only on the device: launch it at full
+    // width; it returns at once when nothing was deferred.
+    const int64_t need = list_pass ? blocks : cdiv(cdiv(P.nrhs, (int64_t)P.chunk), nwarps);
     if (need < blocks)
         blocks = need < 1 ? 1 : need;
     bpp_solve_kernel<KW, PT, MODE><<<(unsigned)blocks, nwarps * 32, smem, s>>>(P, pmax, LS,
-                                                                              staged);
+                                                                              staged, list_pass);
     NMF_LAUNCHED("bpp_solve_kernel");
     return NMF_OK;
 }
@@ -859,9 +730,10 @@ nmf_status launch_solve(const SolveParams &P, cudaStream_t s)
 template <int KW>
 nmf_status launch_modes(const SolveParams &P, cudaStream_t s)
 {
-    NMF_TRY((launch_solve<KW, (KW + 1) / 2, 0>(P, s)));
-    NMF_TRY((launch_solve<KW, (KW + 1) / 2, 1>(P, s)));
-    return launch_solve<KW, KW, 2>(P, s);
+    NMF_TRY(launch_solve32(P, s));
+    NMF_TRY((launch_solve<KW, (KW + 1) / 2, 1>(P, 0, s)));
+    NMF_TRY((launch_solve<KW, KW, 2>(P, 0, s)));
+    return launch_solve<KW, (KW + 1) / 2, 1>(P, 1, s);
 }
 
 }  // namespace
@@ -908,7 +780,8 @@ SolveParams solve_params(int k, int64_t nrhs, const double *G, const float *B, f
     P.pout = passive_out;
     P.rounds_out = rounds_out;
     P.status_out = status_out;
-    P.counter = reinterpret_cast<unsigned long long *>(w + L.counter);
+    P.counters = reinterpret_cast<unsigned long long *>(w + L.counters);
+    P.defer = reinterpret_cast<int64_t *>(w + L.defer);
     P.stats = stats_dev;
     const BppShape sh = shape_for(k);
     P.warps = sh.warps;
@@ -943,7 +816,7 @@ nmf_status launch_bpp_prep(int k, const double *G, void *work, BppStats *stats_d
     bpp_prep_kernel<<<1, PREP_THREADS, prep_smem, s>>>(
         G, k, const_cast<float *>(P.G32), const_cast<float *>(P.M32),
         const_cast<double *>(P.M64), const_cast<uint32_t *>(P.usable_words),
-        const_cast<int *>(P.flags), P.counter, stats_dev);
+        const_cast<int *>(P.flags), P.counters, stats_dev);
     NMF_LAUNCHED("bpp_prep_kernel");
     return NMF_OK;
 }
@@ -968,7 +841,7 @@ nmf_status bpp_tune(int k, int64_t nrhs, const double *G, const float *B, float 
                     const uint64_t *passive_in, int max_rounds, void *work, BppStats *stats_dev,
                     cudaStream_t s, int *warps_out, int *chunk_out)
 {
-    static const BppShape cand[] = {{8, 1}, {8, 4}, {8, 8}, {8, 32}, {4, 4}, {4, 16}};
+    static const BppShape cand[] = {{16, 4}, {16, 8}, {8, 1}, {8, 4}, {8, 8}, {8, 32}, {4, 16}};
     NMF_TRY(launch_bpp_prep(k, G, work, stats_dev, s));
     SolveParams P = solve_params(k, nrhs, G, B, X, passive_in, nullptr, nullptr, nullptr,
                                  max_rounds, work, stats_dev);

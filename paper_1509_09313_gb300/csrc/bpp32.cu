@@ -1,0 +1,646 @@
+// FP32 solves of batched BPP (Eq. 3, Eq. 4, Sec. 4.2) for Grams whose
+// diagonally scaled cond_1 the preparation found at most 1e4 (mode 0).
+//
+// Same method as the FP64 kernel in bpp.cu: one warp per right-hand side,
+// lane l holding indices l, l + 32, ... (KW slots); each exchange round solves
+// the smaller of the direct system G_FF x_F = g_F and the complement system
+// M_AA y_A = -u_A (u = M g, x_F = u_F + M_FA y_A), refines once through the
+// same factor, recomputes y = G x - g, and tests the signs with the FP32
+// tolerances in the diagonally scaled variables. Organised for fewer
+// instructions per solve:
+//  * G and M sit in shared memory lane-interleaved: entry (r, c) at
+//    r * 32 KW + (c % 32) * KW + c / 32, so a lane reads its KW entries of a
+//    row with one vector load and updates them with packed FP32x2 FMAs;
+//  * a product with a vector supported on a short index list (F in the direct
+//    form, the active set in the complement form) loops over that list only:
+//    y = G_{:,F} x_F costs |F| row reads, not k;
+//  * u = M g is formed only when a complement solve first needs it;
+//  * the Cholesky keeps each row's reciprocal pivot in its lane: with
+//    q = rsqrt(d), L_jj = d q and L_ij = s_i q;
+//  * no FP64 arithmetic: a system that meets the pivot floor defers its
+//    right-hand side to the FP64 kernel's second pass, which re-solves it from
+//    its starting partition.
+#include <math.h>
+
+#include "bpp_internal.cuh"
+
+namespace nmf {
+namespace bpp {
+namespace {
+
+constexpr int S32_MAX_WARPS = 16;
+constexpr int DEFERRED = -1;   // internal status: re-solve this right-hand side in FP64
+constexpr size_t SMEM_LIMIT32 = 227 * 1024;
+
+// acc[s] += p[s] * a for the KW entries of one row that a lane owns.
+template <int KW>
+__device__ __forceinline__ void row_fma(const float *__restrict__ p, float a, float (&acc)[KW])
+{
+    if constexpr (KW == 1) {
+        acc[0] = fmaf(p[0], a, acc[0]);
+    } else if constexpr (KW == 2) {
+        const float2 q = *reinterpret_cast<const float2 *>(p);
+        const float2 r = __ffma2_rn(q, make_float2(a, a), make_float2(acc[0], acc[1]));
+        acc[0] = r.x;
+        acc[1] = r.y;
+    } else {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        const float2 r0 =
+            __ffma2_rn(make_float2(q.x, q.y), make_float2(a, a), make_float2(acc[0], acc[1]));
+        const float2 r1 =
+            __ffma2_rn(make_float2(q.z, q.w), make_float2(a, a), make_float2(acc[2], acc[3]));
+        acc[0] = r0.x;
+        acc[1] = r0.y;
+        acc[2] = r1.x;
+        acc[3] = r1.y;
+    }
+}
+
+// out += Mat^T vec over all rows (vec staged in shared memory, k4 entries,
+// zero past k). Two accumulator sets halve the FMA dependency chain.
+template <int KW>
+__device__ __forceinline__ void mv_full(const float *__restrict__ Mat, int k4,
+                                        const float *__restrict__ vec, float (&out)[KW], int lane)
+{
+    constexpr int RS = 32 * KW;
+    float a1[KW];
+#pragma unroll
+    for (int s = 0; s < KW; ++s)
+        a1[s] = 0.0f;
+    const float *base = Mat + lane * KW;
+    for (int j = 0; j < k4; j += 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(vec + j);
+        row_fma<KW>(base + (j + 0) * RS, q.x, out);
+        row_fma<KW>(base + (j + 1) * RS, q.y, a1);
+        row_fma<KW>(base + (j + 2) * RS, q.z, out);
+        row_fma<KW>(base + (j + 3) * RS, q.w, a1);
+    }
+#pragma unroll
+    for (int s = 0; s < KW; ++s)
+        out[s] += a1[s];
+}
+
+// out += sum_a Mat[idx[a]] * val[a] over a list padded to n4 entries (the
+// padding has idx 0 and val 0).
+template <int KW>
+__device__ __forceinline__ void mv_list(const float *__restrict__ Mat, const int *__restrict__ idx,
+                                        const float *__restrict__ val, int n4, float (&out)[KW],
+                                        int lane)
+{
+    constexpr int RS = 32 * KW;
+    float a1[KW];
+#pragma unroll
+    for (int s = 0; s < KW; ++s)
+        a1[s] = 0.0f;
+    const float *base = Mat + lane * KW;
+    for (int a = 0; a < n4; a += 4) {
+        const int4 c = *reinterpret_cast<const int4 *>(idx + a);
+        const float4 v = *reinterpret_cast<const float4 *>(val + a);
+        row_fma<KW>(base + c.x * RS, v.x, out);
+        row_fma<KW>(base + c.y * RS, v.y, a1);
+        row_fma<KW>(base + c.z * RS, v.z, out);
+        row_fma<KW>(base + c.w * RS, v.w, a1);
+    }
+#pragma unroll
+    for (int s = 0; s < KW; ++s)
+        out[s] += a1[s];
+}
+
+template <int KW>
+__device__ __forceinline__ void stage_vec(float *__restrict__ stage, const float (&v)[KW], int lane)
+{
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < KW; ++s)
+        stage[32 * s + lane] = v[s];
+    __syncwarp();
+}
+
+// Cholesky of the p x p system S_ab = Src(idx[a], idx[b]) (lane-per-row,
+// left-looking, rows a = lane + 32 t). L goes to Lw (row stride LS, even, so
+// that rows are read as float2); inv[t] receives 1 / L_aa for the lane's rows.
+// Returns false (uniformly) when a pivot is at most PIVOT_TOL of its diagonal.
+template <int KW, int PT>
+__device__ __forceinline__ bool chol32(const float *__restrict__ Src, const int *__restrict__ idx,
+                                       int p, float *__restrict__ Lw, int LS, float (&inv)[PT],
+                                       int lane)
+{
+    constexpr int RS = 32 * KW;
+    int roff[PT], coff[PT];
+    float dg[PT];
+#pragma unroll
+    for (int t = 0; t < PT; ++t) {
+        const int a = lane + 32 * t;
+        roff[t] = 0;
+        coff[t] = 0;
+        dg[t] = 1.0f;
+        inv[t] = 0.0f;
+        if (a < p) {
+            const int c = idx[a];
+            roff[t] = c * RS;
+            coff[t] = (c & 31) * KW + (c >> 5);
+            dg[t] = Src[roff[t] + coff[t]];
+        }
+    }
+    for (int j = 0; j < p; ++j) {
+        const int tj = j >> 5, owner = j & 31;
+        int cj = coff[0];
+#pragma unroll
+        for (int t = 1; t < PT; ++t)
+            if (tj == t)
+                cj = coff[t];
+        cj = __shfl_sync(FULL, cj, owner);
+        const float *lj = Lw + j * LS;
+        float sv[PT];
+#pragma unroll
+        for (int t = 0; t < PT; ++t) {
+            const int a = lane + 32 * t;
+            sv[t] = 0.0f;
+            if (a >= j && a < p) {
+                const float *la = Lw + a * LS;
+                float2 acc = make_float2(0.0f, 0.0f);
+                int c = 0;
+                for (; c + 2 <= j; c += 2)
+                    acc = __ffma2_rn(*reinterpret_cast<const float2 *>(la + c),
+                                     *reinterpret_cast<const float2 *>(lj + c), acc);
+                float s = Src[roff[t] + cj] - (acc.x + acc.y);
+                if (c < j)
+                    s = fmaf(-la[c], lj[c], s);
+                sv[t] = s;
+            }
+        }
+        float q = 0.0f;
+#pragma unroll
+        for (int t = 0; t < PT; ++t)
+            if (t == tj && lane == owner)
+                q = sv[t] > PIVOT_TOL * dg[t] ? rsqrtf(sv[t]) : 0.0f;
+        q = __shfl_sync(FULL, q, owner);
+        if (!(q > 0.0f))
+            return false;
+#pragma unroll
+        for (int t = 0; t < PT; ++t) {
+            const int a = lane + 32 * t;
+            if (a >= j && a < p)
+                Lw[a * LS + j] = sv[t] * q;
+            if (t == tj && lane == owner)
+                inv[t] = q;
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+// Solve L L^T z = r in place (row a of r in lane a % 32, slot a / 32).
+template <int PT>
+__device__ __forceinline__ void subst32(int p, const float *__restrict__ Lw, int LS,
+                                        const float (&inv)[PT], float (&r)[PT], int lane)
+{
+    for (int j = 0; j < p; ++j) {
+        const int tj = j >> 5, owner = j & 31;
+        float v = r[0] * inv[0];
+#pragma unroll
+        for (int t = 1; t < PT; ++t)
+            if (tj == t)
+                v = r[t] * inv[t];
+        const float z = __shfl_sync(FULL, v, owner);
+#pragma unroll
+        for (int t = 0; t < PT; ++t) {
+            const int a = lane + 32 * t;
+            if (a > j && a < p)
+                r[t] = fmaf(-Lw[a * LS + j], z, r[t]);
+            if (t == tj && lane == owner)
+                r[t] = z;
+        }
+    }
+    for (int j = p - 1; j >= 0; --j) {
+        const int tj = j >> 5, owner = j & 31;
+        float v = r[0] * inv[0];
+#pragma unroll
+        for (int t = 1; t < PT; ++t)
+            if (tj == t)
+                v = r[t] * inv[t];
+        const float xj = __shfl_sync(FULL, v, owner);
+        const float *lj = Lw + j * LS;
+#pragma unroll
+        for (int t = 0; t < PT; ++t) {
+            const int a = lane + 32 * t;
+            if (a < j)
+                r[t] = fmaf(-lj[a], xj, r[t]);
+            if (t == tj && lane == owner)
+                r[t] = xj;
+        }
+    }
+}
+
+// Shared memory: G and M (k rounded up to 4 rows of 32 KW floats each), then
+// per warp an index list, its values, a staging vector (32 KW each) and the
+// pmax x LS factor.
+__host__ __device__ inline size_t mats_bytes32(int k, int KW)
+{
+    return 2 * sizeof(float) * (size_t)((k + 3) & ~3) * 32 * KW;
+}
+__host__ __device__ inline size_t warp_bytes32(int KW, int pmax, int LS)
+{
+    return (3 * sizeof(float) * 32 * KW + sizeof(float) * (size_t)pmax * LS + 15) & ~size_t(15);
+}
+
+// 64 registers for KW <= 2 (two 16-warp CTAs per SM); the KW = 4 form needs
+// more and runs one CTA per SM.
+template <int KW>
+__global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
+    bpp_solve32_kernel(const SolveParams P, int pmax, int LS)
+{
+    constexpr int RS = 32 * KW;
+    constexpr int PT = (KW + 1) / 2;
+    if (P.flags[0] != 0)
+        return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int k = P.k, k4 = (k + 3) & ~3;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *Gs = reinterpret_cast<float *>(smem_raw);
+    float *Ms = Gs + k4 * RS;
+    for (int e = threadIdx.x; e < k4 * RS; e += blockDim.x) {
+        const int r = e / RS, q = e - r * RS;
+        const int c = q / KW + 32 * (q % KW);
+        const bool in = r < k && c < k;
+        Gs[e] = in ? P.G32[r * k + c] : 0.0f;
+        Ms[e] = in ? P.M32[r * k + c] : 0.0f;
+    }
+    unsigned char *wp = smem_raw + mats_bytes32(k, KW) + warp * warp_bytes32(KW, pmax, LS);
+    int *widx = reinterpret_cast<int *>(wp);
+    float *zbuf = reinterpret_cast<float *>(widx + RS);
+    float *stage = zbuf + RS;
+    float *Lw = stage + RS;
+    __syncthreads();
+
+    bool usable[KW];
+    float dsq[KW];   // sqrt(G_ii) (1 where unusable): the scale of the sign tolerances
+    int nU = 0;
+#pragma unroll
+    for (int s = 0; s < KW; ++s) {
+        const uint32_t w = P.usable_words[s];
+        usable[s] = (w >> lane) & 1u;
+        nU += __popc(w);
+        const int i = lane + 32 * s;
+        dsq[s] = usable[s] ? sqrtf(Gs[i * RS + lane * KW + s]) : 1.0f;
+    }
+
+    unsigned long long st_rounds = 0, st_max = 0, st_def = 0, st_nc = 0, st_nf = 0, st_rhs = 0;
+
+    for (;;) {
+        unsigned long long j0 = 0;
+        if (lane == 0)
+            j0 = atomicAdd(&P.counters[CNT_WORK], (unsigned long long)P.chunk);
+        j0 = __shfl_sync(FULL, j0, 0);
+        if (j0 >= (unsigned long long)P.nrhs)
+            break;
+        const int64_t jend = min((int64_t)j0 + P.chunk, P.nrhs);
+        for (int64_t j = (int64_t)j0; j < jend; ++j) {
+            float g[KW], u[KW], x[KW], y[KW];
+            bool inF[KW];
+            bool bad = false, have_u = false;
+            float gmax = 0.0f;
+#pragma unroll
+            for (int s = 0; s < KW; ++s) {
+                const int i = lane + 32 * s;
+                g[s] = i < k ? P.B[j * k + i] : 0.0f;
+                bad |= !isfinite(g[s]);
+                gmax = fmaxf(gmax, fabsf(g[s]) / dsq[s]);
+                u[s] = 0.0f;
+                x[s] = 0.0f;
+                y[s] = -g[s];
+                inF[s] = false;
+            }
+            bad = __any_sync(FULL, bad);
+            gmax = warp_max(gmax);
+            const float ytol = FEAS_TOL32 * gmax;
+            float xtol = 0.0f;
+            int status = NMF_OK;
+            int rounds = 0;
+            if (bad) {
+                status = NMF_ERR_NONFINITE;
+#pragma unroll
+                for (int s = 0; s < KW; ++s)
+                    x[s] = 0.0f;
+            } else {
+                if (P.pin) {
+#pragma unroll
+                    for (int s = 0; s < KW; ++s) {
+                        const int i = lane + 32 * s;
+                        bool f = false;
+                        if (i < k) {
+                            const uint64_t wv = P.pin[j * P.nwords + (i >> 6)];
+                            f = (wv >> (i & 63)) & 1ull;
+                        }
+                        inF[s] = f && usable[s];
+                    }
+                }
+
+                // Candidate point of the current partition: fills x and y.
+                auto solve = [&]() -> int {
+                    int nF = 0;
+#pragma unroll
+                    for (int s = 0; s < KW; ++s)
+                        nF += __popc(__ballot_sync(FULL, inF[s]));
+                    const bool comp = nU - nF < nF;
+                    if (comp && !have_u) {
+                        stage_vec<KW>(stage, g, lane);
+                        mv_full<KW>(Ms, k4, stage, u, lane);
+                        have_u = true;
+                    }
+                    bool inS[KW];
+                    int rank[KW];
+                    int pos = 0;
+                    __syncwarp();
+#pragma unroll
+                    for (int s = 0; s < KW; ++s) {
+                        inS[s] = comp ? (usable[s] && !inF[s]) : inF[s];
+                        const unsigned mk = __ballot_sync(FULL, inS[s]);
+                        rank[s] = pos + __popc(mk & lanemask_lt(lane));
+                        if (inS[s]) {
+                            widx[rank[s]] = lane + 32 * s;
+                            zbuf[rank[s]] = comp ? -u[s] : g[s];
+                        }
+                        pos += __popc(mk);
+                    }
+                    const int p = pos, p4 = (p + 3) & ~3;
+                    if (lane < p4 - p) {
+                        widx[p + lane] = 0;
+                        zbuf[p + lane] = 0.0f;
+                    }
+                    __syncwarp();
+                    float inv[PT], r[PT];
+                    if (p > 0) {
+                        if (!chol32<KW, PT>(comp ? Ms : Gs, widx, p, Lw, LS, inv, lane))
+                            return DEFERRED;
+#pragma unroll
+                        for (int t = 0; t < PT; ++t) {
+                            const int a = lane + 32 * t;
+                            r[t] = a < p ? zbuf[a] : 0.0f;
+                        }
+                        subst32<PT>(p, Lw, LS, inv, r, lane);
+                        __syncwarp();
+#pragma unroll
+                        for (int t = 0; t < PT; ++t)
+                            if (lane + 32 * t < p)
+                                zbuf[lane + 32 * t] = r[t];
+                        __syncwarp();
+                    }
+                    if (!comp) {
+#pragma unroll
+                        for (int s = 0; s < KW; ++s)
+                            x[s] = inF[s] ? zbuf[rank[s]] : 0.0f;
+                    } else {
+                        float acc[KW];
+#pragma unroll
+                        for (int s = 0; s < KW; ++s)
+                            acc[s] = u[s];
+                        mv_list<KW>(Ms, widx, zbuf, p4, acc, lane);
+#pragma unroll
+                        for (int s = 0; s < KW; ++s)
+                            x[s] = inF[s] ? acc[s] : 0.0f;
+                    }
+                    // One refinement step through the same factor: the explicit
+                    // inverse alone is not backward stable in FP32.
+                    if (nF > 0) {
+                        float w[KW], res[KW], up[KW];
+#pragma unroll
+                        for (int s = 0; s < KW; ++s) {
+                            w[s] = 0.0f;
+                            up[s] = 0.0f;
+                        }
+                        if (!comp) {
+                            mv_list<KW>(Gs, widx, zbuf, p4, w, lane);   // zbuf = x_F
+                        } else {
+                            stage_vec<KW>(stage, x, lane);
+                            mv_full<KW>(Gs, k4, stage, w, lane);
+                        }
+#pragma unroll
+                        for (int s = 0; s < KW; ++s)
+                            res[s] = inF[s] ? g[s] - w[s] : 0.0f;
+                        if (comp) {
+                            stage_vec<KW>(stage, res, lane);
+                            mv_full<KW>(Ms, k4, stage, up, lane);
+                        }
+                        __syncwarp();
+#pragma unroll
+                        for (int s = 0; s < KW; ++s)
+                            if (inS[s])
+                                zbuf[rank[s]] = comp ? -up[s] : res[s];
+                        __syncwarp();
+                        if (p > 0) {
+#pragma unroll
+                            for (int t = 0; t < PT; ++t) {
+                                const int a = lane + 32 * t;
+                                r[t] = a < p ? zbuf[a] : 0.0f;
+                            }
+                            subst32<PT>(p, Lw, LS, inv, r, lane);
+                            __syncwarp();
+#pragma unroll
+                            for (int t = 0; t < PT; ++t)
+                                if (lane + 32 * t < p)
+                                    zbuf[lane + 32 * t] = r[t];
+                            __syncwarp();
+                        }
+                        if (!comp) {
+#pragma unroll
+                            for (int s = 0; s < KW; ++s)
+                                if (inF[s])
+                                    x[s] += zbuf[rank[s]];
+                        } else {
+                            mv_list<KW>(Ms, widx, zbuf, p4, up, lane);
+#pragma unroll
+                            for (int s = 0; s < KW; ++s)
+                                if (inF[s])
+                                    x[s] += up[s];
+                        }
+                    }
+                    // y = G x - g off F (0 on F), from the refined x.
+                    float w[KW];
+#pragma unroll
+                    for (int s = 0; s < KW; ++s)
+                        w[s] = 0.0f;
+                    if (!comp) {
+                        __syncwarp();
+#pragma unroll
+                        for (int s = 0; s < KW; ++s)
+                            if (inS[s])
+                                zbuf[rank[s]] = x[s];
+                        __syncwarp();
+                        mv_list<KW>(Gs, widx, zbuf, p4, w, lane);
+                    } else {
+                        stage_vec<KW>(stage, x, lane);
+                        mv_full<KW>(Gs, k4, stage, w, lane);
+                    }
+                    float xm = 0.0f;
+#pragma unroll
+                    for (int s = 0; s < KW; ++s) {
+                        y[s] = inF[s] ? 0.0f : w[s] - g[s];
+                        xm = fmaxf(xm, inF[s] ? fabsf(x[s]) * dsq[s] : 0.0f);
+                    }
+                    xtol = FEAS_TOL32 * warp_max(xm);   // scaled: compares x_i * d_i
+                    return NMF_OK;
+                };
+
+                bool anyF = false;
+#pragma unroll
+                for (int s = 0; s < KW; ++s)
+                    anyF |= inF[s];
+                if (__any_sync(FULL, anyF))
+                    status = solve();
+                int alpha = 3, beta = k + 1;
+                while (status == NMF_OK) {
+                    bool inf[KW];
+                    unsigned vm[KW];
+                    int nV = 0;
+#pragma unroll
+                    for (int s = 0; s < KW; ++s) {
+                        inf[s] = usable[s] && (inF[s] ? (x[s] * dsq[s] < -xtol)
+                                                      : (y[s] < -ytol * dsq[s]));
+                        vm[s] = __ballot_sync(FULL, inf[s]);
+                        nV += __popc(vm[s]);
+                    }
+                    if (nV == 0)
+                        break;
+                    if (rounds >= P.max_rounds) {
+                        status = NMF_ERR_NOT_CONVERGED;
+                        break;
+                    }
+                    if (nV < beta) {   // full exchange; the count dropped
+                        beta = nV;
+                        alpha = 3;
+#pragma unroll
+                        for (int s = 0; s < KW; ++s)
+                            inF[s] = inF[s] != inf[s];
+                    } else if (alpha >= 1) {   // full exchange, one of three more
+                        alpha -= 1;
+#pragma unroll
+                        for (int s = 0; s < KW; ++s)
+                            inF[s] = inF[s] != inf[s];
+                    } else {   // backup rule: the largest infeasible index alone
+                        int top = -1;
+#pragma unroll
+                        for (int s = KW - 1; s >= 0; --s)
+                            if (top < 0 && vm[s])
+                                top = 32 * s + 31 - __clz(vm[s]);
+#pragma unroll
+                        for (int s = 0; s < KW; ++s)
+                            if (lane + 32 * s == top)
+                                inF[s] = !inF[s];
+                    }
+                    rounds += 1;
+                    status = solve();
+                }
+                if (status != DEFERRED) {
+                    bool nf = false;
+#pragma unroll
+                    for (int s = 0; s < KW; ++s) {
+                        x[s] = x[s] > 0.0f ? x[s] : 0.0f;   // within-tolerance negatives -> 0
+                        nf |= !isfinite(x[s]);
+                    }
+                    if (__any_sync(FULL, nf) && status == NMF_OK)
+                        status = NMF_ERR_NONFINITE;
+                }
+            }
+            if (status == DEFERRED) {
+                if (lane == 0) {
+                    const unsigned long long slot = atomicAdd(&P.counters[CNT_DEFERRED], 1ull);
+                    if (slot < (unsigned long long)DEFER_CAP)
+                        P.defer[slot] = j;
+                    st_def += 1;
+                }
+                continue;
+            }
+#pragma unroll
+            for (int s = 0; s < KW; ++s) {
+                const int i = lane + 32 * s;
+                if (i < k)
+                    P.X[j * k + i] = x[s];
+            }
+            if (P.pout) {
+                unsigned bm[KW];
+#pragma unroll
+                for (int s = 0; s < KW; ++s)
+                    bm[s] = __ballot_sync(FULL, inF[s]);
+                if (lane == 0) {
+#pragma unroll
+                    for (int w = 0; w < (KW + 1) / 2; ++w) {
+                        const uint64_t lo = bm[2 * w];
+                        const uint64_t hi = (2 * w + 1 < KW) ? bm[2 * w + 1] : 0u;
+                        P.pout[j * P.nwords + w] = lo | (hi << 32);
+                    }
+                }
+            }
+            if (lane == 0) {
+                if (P.rounds_out)
+                    P.rounds_out[j] = rounds;
+                if (P.status_out)
+                    P.status_out[j] = (int8_t)status;
+                st_rhs += 1;
+                st_rounds += rounds;
+                st_max = st_max > (unsigned long long)rounds ? st_max : (unsigned long long)rounds;
+                st_nc += status == NMF_ERR_NOT_CONVERGED;
+                st_nf += status == NMF_ERR_NONFINITE;
+            }
+        }
+    }
+    if (lane == 0 && (st_rhs || st_def)) {
+        atomicAdd(&P.stats->rhs, st_rhs);
+        atomicAdd(&P.stats->rounds, st_rounds);
+        atomicMax(&P.stats->max_rounds, st_max);
+        if (st_def) atomicAdd(&P.stats->fp64_solves, st_def);
+        if (st_nc) atomicAdd(&P.stats->not_converged, st_nc);
+        if (st_nf) atomicAdd(&P.stats->nonfinite, st_nf);
+    }
+}
+
+template <int KW>
+nmf_status launch32(const SolveParams &P, cudaStream_t s)
+{
+    const int k = P.k;
+    const int pmax = k / 2 > 1 ? k / 2 : 1;   // min(|F|, |A|) <= k / 2
+    int q = (pmax + 1) / 2;
+    if (!(q & 1))
+        ++q;
+    const int LS = 2 * q;   // 2 * odd: conflict-free float2 row reads and column accesses
+    int nwarps = P.warps < S32_MAX_WARPS ? P.warps : S32_MAX_WARPS;
+    const size_t mats = mats_bytes32(k, KW);
+    auto bytes = [&](int nw) { return mats + (size_t)nw * warp_bytes32(KW, pmax, LS); };
+    while (nwarps > 1 && bytes(nwarps) > SMEM_LIMIT32)
+        --nwarps;
+    const size_t smem = bytes(nwarps);
+    if (smem > SMEM_LIMIT32)
+        return NMF_ERR_INVALID_ARG;
+    static int configured_bytes = 0;
+    if ((int)smem > configured_bytes) {
+        NMF_CUDA(cudaFuncSetAttribute(bpp_solve32_kernel<KW>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured_bytes = (int)smem;
+    }
+    int per_sm = 0;
+    NMF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bpp_solve32_kernel<KW>,
+                                                           nwarps * 32, smem));
+    if (per_sm < 1)
+        return NMF_ERR_INVALID_ARG;
+    int64_t blocks = (int64_t)per_sm * sm_count();
+    const int64_t need = cdiv(cdiv(P.nrhs, (int64_t)P.chunk), nwarps);
+    if (need < blocks)
+        blocks = need < 1 ? 1 : need;
+    bpp_solve32_kernel<KW><<<(unsigned)blocks, nwarps * 32, smem, s>>>(P, pmax, LS);
+    NMF_LAUNCHED("bpp_solve32_kernel");
+    return NMF_OK;
+}
+
+}  // namespace
+
+nmf_status launch_solve32(const SolveParams &P, cudaStream_t s)
+{
+    if (P.k <= 32)
+        return launch32<1>(P, s);
+    if (P.k <= 64)
+        return launch32<2>(P, s);
+    return launch32<4>(P, s);
+}
+
+}  // namespace bpp
+}  // namespace nmf
