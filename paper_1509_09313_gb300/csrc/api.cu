@@ -234,6 +234,7 @@ struct nmf_handle {
     BppStats *stats_dev = nullptr;
     double *gram_part = nullptr;
     double *obj_part = nullptr;
+    double *a_sq = nullptr;                     // ||A||^2 (sparse input)
     double *f_hist = nullptr;                   // ring of objective values
     double *f_now = nullptr;
     void *tc_work = nullptr;
@@ -341,17 +342,23 @@ nmf_status mm(nmf_handle *h, int trans, const float *F, float *out)
     return launch_mm_simt(h->A.dense, c.m, c.n, h->A.lda, F, c.k, trans, out, h->stream);
 }
 
-nmf_status objective_into(nmf_handle *h, double *f_dev)
+// f(W, H) into *f_dev. Sparse input: after an H half-step (after_h) Y holds
+// A^T W and GW = W^T W for the current W; otherwise both are formed here (Y
+// and GW are scratch between iterations).
+nmf_status objective_into(nmf_handle *h, double *f_dev, bool after_h = false)
 {
     const nmf_config &c = h->cfg;
     if (h->fused_obj)
         return launch_mm_tc_obj(h->A.dense, c.m, c.n, h->A.lda, h->Ht, c.k, 0, h->V, h->W,
                                 f_dev, h->tc_work, h->tc_work_bytes, h->stream);
     if (c.input_kind == NMF_INPUT_CSR) {
+        if (!after_h) {
+            NMF_TRY(mm(h, 1, h->W, h->Y));
+            NMF_TRY(launch_gram(h->W, c.m, c.k, h->GW, h->gram_part, h->stream));
+        }
         NMF_TRY(launch_gram(h->Ht, c.n, c.k, h->GH, h->gram_part, h->stream));
-        NMF_TRY(launch_gram(h->W, c.m, c.k, h->GW, h->gram_part, h->stream));
-        return launch_objective_csr(h->A.rowptr, h->A.colidx, h->A.vals, c.m, h->W, h->Ht, c.k,
-                                    h->GW, h->GH, h->obj_part, f_dev, h->stream);
+        return launch_objective_csr(h->Ht, h->Y, c.n, c.k, h->a_sq, h->GW, h->GH, h->obj_part,
+                                    f_dev, h->stream);
     }
     return launch_objective_dense(h->A.dense, c.m, c.n, h->A.lda, h->W, h->Ht, c.k, c.precision,
                                   h->obj_part, f_dev, h->stream);
@@ -437,7 +444,7 @@ nmf_status one_iteration(nmf_handle *h)
             h->obj_pending = true;   // computed by the next A H^T pass or a flush
         } else {
             PhaseTimer t(h, 3);
-            NMF_TRY(objective_into(h, h->f_hist + (h->f_count % F_HIST_CAP)));
+            NMF_TRY(objective_into(h, h->f_hist + (h->f_count % F_HIST_CAP), true));
         }
         h->f_count += 1;
     }
@@ -473,6 +480,7 @@ void free_handle(nmf_handle *h)
     cudaFree(h->stats_dev);
     cudaFree(h->gram_part);
     cudaFree(h->obj_part);
+    cudaFree(h->a_sq);
     cudaFree(h->f_hist);
     cudaFree(h->f_now);
     cudaFree(h->tc_work);
@@ -569,6 +577,7 @@ extern "C" nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nm
         chk(dalloc(&h->t_rowptr, (size_t)c.n + 1));
         chk(dalloc(&h->t_colidx, (size_t)A->nnz));
         chk(dalloc(&h->t_vals, (size_t)A->nnz));
+        chk(dalloc(&h->a_sq, 1));
     }
     if (e != cudaSuccess) {
         free_handle(h);
@@ -592,6 +601,7 @@ extern "C" nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nm
                                                  h->stream);
             cudaFreeAsync(cursor, h->stream);
             NMF_TRY(s2);
+            NMF_TRY(launch_sq_norm(A->vals, A->nnz, h->obj_part, h->a_sq, h->stream));
         }
         NMF_CUDA(cudaStreamSynchronize(h->stream));
         return NMF_OK;

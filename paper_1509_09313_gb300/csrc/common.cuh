@@ -88,11 +88,14 @@ int64_t objective_partials_len();
 nmf_status launch_objective_dense(const float *A, int64_t m, int64_t n, int64_t lda,
                                   const float *W, const float *Ht, int k, int precision,
                                   double *partials, double *f_dev, cudaStream_t s);
-// Sparse: f = sum over stored (A_ij - wh)^2 - wh^2, plus trace(GW GH).
-nmf_status launch_objective_csr(const int64_t *rowptr, const int32_t *colidx,
-                                const float *vals, int64_t m, const float *W, const float *Ht,
-                                int k, const double *GW, const double *GH, double *partials,
-                                double *f_dev, cudaStream_t s);
+// Sparse: f = ||A||^2 - 2 sum_j h_j . Y_j + trace(GW GH), with Y = A^T W
+// (n x k), GW = W^T W and GH = H H^T current, and *a_sq = ||A||^2.
+nmf_status launch_objective_csr(const float *Ht, const float *Y, int64_t n, int k,
+                                const double *a_sq, const double *GW, const double *GH,
+                                double *partials, double *f_dev, cudaStream_t s);
+// *out = ||v||^2 (FP64), e.g. of the stored values of A.
+nmf_status launch_sq_norm(const float *v, int64_t len, double *partials, double *out,
+                          cudaStream_t s);
 
 // Batched BPP. Workspace layout is private to bpp.cu; size from bpp_work_bytes.
 size_t bpp_work_bytes(int k);

@@ -9,9 +9,13 @@
 // Per-CTA FP64 partials are summed in CTA order by a one-block kernel.
 //
 // Sparse A (CSR): the sum over all m*n positions splits exactly into
-//   f = sum_{stored} [(A_ij - wh_ij)^2 - wh_ij^2] + trace((W^T W)(H H^T)),
-// the first term one warp per row (FP32 dot products, FP64 accumulation), the
-// trace in FP64 from the FP64 Gram matrices.
+//   f = ||A||^2 - 2 sum_{stored} A_ij w_i.h_j + trace((W^T W)(H H^T)),
+// and the cross term regroups by column: sum_j h_j . (A^T W)_j. The caller
+// passes Y = A^T W (n x k; the right-hand sides of the H half-step, so no
+// stored entry is revisited), and the cross term is one dot product of two
+// n x k arrays (FP32 within a float4, FP64 across them). The trace uses the
+// FP64 Grams; ||A||^2 is summed once when the matrix is loaded. A is not low
+// rank, so the fit is loose and the three terms do not cancel badly.
 #include "common.cuh"
 
 namespace nmf {
@@ -108,7 +112,10 @@ __global__ void __launch_bounds__(OBJ_THREADS)
         partials[blockIdx.x] = s;
 }
 
-__global__ void sum_partials_kernel(const double *__restrict__ partials, int nparts,
+// f = base + scale * sum(partials) + trace(GW GH) (GW null: no trace), the
+// three sums formed separately in a fixed order.
+__global__ void sum_partials_kernel(const double *__restrict__ partials, int nparts, double scale,
+                                    const double *__restrict__ base,
                                     const double *__restrict__ GW, const double *__restrict__ GH,
                                     int k, double *__restrict__ f_dev)
 {
@@ -116,57 +123,48 @@ __global__ void sum_partials_kernel(const double *__restrict__ partials, int npa
     double s = 0.0;
     for (int p = threadIdx.x; p < nparts; p += blockDim.x)
         s += partials[p];
+    const double S = block_sum(s, red);
+    double t = 0.0;
     if (GW)
         for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
             const int a = e / k, b = e % k;
-            s += GW[a * k + b] * GH[b * k + a];
+            t += GW[a * k + b] * GH[b * k + a];
         }
-    const double t = block_sum(s, red);
+    const double T = block_sum(t, red);
     if (threadIdx.x == 0)
-        *f_dev = t;
+        *f_dev = (base ? *base : 0.0) + scale * S + T;
 }
 
-template <int KW>
+// Per-block FP64 partial sums of sum_e X_e Y_e (float4 loads when both
+// arrays are 16-byte aligned; products within a float4 summed in FP32).
 __global__ void __launch_bounds__(OBJ_THREADS)
-    objective_csr_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                         const float *__restrict__ vals, int64_t m, const float *__restrict__ W,
-                         const float *__restrict__ Ht, int k, double *__restrict__ partials)
+    dot_partials_kernel(const float *__restrict__ X, const float *__restrict__ Y, int64_t len,
+                        int vec, double *__restrict__ partials)
 {
     __shared__ double red[OBJ_THREADS / 32];
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = ((int64_t)blockIdx.x * OBJ_THREADS + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * OBJ_THREADS) >> 5;
-    double acc64 = 0.0;
-    for (int64_t i = warp0; i < m; i += nw) {
-        float w[KW];
-#pragma unroll
-        for (int s = 0; s < KW; ++s) {
-            const int r = lane + 32 * s;
-            w[s] = r < k ? W[i * k + r] : 0.0f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    int64_t done = 0;
+    if (vec) {
+        const int64_t n4 = len >> 2;
+        const float4 *X4 = reinterpret_cast<const float4 *>(X);
+        const float4 *Y4 = reinterpret_cast<const float4 *>(Y);
+        for (int64_t e = t0; e < n4; e += stride) {
+            const float4 a = X4[e], b = Y4[e];
+            float d = a.x * b.x;
+            d = fmaf(a.y, b.y, d);
+            d = fmaf(a.z, b.z, d);
+            d = fmaf(a.w, b.w, d);
+            acc += (double)d;
         }
-        float rowsum = 0.0f;
-        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-            const int64_t j = colidx[p];
-            float d = 0.0f;
-#pragma unroll
-            for (int s = 0; s < KW; ++s) {
-                const int r = lane + 32 * s;
-                if (r < k)
-                    d = fmaf(w[s], Ht[j * k + r], d);
-            }
-            for (int o = 16; o > 0; o >>= 1)
-                d += __shfl_xor_sync(FULL, d, o);
-            const float e = vals[p] - d;
-            rowsum += e * e - d * d;
-        }
-        acc64 += (double)rowsum;
+        done = n4 << 2;
     }
-    // Every lane holds the same row sums; count them once.
-    if (lane != 0)
-        acc64 = 0.0;
-    const double s = block_sum(acc64, red);
+    for (int64_t e = done + t0; e < len; e += stride)
+        acc += (double)(X[e] * Y[e]);
+    const double t = block_sum(acc, red);
     if (threadIdx.x == 0)
-        partials[blockIdx.x] = s;
+        partials[blockIdx.x] = t;
 }
 
 int obj_parts() { return 2 * sm_count(); }
@@ -183,30 +181,36 @@ nmf_status launch_objective_dense(const float *A, int64_t m, int64_t n, int64_t 
     const int parts = obj_parts();
     objective_dense_kernel<<<parts, OBJ_THREADS, 0, s>>>(A, m, n, lda, W, Ht, k, partials);
     NMF_LAUNCHED("objective_dense_kernel");
-    sum_partials_kernel<<<1, 256, 0, s>>>(partials, parts, nullptr, nullptr, k, f_dev);
+    sum_partials_kernel<<<1, 256, 0, s>>>(partials, parts, 1.0, nullptr, nullptr, nullptr, k,
+                                          f_dev);
     NMF_LAUNCHED("sum_partials_kernel");
     return NMF_OK;
 }
 
-nmf_status launch_objective_csr(const int64_t *rowptr, const int32_t *colidx,
-                                const float *vals, int64_t m, const float *W, const float *Ht,
-                                int k, const double *GW, const double *GH, double *partials,
-                                double *f_dev, cudaStream_t s)
+static nmf_status launch_dot(const float *X, const float *Y, int64_t len, double scale,
+                             const double *base, const double *GW, const double *GH,
+                             int k, double *partials, double *f_dev, cudaStream_t s)
 {
     const int parts = obj_parts();
-    if (k <= 32)
-        objective_csr_kernel<1><<<parts, OBJ_THREADS, 0, s>>>(rowptr, colidx, vals, m, W, Ht, k,
-                                                              partials);
-    else if (k <= 64)
-        objective_csr_kernel<2><<<parts, OBJ_THREADS, 0, s>>>(rowptr, colidx, vals, m, W, Ht, k,
-                                                              partials);
-    else
-        objective_csr_kernel<4><<<parts, OBJ_THREADS, 0, s>>>(rowptr, colidx, vals, m, W, Ht, k,
-                                                              partials);
-    NMF_LAUNCHED("objective_csr_kernel");
-    sum_partials_kernel<<<1, 256, 0, s>>>(partials, parts, GW, GH, k, f_dev);
+    const int vec = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15) == 0;
+    dot_partials_kernel<<<parts, OBJ_THREADS, 0, s>>>(X, Y, len, vec, partials);
+    NMF_LAUNCHED("dot_partials_kernel");
+    sum_partials_kernel<<<1, 256, 0, s>>>(partials, parts, scale, base, GW, GH, k, f_dev);
     NMF_LAUNCHED("sum_partials_kernel");
     return NMF_OK;
+}
+
+nmf_status launch_objective_csr(const float *Ht, const float *Y, int64_t n, int k,
+                                const double *a_sq, const double *GW, const double *GH,
+                                double *partials, double *f_dev, cudaStream_t s)
+{
+    return launch_dot(Ht, Y, n * k, -2.0, a_sq, GW, GH, k, partials, f_dev, s);
+}
+
+nmf_status launch_sq_norm(const float *v, int64_t len, double *partials, double *out,
+                          cudaStream_t s)
+{
+    return launch_dot(v, v, len, 1.0, nullptr, nullptr, nullptr, 0, partials, out, s);
 }
 
 }  // namespace nmf

@@ -103,6 +103,27 @@ def test_sparse_config_scaled(nmf):
     check(nmf, g, ref)
 
 
+def test_sparse_objective_standalone(nmf):
+    # nmf_objective outside an iteration (A^T W and W^T W formed on the spot) at
+    # the starting point and after two iterations; the in-iteration form (from
+    # the H half-step's right-hand sides) must give the same value.
+    m, n, k = 3000, 2000, 20
+    csr = synth.csr_uniform(m, n, 60000, seed=7)
+    W0, Ht0 = synth.init_factors(m, n, k, seed=7)
+    h = nmf.nmf_init(tuple(dev(x) for x in csr), dev(W0), dev(Ht0), shape=(m, n))
+    f0 = h.nmf_objective()
+    ref0 = oracle.objective_csr(*csr, m, n, W0, Ht0)
+    assert abs(f0 - ref0) / ref0 <= 1e-6
+    h.nmf_iterate(2)
+    f2 = h.nmf_objective()
+    W, Ht = h.nmf_get_factors()
+    ref2 = oracle.objective_csr(*csr, m, n, W.double().cpu().numpy(), Ht.double().cpu().numpy())
+    assert abs(f2 - ref2) / ref2 <= 1e-6
+    hist = h.nmf_objective_history()
+    assert abs(hist[-1] - f2) / f2 <= 1e-6
+    h.nmf_destroy()
+
+
 def test_checkpoint_resume(nmf):
     m, n, k = 600, 400, 8
     A = synth.dense_planted(m, n, k, 0.01, seed=5)
