@@ -37,9 +37,11 @@ WORKLOADS = {
                     "dense A=W0*H0+|N(0,0.01^2)| 2000x1000 k=10 fp32"),
     "sparse-large": (2000000, 1000000, 50, None,
                      "sparse CSR 2000000x1000000, 20M uniform draws, values U(0,1], k=50"),
+    "sparse-medium": (200000, 100000, 50, None,
+                      "sparse CSR 200000x100000, 2M uniform draws, values U(0,1], k=50"),
 }
 # Sparse workloads: number of uniform position draws (duplicates merged).
-SPARSE_DRAWS = {"sparse-large": 20000000}
+SPARSE_DRAWS = {"sparse-large": 20000000, "sparse-medium": 2000000}
 SEED = 1509
 METRIC = "ANLS-BPP iterations/s"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")

@@ -538,7 +538,13 @@ extern "C" nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nm
     h->A = *A;
     h->stream = as_stream(stream);
     h->nwords = (c.k + 63) / 64;
-    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+    // The side stream (Gram + BPP preparation, overlapping the product) gets
+    // the highest priority, so its blocks are scheduled as soon as an SM frees
+    // up instead of after every queued block of the product.
+    int prio_least = 0, prio_greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_greatest) !=
+            cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         free_handle(h);

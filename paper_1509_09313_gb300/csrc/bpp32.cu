@@ -337,6 +337,10 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
                 }
 
                 // Candidate point of the current partition: fills x and y.
+                // The solve and its refinement are two passes of one loop
+                // (substitution, the step dx, then w = G x), so each piece of
+                // code appears once: the kernel is bound by instruction
+                // issue and fetch, not by arithmetic.
                 auto solve = [&]() -> int {
                     int nF = 0;
 #pragma unroll
@@ -369,66 +373,20 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
                         zbuf[p + lane] = 0.0f;
                     }
                     __syncwarp();
-                    float inv[PT], r[PT];
-                    if (p > 0) {
-                        if (!chol32<KW, PT>(comp ? Ms : Gs, widx, p, Lw, LS, inv, lane))
-                            return DEFERRED;
+                    float inv[PT];
+                    if (p > 0 && !chol32<KW, PT>(comp ? Ms : Gs, widx, p, Lw, LS, inv, lane))
+                        return DEFERRED;
+                    // Pass 0 solves the system (zbuf = g_F, or -u_A in the
+                    // complement form); pass 1 solves it again for the
+                    // residual g_F - (G x)_F through the same factor (the
+                    // explicit inverse alone is not backward stable in FP32).
+                    float base[KW], w[KW];
 #pragma unroll
-                        for (int t = 0; t < PT; ++t) {
-                            const int a = lane + 32 * t;
-                            r[t] = a < p ? zbuf[a] : 0.0f;
-                        }
-                        subst32<PT>(p, Lw, LS, inv, r, lane);
-                        __syncwarp();
-#pragma unroll
-                        for (int t = 0; t < PT; ++t)
-                            if (lane + 32 * t < p)
-                                zbuf[lane + 32 * t] = r[t];
-                        __syncwarp();
-                    }
-                    if (!comp) {
-#pragma unroll
-                        for (int s = 0; s < KW; ++s)
-                            x[s] = inF[s] ? zbuf[rank[s]] : 0.0f;
-                    } else {
-                        float acc[KW];
-#pragma unroll
-                        for (int s = 0; s < KW; ++s)
-                            acc[s] = u[s];
-                        mv_list<KW>(Ms, widx, zbuf, p4, acc, lane);
-#pragma unroll
-                        for (int s = 0; s < KW; ++s)
-                            x[s] = inF[s] ? acc[s] : 0.0f;
-                    }
-                    // One refinement step through the same factor: the explicit
-                    // inverse alone is not backward stable in FP32.
-                    if (nF > 0) {
-                        float w[KW], res[KW], up[KW];
-#pragma unroll
-                        for (int s = 0; s < KW; ++s) {
-                            w[s] = 0.0f;
-                            up[s] = 0.0f;
-                        }
-                        if (!comp) {
-                            mv_list<KW>(Gs, widx, zbuf, p4, w, lane);   // zbuf = x_F
-                        } else {
-                            stage_vec<KW>(stage, x, lane);
-                            mv_full<KW>(Gs, k4, stage, w, lane);
-                        }
-#pragma unroll
-                        for (int s = 0; s < KW; ++s)
-                            res[s] = inF[s] ? g[s] - w[s] : 0.0f;
-                        if (comp) {
-                            stage_vec<KW>(stage, res, lane);
-                            mv_full<KW>(Ms, k4, stage, up, lane);
-                        }
-                        __syncwarp();
-#pragma unroll
-                        for (int s = 0; s < KW; ++s)
-                            if (inS[s])
-                                zbuf[rank[s]] = comp ? -up[s] : res[s];
-                        __syncwarp();
+                    for (int s = 0; s < KW; ++s)
+                        base[s] = u[s];
+                    for (int pass = 0;; ++pass) {
                         if (p > 0) {
+                            float r[PT];
 #pragma unroll
                             for (int t = 0; t < PT; ++t) {
                                 const int a = lane + 32 * t;
@@ -442,36 +400,50 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
                                     zbuf[lane + 32 * t] = r[t];
                             __syncwarp();
                         }
-                        if (!comp) {
+                        // The step: dx_F from the direct solution, or
+                        // base_F + M_FA z_A from the complement one.
+                        if (comp)
+                            mv_list<KW>(Ms, widx, zbuf, p4, base, lane);
 #pragma unroll
-                            for (int s = 0; s < KW; ++s)
-                                if (inF[s])
-                                    x[s] += zbuf[rank[s]];
-                        } else {
-                            mv_list<KW>(Ms, widx, zbuf, p4, up, lane);
-#pragma unroll
-                            for (int s = 0; s < KW; ++s)
-                                if (inF[s])
-                                    x[s] += up[s];
+                        for (int s = 0; s < KW; ++s) {
+                            const float dx = inF[s] ? (comp ? base[s] : zbuf[rank[s]]) : 0.0f;
+                            x[s] = pass ? x[s] + dx : dx;
+                            w[s] = 0.0f;
                         }
-                    }
-                    // y = G x - g off F (0 on F), from the refined x.
-                    float w[KW];
+                        // w = G x: over the F list in the direct form, all
+                        // rows in the complement form.
+                        if (!comp) {
+                            __syncwarp();
 #pragma unroll
-                    for (int s = 0; s < KW; ++s)
-                        w[s] = 0.0f;
-                    if (!comp) {
+                            for (int s = 0; s < KW; ++s)
+                                if (inS[s])
+                                    zbuf[rank[s]] = x[s];
+                            __syncwarp();
+                            mv_list<KW>(Gs, widx, zbuf, p4, w, lane);
+                        } else {
+                            stage_vec<KW>(stage, x, lane);
+                            mv_full<KW>(Gs, k4, stage, w, lane);
+                        }
+                        if (pass == 1 || nF == 0)
+                            break;
+                        float res[KW];
+#pragma unroll
+                        for (int s = 0; s < KW; ++s) {
+                            res[s] = inF[s] ? g[s] - w[s] : 0.0f;
+                            base[s] = 0.0f;
+                        }
+                        if (comp) {
+                            stage_vec<KW>(stage, res, lane);
+                            mv_full<KW>(Ms, k4, stage, base, lane);   // up = M res
+                        }
                         __syncwarp();
 #pragma unroll
                         for (int s = 0; s < KW; ++s)
                             if (inS[s])
-                                zbuf[rank[s]] = x[s];
+                                zbuf[rank[s]] = comp ? -base[s] : res[s];
                         __syncwarp();
-                        mv_list<KW>(Gs, widx, zbuf, p4, w, lane);
-                    } else {
-                        stage_vec<KW>(stage, x, lane);
-                        mv_full<KW>(Gs, k4, stage, w, lane);
                     }
+                    // y = G x - g off F (0 on F), from the refined x.
                     float xm = 0.0f;
 #pragma unroll
                     for (int s = 0; s < KW; ++s) {
@@ -482,14 +454,20 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
                     return NMF_OK;
                 };
 
+                // One solve per exchange round, from a single call site.
                 bool anyF = false;
 #pragma unroll
                 for (int s = 0; s < KW; ++s)
                     anyF |= inF[s];
-                if (__any_sync(FULL, anyF))
-                    status = solve();
+                bool need = __any_sync(FULL, anyF);   // else x = 0, y = -g already
                 int alpha = 3, beta = k + 1;
-                while (status == NMF_OK) {
+                for (;;) {
+                    if (need) {
+                        status = solve();
+                        if (status != NMF_OK)
+                            break;
+                    }
+                    need = true;
                     bool inf[KW];
                     unsigned vm[KW];
                     int nV = 0;
@@ -506,14 +484,15 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
                         status = NMF_ERR_NOT_CONVERGED;
                         break;
                     }
-                    if (nV < beta) {   // full exchange; the count dropped
-                        beta = nV;
-                        alpha = 3;
-#pragma unroll
-                        for (int s = 0; s < KW; ++s)
-                            inF[s] = inF[s] != inf[s];
-                    } else if (alpha >= 1) {   // full exchange, one of three more
-                        alpha -= 1;
+                    if (nV < beta || alpha >= 1) {
+                        // Full exchange: the count dropped (reset the budget),
+                        // or one of the three further full exchanges.
+                        if (nV < beta) {
+                            beta = nV;
+                            alpha = 3;
+                        } else {
+                            alpha -= 1;
+                        }
 #pragma unroll
                         for (int s = 0; s < KW; ++s)
                             inF[s] = inF[s] != inf[s];
@@ -529,7 +508,6 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
                                 inF[s] = !inF[s];
                     }
                     rounds += 1;
-                    status = solve();
                 }
                 if (status != DEFERRED) {
                     bool nf = false;
