@@ -483,9 +483,6 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                 for (int s = 0; s < KW; ++s)
                     x[s] = 0;
             } else {
-                // Unconstrained solution u = M g.
-                if (HAVE_M)
-                    warp_matvec<T, KW>(Ms, k, g, u, stage, lane);
                 // Starting partition: empty (cold) or the given bitmask (warm).
                 if (P.pin) {
 #pragma unroll
@@ -499,18 +496,20 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                         inF[s] = f && usable[s];
                     }
                 }
+                bool have_u = false;   // u = M g, formed when a complement solve first needs it
 
                 // Candidate point of the current partition: fills x and y.
                 auto solve = [&]() -> int {
-                    unsigned fm[KW];
                     int nF = 0;
 #pragma unroll
-                    for (int s = 0; s < KW; ++s) {
-                        fm[s] = __ballot_sync(FULL, inF[s]);
-                        nF += __popc(fm[s]);
-                    }
+                    for (int s = 0; s < KW; ++s)
+                        nF += __popc(__ballot_sync(FULL, inF[s]));
                     const int nA = nU - nF;
                     const bool comp = HAVE_M && nA < nF;
+                    if (comp && !have_u) {
+                        warp_matvec<T, KW>(Ms, k, g, u, stage, lane);
+                        have_u = true;
+                    }
                     bool inS[KW];
                     int rank[KW];
                     int pos = 0;
@@ -546,47 +545,54 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                         }
                         __syncwarp();
                     }
+                    // The compact solution z (zbuf, p entries) against the
+                    // rows it touches: x_F = u_F + M_FA z in the complement
+                    // form; y = G_{:,F} x_F - g in the direct form. Both loop
+                    // over the p-entry list, not over all k rows.
+                    const T *Lst = comp ? Ms : Gs;
+                    T acc[KW];
+#pragma unroll
+                    for (int s = 0; s < KW; ++s)
+                        acc[s] = comp ? u[s] : -g[s];
+                    for (int a = 0; a < p; ++a) {
+                        const T za = zbuf[a];
+                        const T *row = Lst + widx[a] * k;
+#pragma unroll
+                        for (int s = 0; s < KW; ++s) {
+                            const int i = lane + 32 * s;
+                            if (i < k)
+                                acc[s] = fma(row[i], za, acc[s]);
+                        }
+                    }
 #pragma unroll
                     for (int s = 0; s < KW; ++s) {
-                        const int i = lane + 32 * s;
-                        if (!comp) {
-                            x[s] = inF[s] ? zbuf[rank[s]] : (T)0;
+                        if (comp) {
+                            // y_A is the complement solution itself (accurate in FP64).
+                            x[s] = inF[s] ? acc[s] : (T)0;
+                            y[s] = inS[s] ? zbuf[rank[s]] : (inF[s] ? (T)0 : -g[s]);
                         } else {
-                            T acc = u[s];
-                            if (inF[s])
-                                for (int a = 0; a < p; ++a)
-                                    acc = fma(Ms[widx[a] * k + i], zbuf[a], acc);
-                            x[s] = inF[s] ? acc : (T)0;
+                            x[s] = inF[s] ? zbuf[rank[s]] : (T)0;
+                            y[s] = inF[s] ? (T)0 : acc[s];
                         }
                     }
                     __syncwarp();
-                    // y = G x - g off F, 0 on F: the complement solve gives y_A
-                    // directly (accurate in FP64); the direct one recomputes it.
-                    if (comp) {
-#pragma unroll
-                        for (int s = 0; s < KW; ++s)
-                            y[s] = inS[s] ? zbuf[rank[s]] : (inF[s] ? (T)0 : -g[s]);
-                    } else {
-                        T w[KW];
-#pragma unroll
-                        for (int s = 0; s < KW; ++s)
-                            w[s] = 0;
-                        warp_matvec<T, KW>(Gs, k, x, w, stage, lane);
-#pragma unroll
-                        for (int s = 0; s < KW; ++s)
-                            y[s] = inF[s] ? (T)0 : w[s] - g[s];
-                    }
                     return NMF_OK;
                 };
 
+                // One solve per exchange round, from a single call site.
                 bool anyF = false;
 #pragma unroll
                 for (int s = 0; s < KW; ++s)
                     anyF |= inF[s];
-                if (__any_sync(FULL, anyF))
-                    status = solve();
+                bool need = __any_sync(FULL, anyF);   // else x = 0, y = -g already
                 int alpha = 3, beta = k + 1;
-                while (status == NMF_OK) {
+                for (;;) {
+                    if (need) {
+                        status = solve();
+                        if (status != NMF_OK)
+                            break;
+                    }
+                    need = true;
                     bool inf[KW];
                     unsigned vm[KW];
                     int nV = 0;
@@ -602,18 +608,17 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                         status = NMF_ERR_NOT_CONVERGED;
                         break;
                     }
-                    if (nV < beta) {
-                        beta = nV;
-                        alpha = 3;
+                    if (nV < beta || alpha >= 1) {   // full exchange
+                        if (nV < beta) {
+                            beta = nV;
+                            alpha = 3;
+                        } else {
+                            alpha -= 1;
+                        }
 #pragma unroll
                         for (int s = 0; s < KW; ++s)
                             inF[s] = inF[s] != inf[s];
-                    } else if (alpha >= 1) {
-                        alpha -= 1;
-#pragma unroll
-                        for (int s = 0; s < KW; ++s)
-                            inF[s] = inF[s] != inf[s];
-                    } else {
+                    } else {   // backup rule: the largest infeasible index alone
                         int top = -1;
 #pragma unroll
                         for (int s = KW - 1; s >= 0; --s)
@@ -625,7 +630,6 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                                 inF[s] = !inF[s];
                     }
                     rounds += 1;
-                    status = solve();
                 }
                 bool nf = false;
 #pragma unroll
