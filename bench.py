@@ -35,6 +35,9 @@ WORKLOADS = {
                      "dense A=W0*H0+|N(0,0.05^2)| 24000x16000 k=50 fp32 (1.5 GB)"),
     "dense-small": (2000, 1000, 10, 0.01,
                     "dense A=W0*H0+|N(0,0.01^2)| 2000x1000 k=10 fp32"),
+    "dense-video": (1013400, 2400, 50, 0.05,
+                    "dense A=W0*H0+|N(0,0.05^2)| 1013400x2400 k=50 fp32 (9.7 GB; the shape of the "
+                    "paper's Video matrix, synthetic)"),
     "sparse-large": (2000000, 1000000, 50, None,
                      "sparse CSR 2000000x1000000, 20M uniform draws, values U(0,1], k=50"),
     "sparse-medium": (200000, 100000, 50, None,

@@ -897,7 +897,7 @@ struct TcWork {
     size_t f_off, w_off, part_off, split_off, total;
 };
 
-constexpr int TC_MAX_SPLITS = 4;
+constexpr int TC_MAX_SPLITS = 16;   // tall-skinny A: few output tiles, a long contraction
 
 // Contraction splits that fill the last wave of CTAs better (1 CTA per SM).
 int choose_splits(int64_t P, int64_t Q)
@@ -937,8 +937,9 @@ TcWork tc_work(int64_t m, int64_t n, int k, int trans, bool obj)
     if (obj)
         off += al(sizeof(double) * (size_t)(Pp / TC_BM));
     w.split_off = off;
-    if (!obj)
-        off += al(sizeof(float) * (size_t)TC_MAX_SPLITS * (size_t)(P > 0 ? P : 1) * (size_t)k);
+    const int splits = obj ? 1 : choose_splits(P, Q);
+    if (splits > 1)
+        off += al(sizeof(float) * (size_t)splits * (size_t)(P > 0 ? P : 1) * (size_t)k);
     w.total = off;
     return w;
 }
