@@ -26,6 +26,7 @@ LIB_PATH = os.path.join(_HERE, "liboracle.so")
 OK = 0
 NOT_CONVERGED = 4
 SINGULAR = 5
+SOLVERS = {"bpp": 0, "mu": 1, "hals": 2}
 
 
 def compile_source(src: str, out: str) -> str:
@@ -67,7 +68,9 @@ class Oracle:
         lib.oracle_objective_csr.restype = ctypes.c_double
         lib.oracle_bpp.argtypes = [P, I, P, I64, P, P, I, I, P, P]
         lib.oracle_bpp.restype = I
-        lib.oracle_anls.argtypes = [I, P, I64, P, P, P, I64, I64, I, P, P, I, I, I, P, P, P, P]
+        lib.oracle_anls.argtypes = [I, P, I64, P, P, P, I64, I64, I, P, P, I, I, I, P, P, P, P, I]
+        lib.oracle_mu.argtypes = [P, I, P, I64, P]
+        lib.oracle_hals.argtypes = [P, I, P, I64, P]
         lib.oracle_anls.restype = I
         self.lib = lib
 
@@ -139,10 +142,26 @@ class Oracle:
                                     _p(rounds), _p(status))
         return X, passive, rounds, status, worst
 
+    def mu(self, G, R, X) -> np.ndarray:
+        """One MU step (Eq. 5) of the rows of X (rows x k) with Gram G and
+        right-hand sides R (rows x k); returns the new X."""
+        G, R = _f64(G), _f64(R)
+        X = _f64(X).copy()
+        self.lib.oracle_mu(_p(G), G.shape[0], _p(R), X.shape[0], _p(X))
+        return X
+
+    def hals(self, G, R, X) -> np.ndarray:
+        """One HALS sweep (Eq. 6) of the rows of X; returns the new X."""
+        G, R = _f64(G), _f64(R)
+        X = _f64(X).copy()
+        self.lib.oracle_hals(_p(G), G.shape[0], _p(R), X.shape[0], _p(X))
+        return X
+
     def anls(self, A=None, W0=None, Ht0=None, iters: int = 10, warm: bool = False,
-             max_rounds: int = 1000, csr=None, shape=None):
+             max_rounds: int = 1000, csr=None, shape=None, solver: str = "bpp"):
         """Alg. 1 for ``iters`` iterations from (W0, H0^T). Dense A (float32 m x n)
-        or csr=(rowptr, colidx, vals) with shape=(m, n).
+        or csr=(rowptr, colidx, vals) with shape=(m, n). solver: "bpp" (Sec. 4.2),
+        "mu" (Eq. 5) or "hals" (Eq. 6).
 
         Returns dict(W, Ht, f (iters+1), passive_W, passive_H, rounds (2*iters),
         status)."""
@@ -158,7 +177,8 @@ class Oracle:
             A = np.ascontiguousarray(A, dtype=np.float32)
             assert A.shape == (m, n)
             st = self.lib.oracle_anls(0, _p(A), n, None, None, None, m, n, k, _p(W), _p(Ht),
-                                      iters, int(warm), max_rounds, _p(f), _p(pW), _p(pH), _p(rh))
+                                      iters, int(warm), max_rounds, _p(f), _p(pW), _p(pH), _p(rh),
+                                      SOLVERS[solver])
         else:
             rowptr, colidx, vals = csr
             rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
@@ -167,7 +187,7 @@ class Oracle:
             assert shape == (m, n)
             st = self.lib.oracle_anls(1, None, 0, _p(rowptr), _p(colidx), _p(vals), m, n, k,
                                       _p(W), _p(Ht), iters, int(warm), max_rounds, _p(f), _p(pW),
-                                      _p(pH), _p(rh))
+                                      _p(pH), _p(rh), SOLVERS[solver])
         return dict(W=W, Ht=Ht, f=f, passive_W=pW, passive_H=pH, rounds=rh, status=st)
 
 
@@ -209,5 +229,14 @@ def bpp(G, B, passive_in=None, max_rounds=1000):
     return default().bpp(G, B, passive_in, max_rounds)
 
 
-def anls(A=None, W0=None, Ht0=None, iters=10, warm=False, max_rounds=1000, csr=None, shape=None):
-    return default().anls(A, W0, Ht0, iters, warm, max_rounds, csr, shape)
+def mu(G, R, X):
+    return default().mu(G, R, X)
+
+
+def hals(G, R, X):
+    return default().hals(G, R, X)
+
+
+def anls(A=None, W0=None, Ht0=None, iters=10, warm=False, max_rounds=1000, csr=None, shape=None,
+         solver="bpp"):
+    return default().anls(A, W0, Ht0, iters, warm, max_rounds, csr, shape, solver)

@@ -27,6 +27,13 @@
  *           exchanges after it stops dropping, then single exchange of the
  *           largest infeasible index (the backup rule).
  *
+ * Alternative local updates the paper names for the same two steps (Sec. 3):
+ *   Eq. 5   MU: every entry of W scaled by (A H^T)_ij / (W H H^T)_ij, all from
+ *           the iterate before the update; likewise H with (W^T A) and W^T W H.
+ *   Eq. 6   HALS: column i of W (row i of H) replaced by
+ *           [(A H^T)^i - sum_{l != i} (H H^T)_li w^l]_+ / (H H^T)_ii, the columns
+ *           taken in order 1..k with the newest values of the others.
+ *
  * Storage: A is float32 row-major (the stored input both paths read); W is
  * m x k row-major; H is kept as H^T, n x k row-major, so each right-hand side
  * of either half-step is one contiguous k-vector.
@@ -343,6 +350,75 @@ int oracle_bpp(const double *G, int k, const double *B, int64_t nrhs, double *X,
     return worst;
 }
 
+/* MU step of Eq. 5 for the rows of X (rows x k): with R the matching rows of
+ * A H^T (or of (W^T A)^T) and G = H H^T (or W^T W),
+ *   x_ij <- x_ij R_ij / (X G)_ij,
+ * every (X G)_ij from the X before the step. Where (X G)_ij is not positive
+ * (only when x_ij = 0 or G_jj = 0 for nonnegative data) x_ij is left as it is:
+ * Eq. 5 is silent there and 0 is a fixed point of the rule. */
+void oracle_mu(const double *G, int k, const double *R, int64_t rows, double *X)
+{
+#pragma omp parallel
+    {
+        double *den = (double *)malloc(sizeof(double) * (size_t)k);
+#pragma omp for schedule(static)
+        for (int64_t r = 0; r < rows; ++r) {
+            double *x = X + r * k;
+            for (int j = 0; j < k; ++j) {
+                double d = 0.0;
+                for (int l = 0; l < k; ++l)
+                    d += x[l] * G[l * k + j];
+                den[j] = d;
+            }
+            for (int j = 0; j < k; ++j)
+                if (den[j] > 0.0)
+                    x[j] = x[j] * R[r * k + j] / den[j];
+        }
+        free(den);
+    }
+}
+
+/* HALS step of Eq. 6 for the rows of X: for i = 0..k-1 in order,
+ *   x_i <- [R_i - sum_{l != i} G_li x_l]_+ / G_ii,
+ * the sum using the values of x already updated for l < i. A column with
+ * G_ii <= 0 (its factor row or column is zero) is set to 0: Eq. 6 divides by
+ * G_ii, and such a column does not change f. */
+void oracle_hals(const double *G, int k, const double *R, int64_t rows, double *X)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < rows; ++r) {
+        double *x = X + r * k;
+        for (int i = 0; i < k; ++i) {
+            const double gii = G[i * k + i];
+            if (!(gii > 0.0)) {
+                x[i] = 0.0;
+                continue;
+            }
+            double num = R[r * k + i];
+            for (int l = 0; l < k; ++l)
+                if (l != i)
+                    num -= G[l * k + i] * x[l];
+            x[i] = (num > 0.0 ? num : 0.0) / gii;
+        }
+    }
+}
+
+/* One local update of X from (G, R) by the chosen method: 0 BPP (x = the exact
+ * NLS minimiser), 1 MU, 2 HALS. */
+static int local_update(int solver, const double *G, int k, const double *R, int64_t rows,
+                        double *X, uint8_t *passive, int warm, int max_rounds, int32_t *rounds)
+{
+    if (solver == 1) {
+        oracle_mu(G, k, R, rows, X);
+        return OR_OK;
+    }
+    if (solver == 2) {
+        oracle_hals(G, k, R, rows, X);
+        return OR_OK;
+    }
+    return oracle_bpp(G, k, R, rows, X, passive, warm, max_rounds, rounds, NULL);
+}
+
 /* ---------------------------------------------------------------------------
  * ANLS (Alg. 1 with Eq. 2): T iterations, W-update then H-update, each an
  * exact block minimisation solved row by row with BPP.
@@ -352,12 +428,15 @@ int oracle_bpp(const double *G, int k, const double *B, int64_t nrhs, double *X,
  *   pW (m x k bytes) / pH (n x k bytes), nullable: passive sets; with warm = 1
  *   each solve starts from the previous iteration's sets (first solve cold).
  *   rounds_hist (nullable, 2 * iters): total exchange rounds per half-step.
+ *   solver: 0 BPP (the paper's method), 1 MU (Eq. 5), 2 HALS (Eq. 6); for MU and
+ *   HALS each half-step is one update of the factor, and W, Ht are read as the
+ *   iterate being updated (rounds are 0).
  * Returns the worst BPP status seen.
  * ------------------------------------------------------------------------- */
 int oracle_anls(int kind, const float *A, int64_t lda, const int64_t *rowptr,
                 const int32_t *colidx, const float *vals, int64_t m, int64_t n, int k,
                 double *W, double *Ht, int iters, int warm, int max_rounds, double *f_hist,
-                uint8_t *pW, uint8_t *pH, int64_t *rounds_hist)
+                uint8_t *pW, uint8_t *pH, int64_t *rounds_hist, int solver)
 {
     double *G = (double *)malloc(sizeof(double) * (size_t)k * (size_t)k);
     double *V = (double *)malloc(sizeof(double) * (size_t)m * (size_t)k);
@@ -379,7 +458,8 @@ int oracle_anls(int kind, const float *A, int64_t lda, const int64_t *rowptr,
             oracle_mm_dense(A, m, n, lda, Ht, k, 0, V);
         else
             oracle_mm_csr(rowptr, colidx, vals, m, n, Ht, k, 0, V);
-        int st = oracle_bpp(G, k, V, m, W, PW, w, max_rounds, rw, NULL);
+        memset(rw, 0, sizeof(int32_t) * (size_t)m);
+        int st = local_update(solver, G, k, V, m, W, PW, w, max_rounds, rw);
         if (st > worst)
             worst = st;
         if (rounds_hist) {
@@ -394,7 +474,8 @@ int oracle_anls(int kind, const float *A, int64_t lda, const int64_t *rowptr,
             oracle_mm_dense(A, m, n, lda, W, k, 1, Y);
         else
             oracle_mm_csr(rowptr, colidx, vals, m, n, W, k, 1, Y);
-        st = oracle_bpp(G, k, Y, n, Ht, PH, w, max_rounds, rw, NULL);
+        memset(rw, 0, sizeof(int32_t) * (size_t)n);
+        st = local_update(solver, G, k, Y, n, Ht, PH, w, max_rounds, rw);
         if (st > worst)
             worst = st;
         if (rounds_hist) {

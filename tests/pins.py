@@ -225,5 +225,105 @@ def pin_planted(orc):
     assert np.all(np.sort(C.max(axis=1)) > 1 - 1e-6), C
 
 
+def _spd_nonneg(k, rng):
+    """A Gram of a nonnegative factor (entrywise >= 0, positive definite)."""
+    C = rng.uniform(0.0, 1.0, (3 * k, k))
+    return C.T @ C
+
+
+def _nls_value(G, g, x):
+    return 0.5 * x @ G @ x - g @ x
+
+
+def pin_mu(orc, seed=13):
+    """Eq. 5 (MU). Hand-worked step: G = [[2, 1], [1, 2]], R = (3, 3),
+    x = (1, 2): X G = (4, 5), so x becomes (1*3/4, 2*3/5) = (0.75, 1.2); every
+    denominator uses the x from before the step (taking the new x_1 would give
+    x_2 = 6/4.75). Then: the NLS minimiser (brute force) is a fixed point;
+    k = 1 reaches R/G in one step; a zero row stays zero (no 0/0); and the
+    NLS objective never increases (Lee and Seung 2001)."""
+    G = np.array([[2.0, 1.0], [1.0, 2.0]])
+    X = orc.mu(G, np.array([[3.0, 3.0]]), np.array([[1.0, 2.0]]))
+    np.testing.assert_allclose(X, [[0.75, 1.2]], rtol=0, atol=1e-15)
+    rng = np.random.default_rng(seed)
+    for k in (2, 4, 6):
+        G = _spd_nonneg(k, rng)
+        g = rng.uniform(0.0, 1.0, k) * np.diag(G)
+        sols = brute_force_nls(G, g)
+        assert len(sols) == 1
+        xs = sols[0]
+        np.testing.assert_allclose(orc.mu(G, g[None, :], xs[None, :])[0], xs, rtol=1e-10,
+                                   atol=1e-14)
+    X = orc.mu(np.array([[4.0]]), np.array([[6.0], [2.0]]), np.array([[0.3], [7.0]]))
+    np.testing.assert_allclose(X[:, 0], [1.5, 0.5], rtol=1e-15)
+    X = orc.mu(G, g[None, :], np.zeros((1, len(g))))
+    assert np.isfinite(X).all() and (X == 0).all()
+    k = 8
+    G = _spd_nonneg(k, rng)
+    g = rng.uniform(0.0, 1.0, k) * np.diag(G)
+    x = rng.uniform(0.1, 1.0, k)
+    f = [_nls_value(G, g, x)]
+    for _ in range(30):
+        x = orc.mu(G, g[None, :], x[None, :])[0]
+        f.append(_nls_value(G, g, x))
+    f = np.array(f)
+    assert (f[1:] <= f[:-1] + 1e-12 * np.abs(f[:-1])).all(), f
+
+
+def pin_hals(orc, seed=17):
+    """Eq. 6 (HALS). Hand-worked sweep: G = [[2, 1], [1, 2]], R = (3, 3),
+    x = (0, 0): x_1 = (3 - 1*0)/2 = 1.5, then x_2 = (3 - 1*1.5)/2 = 0.75 with the
+    new x_1 (the old one would give 1.5). With R = (3, -3) the second numerator
+    is -4.5 and the projection gives x_2 = 0. A diagonal G gives the exact NLS
+    solution max(R, 0)/G_ii in one sweep; repeated sweeps converge to the
+    brute-force minimiser (coordinate descent on a strictly convex quadratic)
+    with a non-increasing objective; a zero Gram column gives 0."""
+    G = np.array([[2.0, 1.0], [1.0, 2.0]])
+    X = orc.hals(G, np.array([[3.0, 3.0], [3.0, -3.0]]), np.zeros((2, 2)))
+    np.testing.assert_allclose(X, [[1.5, 0.75], [1.5, 0.0]], rtol=0, atol=1e-15)
+    D = np.diag([2.0, 4.0, 0.5])
+    R = np.array([[1.0, -2.0, 3.0]])
+    np.testing.assert_allclose(orc.hals(D, R, np.ones((1, 3))), [[0.5, 0.0, 6.0]], rtol=1e-15)
+    rng = np.random.default_rng(seed)
+    for k in (3, 5, 7):
+        G = _spd_nonneg(k, rng)
+        g = rng.normal(0.0, 1.0, k) * np.diag(G)
+        sols = brute_force_nls(G, g)
+        assert len(sols) == 1
+        x = np.zeros(k)
+        f = [_nls_value(G, g, x)]
+        for _ in range(3000):
+            x = orc.hals(G, g[None, :], x[None, :])[0]
+            f.append(_nls_value(G, g, x))
+        f = np.array(f)
+        assert (f[1:] <= f[:-1] + 1e-12 * np.abs(f[:-1]) + 1e-300).all()
+        np.testing.assert_allclose(x, sols[0], rtol=1e-7, atol=1e-9 * np.abs(sols[0]).max())
+        np.testing.assert_allclose(orc.hals(G, g[None, :], sols[0][None, :])[0], sols[0],
+                                   rtol=1e-10, atol=1e-12 * np.abs(sols[0]).max())
+    Gz = np.array([[2.0, 0.0], [0.0, 0.0]])
+    np.testing.assert_allclose(orc.hals(Gz, np.array([[4.0, 1.0]]), np.ones((1, 2))), [[2.0, 0.0]])
+
+
+def pin_anls_local(orc, seed=19):
+    """Alg. 1 with the MU and HALS updates: the objective never increases
+    (each update does not increase f with the other factor fixed) and it ends
+    at the recomputed ||A - W H||^2; MU keeps the starting zero pattern."""
+    m, n, k = 70, 40, 5
+    A = synth.dense_planted(m, n, k, 0.05, seed=seed)
+    W0, Ht0 = synth.init_factors(m, n, k, seed=seed)
+    Ad = A.astype(np.float64)
+    for solver in ("mu", "hals"):
+        r = orc.anls(A, W0, Ht0, iters=25, solver=solver)
+        f = r["f"]
+        assert (f[1:] <= f[:-1] * (1 + 1e-12)).all(), (solver, f)
+        assert f[-1] < 0.5 * f[0], (solver, f[0], f[-1])
+        np.testing.assert_allclose(f[-1], np.sum((Ad - r["W"] @ r["Ht"].T) ** 2), rtol=1e-12)
+        assert (r["W"] >= 0).all() and (r["Ht"] >= 0).all()
+    Wz = W0.astype(np.float64).copy()
+    Wz[::7, 2] = 0.0
+    r = orc.anls(A, Wz, Ht0, iters=3, solver="mu")
+    assert (r["W"][::7, 2] == 0).all()
+
+
 ALL_PINS = [pin_golden, pin_bruteforce, pin_nnls, pin_closed_forms, pin_kkt_and_warm,
-            pin_products, pin_anls, pin_planted]
+            pin_products, pin_anls, pin_planted, pin_mu, pin_hals, pin_anls_local]

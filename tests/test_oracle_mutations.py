@@ -22,6 +22,10 @@ MUTANTS = {
     "infeasible_sign": ("int inf = usable[i] && ((F[i] && x[i] < 0.0) || (!F[i] && y[i] < 0.0));",
                         "int inf = usable[i] && ((F[i] && x[i] < 0.0) || (!F[i] && y[i] > 0.0));"),
     "h_update_wrong_gram": ("oracle_gram(W, m, k, G);", "oracle_gram(Ht, n, k, G);"),
+    "mu_dropped_factor": ("x[j] = x[j] * R[r * k + j] / den[j];", "x[j] = R[r * k + j] / den[j];"),
+    "mu_wrong_gram_index": ("d += x[l] * G[l * k + j];", "d += x[l] * G[l * k + l];"),
+    "hals_dropped_new_values": ("num -= G[l * k + i] * x[l];", "num -= G[l * k + i] * (l < i ? 0.0 : x[l]);"),
+    "hals_no_projection": ("x[i] = (num > 0.0 ? num : 0.0) / gii;", "x[i] = num / gii;"),
 }
 
 
