@@ -47,6 +47,12 @@ WORKLOADS = {
 SPARSE_DRAWS = {"sparse-large": 20000000, "sparse-medium": 2000000}
 SEED = 1509
 METRIC = "ANLS-BPP iterations/s"
+
+
+def metric_name(solver: str) -> str:
+    """BPP is the paper's local solver and the headline; MU (Eq. 5) and HALS
+    (Eq. 6) run the same iteration with the other update."""
+    return METRIC if solver == "bpp" else f"ANLS-{solver.upper()} iterations/s"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 SM_COUNT = 152
@@ -133,7 +139,7 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def oracle_sample(m, n, k, sigma, steps, warm: bool):
+def oracle_sample(m, n, k, sigma, steps, warm: bool, solver="bpp"):
     """Time the FP64 oracle (as it stands) on a crop of the workload and scale
     to the full size by m*n (the products and objective dominate; they scale
     with m*n, the NLS work with m+n). Returns (iter/s full-size, sample text,
@@ -144,9 +150,10 @@ def oracle_sample(m, n, k, sigma, steps, warm: bool):
     A = synth.dense_planted(ms, ns, k, sigma, seed=SEED, n_full=n)
     W0, Ht0 = synth.init_factors(ms, ns, k, seed=SEED)
     orc = oracle.default()
-    r = orc.anls(A, W0, Ht0, iters=1, warm=warm)        # warm-up (first iteration)
+    r = orc.anls(A, W0, Ht0, iters=1, warm=warm, solver=solver)   # warm-up (first iteration)
     t0 = time.perf_counter()
-    orc.anls(A, r["W"].astype("float32"), r["Ht"].astype("float32"), iters=steps, warm=warm)
+    orc.anls(A, r["W"].astype("float32"), r["Ht"].astype("float32"), iters=steps, warm=warm,
+             solver=solver)
     dt = (time.perf_counter() - t0) / steps
     scale = (m * n) / (ms * ns)
     sample = (f"oracle ANLS iterations on the {ms}x{ns} crop of the same recipe (k={k}), "
@@ -154,7 +161,7 @@ def oracle_sample(m, n, k, sigma, steps, warm: bool):
     return 1.0 / (dt * scale), sample, orc.num_threads(), dt
 
 
-def oracle_sample_sparse(m, n, k, draws, steps, warm: bool, csr):
+def oracle_sample_sparse(m, n, k, draws, steps, warm: bool, csr, solver="bpp"):
     """Time the FP64 oracle on the top-left (m/20) x (n/20) block of the same
     CSR matrix and scale by the row-plus-column ratio (the NLS work, one solve
     per row and per column, dominates the sparse iteration)."""
@@ -173,10 +180,10 @@ def oracle_sample_sparse(m, n, k, draws, steps, warm: bool, csr):
     W0, Ht0 = synth.init_factors(ms, ns, k, seed=SEED)
     orc = oracle.default()
     crop = (rp, np.ascontiguousarray(c_c), np.ascontiguousarray(v_c))
-    r = orc.anls(None, W0, Ht0, iters=1, warm=warm, csr=crop, shape=(ms, ns))
+    r = orc.anls(None, W0, Ht0, iters=1, warm=warm, csr=crop, shape=(ms, ns), solver=solver)
     t0 = time.perf_counter()
     orc.anls(None, r["W"].astype("float32"), r["Ht"].astype("float32"), iters=steps, warm=warm,
-             csr=crop, shape=(ms, ns))
+             csr=crop, shape=(ms, ns), solver=solver)
     dt = (time.perf_counter() - t0) / steps
     scale = (m + n) / (ms + ns)
     sample = (f"oracle ANLS iterations on the top-left {ms}x{ns} block of the same CSR "
@@ -196,14 +203,17 @@ def run_reference(args, rank, world):
         import synth
         csr = synth.csr_uniform(m, n, SPARSE_DRAWS[args.workload], seed=SEED)
         value, sample, cores, dt = oracle_sample_sparse(m, n, k, SPARSE_DRAWS[args.workload],
-                                                        steps, args.start == "warm", csr)
+                                                        steps, args.start == "warm", csr,
+                                                        args.solver)
     else:
-        value, sample, cores, dt = oracle_sample(m, n, k, sigma, steps, args.start == "warm")
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s",
+        value, sample, cores, dt = oracle_sample(m, n, k, sigma, steps, args.start == "warm",
+                                                 args.solver)
+    line = {"impl": "reference", "metric": metric_name(args.solver), "value": value,
+            "unit": "iter/s",
             "n_gpus": world, "steps": steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "start": args.start},
+            "config": {"workload": desc, "start": args.start, "solver": args.solver},
             "cpu_baseline": {"value": value, "unit": "iter/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0,
@@ -245,7 +255,7 @@ def run_ours(args, rank, world, local_rank):
     h = nmf.nmf_init(A, W0, Ht0, precision=args.precision,
                      start="cold" if learned else args.start,
                      max_bpp_rounds=args.max_rounds, objective_every=True,
-                     shape=(m, n) if sparse else None)
+                     shape=(m, n) if sparse else None, solver=args.solver)
     net = None
     if learned:
         # Learned starting partitions: the proposal network trains on every
@@ -357,7 +367,7 @@ def run_ours(args, rank, world, local_rank):
         h2 = nmf.nmf_init(A, W0, Ht0, precision=args.precision,
                           start="cold" if learned else args.start,
                           max_bpp_rounds=args.max_rounds, objective_every=True,
-                          shape=(m, n) if sparse else None)
+                          shape=(m, n) if sparse else None, solver=args.solver)
         if learned:
             h2.nmf_set_proposal(net, "use")    # the network trained above
         h2.nmf_iterate(args.steps)
@@ -387,21 +397,24 @@ def run_ours(args, rank, world, local_rank):
         if sparse:   # ~7 s per crop iteration on 16 cores: keep the sample near 20 s
             v, sample, cores, _ = oracle_sample_sparse(m, n, k, SPARSE_DRAWS[args.workload],
                                                        min(args.cpu_steps, 3),
-                                                       args.start == "warm", csr_host)
+                                                       args.start == "warm", csr_host,
+                                                       args.solver)
         else:
             v, sample, cores, _ = oracle_sample(m, n, k, sigma, args.cpu_steps,
-                                                args.start == "warm")
+                                                args.start == "warm", args.solver)
         cpu = {"value": v, "unit": "iter/s", "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
         rounds = st1["bpp_rounds"] - st0["bpp_rounds"]
         rhs = st1["bpp_rhs"] - st0["bpp_rhs"]
-        line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world,
+        line = {"metric": metric_name(args.solver), "value": value, "unit": "iter/s",
+                "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision == "fp32" else "bf16x3/f32",
                 "data": "synthetic",
                 "config": {"workload": desc, "precision": args.precision, "start": args.start,
+                           "solver": args.solver,
                            "seed": SEED,
                            "l2": "small input (L2-resident)" if args.workload == "dense-small"
                            else (f"CSR {8 * nnz / 1e9:.2f} GB + factors {8 * (m + n) * k / 1e9:.2f} GB, "
@@ -436,6 +449,8 @@ def main():
                     help="BPP starting partitions: empty, the previous iteration's, or the "
                          "proposal network's (trained during the warm-up iterations)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dense-large")
+    ap.add_argument("--solver", choices=["bpp", "mu", "hals"], default="bpp",
+                    help="local update: BPP (Sec. 4.2), MU (Eq. 5) or HALS (Eq. 6)")
     ap.add_argument("--max-rounds", type=int, default=100)
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
@@ -443,6 +458,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.solver != "bpp" and args.start == "learned":
+        ap.error("--start learned proposes BPP partitions; it needs --solver bpp")
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)
     local_rank = env_int("LOCAL_RANK", 0)

@@ -161,6 +161,20 @@ nmf_status nmf_nls_bpp_tune(const nmf_nls_desc *d, void *stream, int32_t *warps,
 #define NMF_NOALLOC_SCRATCH_BYTES (272 * 1024)
 nmf_status nmf_nls_bpp_noalloc(const nmf_nls_desc *d, void *stream);
 
+/* One MU step (Eq. 5) of the rows of X (rows x k, float32, device, updated
+ * in place), with G (k x k float64, the Gram of the fixed factor) and R (rows x k
+ * float32, its right-hand sides: A H^T for W, (W^T A)^T for H^T):
+ *   x_ij <- x_ij R_ij / (X G)_ij,  every (X G)_ij from the X before the step;
+ * x_ij is left unchanged where (X G)_ij <= 0. Asynchronous on `stream`. */
+nmf_status nmf_update_mu(int32_t k, int64_t rows, const double *G, const float *R, float *X,
+                         void *stream);
+
+/* One HALS sweep (Eq. 6) of the rows of X with the same arguments: for
+ * i = 0..k-1 in order, x_i <- [R_i - sum_{l != i} G_li x_l]_+ / G_ii using the
+ * newest x_l; x_i = 0 where G_ii <= 0. Asynchronous on `stream`. */
+nmf_status nmf_update_hals(int32_t k, int64_t rows, const double *G, const float *R, float *X,
+                           void *stream);
+
 /* Objective of Eq. 1 for dense A: f = sum_ij (A_ij - w_i . h_j)^2 with W
  * (m x k) and H^T (n x k), all device; the residuals are formed in FP32 and
  * their squares summed in FP64. Synchronises `stream`; writes *f_out (host). */
@@ -181,6 +195,11 @@ typedef enum nmf_input_kind { NMF_INPUT_DENSE = 0, NMF_INPUT_CSR = 1 } nmf_input
  * (warm). Either way the solution is the same unique minimiser. */
 typedef enum nmf_start_mode { NMF_START_COLD = 0, NMF_START_WARM = 1 } nmf_start_mode;
 
+/* Local update of each half-step: the exact NLS solve by BPP (Sec. 4.2, the
+ * paper's method), or one step of the alternatives the paper names for the
+ * same inputs, MU (Eq. 5) or HALS (Eq. 6). */
+typedef enum nmf_solver { NMF_SOLVER_BPP = 0, NMF_SOLVER_MU = 1, NMF_SOLVER_HALS = 2 } nmf_solver;
+
 typedef struct nmf_config {
     int64_t m, n;              /* A is m x n */
     int32_t k;                 /* rank, 1..NMF_MAX_K */
@@ -192,6 +211,7 @@ typedef struct nmf_config {
     int32_t max_bpp_rounds;    /* per-RHS exchange cap (e.g. 100) */
     int32_t objective_every;   /* 1: f after every iteration (history kept);
                                   0: only on nmf_objective() */
+    int32_t solver;            /* nmf_solver (0, BPP, when zero-initialised) */
 } nmf_config;
 
 /* The input matrix. Its device buffers are BORROWED: the caller keeps them

@@ -44,6 +44,11 @@ NMF_MAX_K = 128
 NMF_PROPOSAL_OFF = 0
 NMF_PROPOSAL_TRAIN = 1
 NMF_PROPOSAL_USE = 2
+NMF_SOLVER_BPP = 0
+NMF_SOLVER_MU = 1
+NMF_SOLVER_HALS = 2
+
+SOLVERS = {"bpp": NMF_SOLVER_BPP, "mu": NMF_SOLVER_MU, "hals": NMF_SOLVER_HALS}
 
 PRECISIONS = {"fp32": NMF_PREC_FP32, "bf16x3": NMF_PREC_BF16X3}
 
@@ -68,7 +73,7 @@ class nmf_nls_desc(ctypes.Structure):
 class nmf_config(ctypes.Structure):
     _fields_ = [("m", _I64), ("n", _I64), ("k", _I32), ("input_kind", _I32),
                 ("precision", _I32), ("start_mode", _I32), ("max_bpp_rounds", _I32),
-                ("objective_every", _I32)]
+                ("objective_every", _I32), ("solver", _I32)]
 
 
 class nmf_matrix(ctypes.Structure):
@@ -96,6 +101,8 @@ def _sig(name, args, res=ctypes.c_int):
 _lib.nmf_status_str.argtypes = [ctypes.c_int]
 _lib.nmf_status_str.restype = ctypes.c_char_p
 _c_gram = _sig("nmf_gram", [_P, _I64, _I32, _P, _P])
+_c_update_mu = _sig("nmf_update_mu", [_I32, _I64, _P, _P, _P, _P])
+_c_update_hals = _sig("nmf_update_hals", [_I32, _I64, _P, _P, _P, _P])
 _c_mm_dense = _sig("nmf_mm_dense", [_P, _I64, _I64, _I64, _P, _I32, _I32, _I32, _P, _P])
 _c_mm_csr = _sig("nmf_mm_csr", [_P, _P, _P, _I64, _I64, _P, _I32, _P, _P])
 _c_csr_transpose = _sig("nmf_csr_transpose", [_P, _P, _P, _I64, _I64, _I64, _P, _P, _P, _P])
@@ -138,7 +145,7 @@ EXPORTED = ["nmf_status_str", "nmf_gram", "nmf_mm_dense", "nmf_mm_csr", "nmf_csr
             "nmf_get_passive", "nmf_get_stats", "nmf_set_timing", "nmf_set_graph", "nmf_destroy",
             "nmf_mlp_param_count", "nmf_mlp_create", "nmf_mlp_get_params", "nmf_mlp_destroy",
             "nmf_mlp_features", "nmf_mlp_forward", "nmf_mlp_propose", "nmf_mlp_gradient",
-            "nmf_mlp_train", "nmf_set_proposal"]
+            "nmf_mlp_train", "nmf_set_proposal", "nmf_update_mu", "nmf_update_hals"]
 
 
 def nmf_status_str(status: int) -> str:
@@ -181,6 +188,29 @@ def nmf_gram(X: torch.Tensor, stream=None) -> torch.Tensor:
     G = torch.empty((k, k), dtype=torch.float64, device=X.device)
     _check(_c_gram(_ptr(X), rows, k, _ptr(G), _stream(stream)), "nmf_gram")
     return G
+
+
+def _local_update(fn, name, G, R, X, stream):
+    _dev(G, torch.float64, "G")
+    _dev(R, torch.float32, "R")
+    _dev(X, torch.float32, "X")
+    rows, k = X.shape
+    if tuple(G.shape) != (k, k) or tuple(R.shape) != (rows, k):
+        raise ValueError("G must be k x k and R rows x k")
+    _check(fn(k, rows, _ptr(G), _ptr(R), _ptr(X), _stream(stream)), name)
+    return X
+
+
+def nmf_update_mu(G: torch.Tensor, R: torch.Tensor, X: torch.Tensor, stream=None) -> torch.Tensor:
+    """One MU step (Eq. 5) of the rows of X (rows x k float32, updated in place)
+    with Gram G (k x k float64) and right-hand sides R (rows x k float32)."""
+    return _local_update(_c_update_mu, "nmf_update_mu", G, R, X, stream)
+
+
+def nmf_update_hals(G: torch.Tensor, R: torch.Tensor, X: torch.Tensor,
+                    stream=None) -> torch.Tensor:
+    """One HALS sweep (Eq. 6) of the rows of X in place; arguments as nmf_update_mu."""
+    return _local_update(_c_update_hals, "nmf_update_hals", G, R, X, stream)
 
 
 def nmf_mm_dense(A: torch.Tensor, F: torch.Tensor, trans: bool, precision="fp32",
@@ -314,7 +344,7 @@ class nmf_init:
 
     def __init__(self, A, W0: torch.Tensor, Ht0: torch.Tensor, precision="fp32",
                  start="cold", max_bpp_rounds: int = 100, objective_every: bool = True,
-                 shape=None, stream=None):
+                 shape=None, stream=None, solver="bpp"):
         _dev(W0, torch.float32, "W0")
         _dev(Ht0, torch.float32, "Ht0")
         m, k = W0.shape
@@ -343,7 +373,7 @@ class nmf_init:
         self.device = W0.device
         cfg = nmf_config(m, n, k, kind, _prec(precision),
                          NMF_START_WARM if start == "warm" else NMF_START_COLD,
-                         max_bpp_rounds, int(bool(objective_every)))
+                         max_bpp_rounds, int(bool(objective_every)), SOLVERS[solver])
         self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
         h = _P()
         _check(_c_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.byref(mat), _ptr(W0), _ptr(Ht0),

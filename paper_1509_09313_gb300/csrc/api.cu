@@ -364,15 +364,19 @@ nmf_status objective_into(nmf_handle *h, double *f_dev, bool after_h = false)
                                   h->obj_part, f_dev, h->stream);
 }
 
-// The BPP solves of one half-step: X (rows x k, the factor, updated in place)
-// from Gram G and right-hand sides R; passive = that factor's bitmasks. With
-// a network attached, its features are formed from the rows of X before the
-// update; it proposes the starting partition (use) or learns from the final
-// one (train).
+// The local update of one half-step: X (rows x k, the factor, updated in
+// place) from Gram G and right-hand sides R. BPP: passive = that factor's
+// bitmasks; with a network attached, its features are formed from the rows of
+// X before the update; it proposes the starting partition (use) or learns from
+// the final one (train). MU and HALS: one step of Eq. 5 or Eq. 6.
 nmf_status solve_half(nmf_handle *h, int64_t rows, const double *G, const float *R, float *X,
                       uint64_t *passive, bool warm)
 {
     const nmf_config &c = h->cfg;
+    if (c.solver != NMF_SOLVER_BPP) {
+        PhaseTimer t(h, 2);
+        return launch_local_update(c.solver, G, c.k, R, X, rows, h->stream);
+    }
     const bool use = h->mlp && h->prop_mode == NMF_PROPOSAL_USE;
     const bool train = h->mlp && h->prop_mode == NMF_PROPOSAL_TRAIN;
     if (use || train) {
@@ -410,7 +414,8 @@ nmf_status one_iteration(nmf_handle *h)
         NMF_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
         PhaseTimer t(h, 0, h->side);
         NMF_TRY(launch_gram(F, rows, c.k, G, h->gram_part, h->side));
-        NMF_TRY(launch_bpp_prep(c.k, G, h->bpp_work, h->stats_dev, h->side));
+        if (c.solver == NMF_SOLVER_BPP)
+            NMF_TRY(launch_bpp_prep(c.k, G, h->bpp_work, h->stats_dev, h->side));
         NMF_CUDA(cudaEventRecord(h->ev_join, h->side));
         return NMF_OK;
     };
@@ -519,6 +524,8 @@ extern "C" nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nm
     if (c.precision != NMF_PREC_FP32 && c.precision != NMF_PREC_BF16X3)
         return NMF_ERR_INVALID_ARG;
     if (c.start_mode != NMF_START_COLD && c.start_mode != NMF_START_WARM)
+        return NMF_ERR_INVALID_ARG;
+    if (c.solver != NMF_SOLVER_BPP && c.solver != NMF_SOLVER_MU && c.solver != NMF_SOLVER_HALS)
         return NMF_ERR_INVALID_ARG;
     if (c.input_kind == NMF_INPUT_DENSE) {
         if (!A->dense || A->lda < c.n)
@@ -922,8 +929,9 @@ extern "C" nmf_status nmf_set_proposal(nmf_handle *h, nmf_mlp *mlp, int32_t mode
         h->prop_mode = NMF_PROPOSAL_OFF;
         return NMF_OK;
     }
-    if (mlp_k(mlp->net) != h->cfg.k || epochs < 0 || batch < 1 || batch > INT32_MAX ||
-        !(lr > 0.0f))
+    // The network proposes BPP starting partitions: no meaning for MU or HALS.
+    if (h->cfg.solver != NMF_SOLVER_BPP || mlp_k(mlp->net) != h->cfg.k || epochs < 0 ||
+        batch < 1 || batch > INT32_MAX || !(lr > 0.0f))
         return NMF_ERR_INVALID_ARG;
     if (!h->feat) {
         const int64_t rows = h->cfg.m > h->cfg.n ? h->cfg.m : h->cfg.n;

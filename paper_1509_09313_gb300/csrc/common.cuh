@@ -97,6 +97,10 @@ nmf_status launch_objective_csr(const float *Ht, const float *Y, int64_t n, int 
 nmf_status launch_sq_norm(const float *v, int64_t len, double *partials, double *out,
                           cudaStream_t s);
 
+// MU (Eq. 5) or HALS (Eq. 6) step of the rows of X in place (local_update.cu).
+nmf_status launch_local_update(int solver, const double *G, int k, const float *R, float *X,
+                               int64_t rows, cudaStream_t s);
+
 // Batched BPP. Workspace layout is private to bpp.cu; size from bpp_work_bytes.
 size_t bpp_work_bytes(int k);
 struct BppStats {
