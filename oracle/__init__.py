@@ -70,6 +70,8 @@ class Oracle:
         lib.oracle_bpp.restype = I
         lib.oracle_anls.argtypes = [I, P, I64, P, P, P, I64, I64, I, P, P, I, I, I, P, P, P, P, I]
         lib.oracle_mu.argtypes = [P, I, P, I64, P]
+        lib.oracle_pgrad_sq.argtypes = [P, I, P, I64, P]
+        lib.oracle_pgrad_sq.restype = ctypes.c_double
         lib.oracle_hals.argtypes = [P, I, P, I64, P]
         lib.oracle_anls.restype = I
         self.lib = lib
@@ -149,6 +151,24 @@ class Oracle:
         X = _f64(X).copy()
         self.lib.oracle_mu(_p(G), G.shape[0], _p(R), X.shape[0], _p(X))
         return X
+
+    def pgrad_sq(self, G, R, X) -> float:
+        """Squared projected-gradient norm of the rows of X: grad = X G - R,
+        entries with x = 0 count only where grad < 0."""
+        G, R, X = _f64(G), _f64(R), _f64(X)
+        return self.lib.oracle_pgrad_sq(_p(G), G.shape[0], _p(R), X.shape[0], _p(X))
+
+    def pgrad(self, W, Ht, A=None, csr=None, shape=None) -> float:
+        """Projected-gradient norm of f at (W, H) (half the gradient of Eq. 1):
+        sqrt(|P[W H H^T - A H^T]|^2 + |P[H^T W^T W - A^T W]|^2)."""
+        W, Ht = _f64(W), _f64(Ht)
+        if csr is None:
+            V, Y = self.mm_dense(A, Ht, False), self.mm_dense(A, W, True)
+        else:
+            m, n = shape
+            V = self.mm_csr(*csr, m, n, Ht, False)
+            Y = self.mm_csr(*csr, m, n, W, True)
+        return float(np.sqrt(self.pgrad_sq(self.gram(Ht), V, W) + self.pgrad_sq(self.gram(W), Y, Ht)))
 
     def hals(self, G, R, X) -> np.ndarray:
         """One HALS sweep (Eq. 6) of the rows of X; returns the new X."""
@@ -235,6 +255,14 @@ def mu(G, R, X):
 
 def hals(G, R, X):
     return default().hals(G, R, X)
+
+
+def pgrad_sq(G, R, X):
+    return default().pgrad_sq(G, R, X)
+
+
+def pgrad(W, Ht, A=None, csr=None, shape=None):
+    return default().pgrad(W, Ht, A, csr, shape)
 
 
 def anls(A=None, W0=None, Ht0=None, iters=10, warm=False, max_rounds=1000, csr=None, shape=None,

@@ -403,6 +403,30 @@ void oracle_hals(const double *G, int k, const double *R, int64_t rows, double *
     }
 }
 
+/* Squared norm of the projected gradient of f with respect to the rows of X
+ * (the stopping measure of Lin 2007, used for ANLS by Kim and Park): with
+ * grad = X G - R (half the gradient of Eq. 1 in X when G and R are the other
+ * factor's Gram and right-hand sides), each entry counts as grad_ij where
+ * x_ij > 0 and as min(0, grad_ij) where x_ij = 0. */
+double oracle_pgrad_sq(const double *G, int k, const double *R, int64_t rows, const double *X)
+{
+    double total = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : total)
+    for (int64_t r = 0; r < rows; ++r) {
+        const double *x = X + r * k;
+        double row = 0.0;
+        for (int j = 0; j < k; ++j) {
+            double gj = -R[r * k + j];
+            for (int l = 0; l < k; ++l)
+                gj += x[l] * G[l * k + j];
+            const double pj = x[j] > 0.0 ? gj : (gj < 0.0 ? gj : 0.0);
+            row += pj * pj;
+        }
+        total += row;
+    }
+    return total;
+}
+
 /* One local update of X from (G, R) by the chosen method: 0 BPP (x = the exact
  * NLS minimiser), 1 MU, 2 HALS. */
 static int local_update(int solver, const double *G, int k, const double *R, int64_t rows,

@@ -325,5 +325,49 @@ def pin_anls_local(orc, seed=19):
     assert (r["W"][::7, 2] == 0).all()
 
 
+def pin_pgrad(orc, seed=23):
+    """Projected-gradient norm (Lin 2007). Hand-worked: G = [[2, 1], [1, 2]],
+    R = (3, 3), x = (1, 0): x G - R = (-1, -2), both count (x_1 > 0; the second
+    is negative): 1 + 4 = 5; with R = (3, 0) the gradient is (-1, 1) and the
+    positive entry at x_2 = 0 is dropped: 1. The full measure equals half the
+    finite-difference gradient of f = ||A - W H||^2 where it is unconstrained
+    (all entries positive), vanishes in H after an exact H half-step (Eq. 4)
+    and at an exact planted factorisation."""
+    G = np.array([[2.0, 1.0], [1.0, 2.0]])
+    assert abs(orc.pgrad_sq(G, np.array([[3.0, 3.0]]), np.array([[1.0, 0.0]])) - 5.0) < 1e-15
+    assert abs(orc.pgrad_sq(G, np.array([[3.0, 0.0]]), np.array([[1.0, 0.0]])) - 1.0) < 1e-15
+    rng = np.random.default_rng(seed)
+    m, n, k = 9, 7, 3
+    A = rng.uniform(0, 1, (m, n)).astype(np.float32)
+    W = rng.uniform(0.5, 1.5, (m, k))
+    Ht = rng.uniform(0.5, 1.5, (n, k))
+    Ad = A.astype(np.float64)
+    f = lambda W_, Ht_: np.sum((Ad - W_ @ Ht_.T) ** 2)
+    gW = np.zeros_like(W)
+    gH = np.zeros_like(Ht)
+    h = 1e-6
+    for idx in np.ndindex(W.shape):
+        E = np.zeros_like(W)
+        E[idx] = h
+        gW[idx] = (f(W + E, Ht) - f(W - E, Ht)) / (2 * h)
+    for idx in np.ndindex(Ht.shape):
+        E = np.zeros_like(Ht)
+        E[idx] = h
+        gH[idx] = (f(W, Ht + E) - f(W, Ht - E)) / (2 * h)
+    expect = 0.5 * np.sqrt(np.sum(gW ** 2) + np.sum(gH ** 2))
+    np.testing.assert_allclose(orc.pgrad(W, Ht, A), expect, rtol=1e-6)
+    m, n, k = 60, 40, 4
+    A = synth.dense_planted(m, n, k, 0.05, seed=seed)
+    W0, Ht0 = synth.init_factors(m, n, k, seed=seed)
+    r = orc.anls(A, W0, Ht0, iters=2)
+    pH = orc.pgrad_sq(orc.gram(r["W"]), orc.mm_dense(A, r["W"], True), r["Ht"])
+    total = orc.pgrad(r["W"], r["Ht"], A)
+    assert pH <= 1e-18 * max(total ** 2, 1e-300) + 1e-20, (pH, total)
+    Wp = rng.uniform(0, 1, (m, k))
+    Hp = rng.uniform(0, 1, (n, k)) * (rng.uniform(0, 1, (n, k)) > 0.3)
+    Ap = Wp @ Hp.T
+    assert orc.pgrad(Wp, Hp, Ap.astype(np.float32)) <= 1e-5 * np.linalg.norm(Ap)
+
+
 ALL_PINS = [pin_golden, pin_bruteforce, pin_nnls, pin_closed_forms, pin_kkt_and_warm,
-            pin_products, pin_anls, pin_planted, pin_mu, pin_hals, pin_anls_local]
+            pin_products, pin_anls, pin_planted, pin_mu, pin_hals, pin_anls_local, pin_pgrad]

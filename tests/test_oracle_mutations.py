@@ -25,6 +25,8 @@ MUTANTS = {
     "mu_dropped_factor": ("x[j] = x[j] * R[r * k + j] / den[j];", "x[j] = R[r * k + j] / den[j];"),
     "mu_wrong_gram_index": ("d += x[l] * G[l * k + j];", "d += x[l] * G[l * k + l];"),
     "hals_dropped_new_values": ("num -= G[l * k + i] * x[l];", "num -= G[l * k + i] * (l < i ? 0.0 : x[l]);"),
+    "pgrad_projection_sign": ("const double pj = x[j] > 0.0 ? gj : (gj < 0.0 ? gj : 0.0);",
+                              "const double pj = x[j] > 0.0 ? gj : (gj > 0.0 ? gj : 0.0);"),
     "hals_no_projection": ("x[i] = (num > 0.0 ? num : 0.0) / gii;", "x[i] = num / gii;"),
 }
 
