@@ -175,6 +175,17 @@ nmf_status nmf_update_mu(int32_t k, int64_t rows, const double *G, const float *
 nmf_status nmf_update_hals(int32_t k, int64_t rows, const double *G, const float *R, float *X,
                            void *stream);
 
+/* Stopping measure for Alg. 1's "while not converged" (the paper leaves the
+ * test open; this is the projected-gradient norm of Lin 2007, used for ANLS by
+ * Kim and Park), with half the gradient of Eq. 1:
+ *   Delta(W, H) = sqrt(|P[W H H^T - A H^T]|_F^2 + |P[H^T W^T W - A^T W]|_F^2),
+ * P[g]_ij = g_ij where the factor entry is > 0 and min(g_ij, 0) where it is 0.
+ * This call: *out = |P[X G - R]|_F^2 for rows of X (rows x k float32) with
+ * G (k x k float64) and R (rows x k float32), all device; *out is host.
+ * Synchronises `stream`. */
+nmf_status nmf_pgrad_sq(int32_t k, int64_t rows, const double *G, const float *R, const float *X,
+                        double *out, void *stream);
+
 /* Objective of Eq. 1 for dense A: f = sum_ij (A_ij - w_i . h_j)^2 with W
  * (m x k) and H^T (n x k), all device; the residuals are formed in FP32 and
  * their squares summed in FP64. Synchronises `stream`; writes *f_out (host). */
@@ -288,6 +299,27 @@ nmf_status nmf_set_timing(nmf_handle *h, int32_t timing);
  * and launches that (fewer launch gaps for small problems). Calls on the
  * legacy default stream or with timing on run eagerly instead. */
 nmf_status nmf_set_graph(nmf_handle *h, int32_t on);
+
+/* Record Delta (see nmf_pgrad_sq) of every iterate from the current one on
+ * (on = 1) or stop recording (0). The part in H is formed at the end of each H
+ * half-step and the part in W in the next iteration's W half-step (its Gram
+ * and right-hand sides are the iterate's), so Delta of iterate t is complete
+ * once iteration t + 1 has run. Turning it on costs one product (A^T W of the
+ * current iterate); nmf_set_factors turns it off. */
+nmf_status nmf_set_pgrad(nmf_handle *h, int32_t on);
+
+/* Delta of the recorded iterates whose value is complete, oldest first (at
+ * most `cap`, host buffer); *count = values written. Synchronises. */
+nmf_status nmf_pgrad_history(nmf_handle *h, double *out, int64_t cap, int64_t *count);
+
+/* Iterate until Delta(t) <= rel_tol * Delta(t0), t0 the first recorded
+ * iterate (the current one if recording was off), or max_iters iterations.
+ * Delta(t) is known after iteration t + 1, so the handle ends one iteration
+ * past the first iterate that meets the test. One host synchronisation per
+ * iteration. *iters_done (nullable): iterations run; *ratio (nullable):
+ * Delta / Delta(t0) of the last complete iterate. */
+nmf_status nmf_iterate_until(nmf_handle *h, int32_t max_iters, double rel_tol,
+                             int32_t *iters_done, double *ratio);
 
 /* Release everything the handle owns. NULL is ignored. */
 void nmf_destroy(nmf_handle *h);

@@ -103,6 +103,11 @@ _lib.nmf_status_str.restype = ctypes.c_char_p
 _c_gram = _sig("nmf_gram", [_P, _I64, _I32, _P, _P])
 _c_update_mu = _sig("nmf_update_mu", [_I32, _I64, _P, _P, _P, _P])
 _c_update_hals = _sig("nmf_update_hals", [_I32, _I64, _P, _P, _P, _P])
+_c_pgrad_sq = _sig("nmf_pgrad_sq", [_I32, _I64, _P, _P, _P, ctypes.POINTER(ctypes.c_double), _P])
+_c_set_pgrad = _sig("nmf_set_pgrad", [_P, _I32])
+_c_pgrad_history = _sig("nmf_pgrad_history", [_P, _P, _I64, ctypes.POINTER(_I64)])
+_c_iterate_until = _sig("nmf_iterate_until", [_P, _I32, ctypes.c_double, ctypes.POINTER(_I32),
+                                              ctypes.POINTER(ctypes.c_double)])
 _c_mm_dense = _sig("nmf_mm_dense", [_P, _I64, _I64, _I64, _P, _I32, _I32, _I32, _P, _P])
 _c_mm_csr = _sig("nmf_mm_csr", [_P, _P, _P, _I64, _I64, _P, _I32, _P, _P])
 _c_csr_transpose = _sig("nmf_csr_transpose", [_P, _P, _P, _I64, _I64, _I64, _P, _P, _P, _P])
@@ -145,7 +150,8 @@ EXPORTED = ["nmf_status_str", "nmf_gram", "nmf_mm_dense", "nmf_mm_csr", "nmf_csr
             "nmf_get_passive", "nmf_get_stats", "nmf_set_timing", "nmf_set_graph", "nmf_destroy",
             "nmf_mlp_param_count", "nmf_mlp_create", "nmf_mlp_get_params", "nmf_mlp_destroy",
             "nmf_mlp_features", "nmf_mlp_forward", "nmf_mlp_propose", "nmf_mlp_gradient",
-            "nmf_mlp_train", "nmf_set_proposal", "nmf_update_mu", "nmf_update_hals"]
+            "nmf_mlp_train", "nmf_set_proposal", "nmf_update_mu", "nmf_update_hals",
+            "nmf_pgrad_sq", "nmf_set_pgrad", "nmf_pgrad_history", "nmf_iterate_until"]
 
 
 def nmf_status_str(status: int) -> str:
@@ -211,6 +217,21 @@ def nmf_update_hals(G: torch.Tensor, R: torch.Tensor, X: torch.Tensor,
                     stream=None) -> torch.Tensor:
     """One HALS sweep (Eq. 6) of the rows of X in place; arguments as nmf_update_mu."""
     return _local_update(_c_update_hals, "nmf_update_hals", G, R, X, stream)
+
+
+def nmf_pgrad_sq(G: torch.Tensor, R: torch.Tensor, X: torch.Tensor, stream=None) -> float:
+    """|P[X G - R]|_F^2: the squared projected-gradient norm of the rows of X
+    (entries with x = 0 count only where the gradient is negative)."""
+    _dev(G, torch.float64, "G")
+    _dev(R, torch.float32, "R")
+    _dev(X, torch.float32, "X")
+    rows, k = X.shape
+    if tuple(G.shape) != (k, k) or tuple(R.shape) != (rows, k):
+        raise ValueError("G must be k x k and R rows x k")
+    out = ctypes.c_double(0.0)
+    _check(_c_pgrad_sq(k, rows, _ptr(G), _ptr(R), _ptr(X), ctypes.byref(out), _stream(stream)),
+           "nmf_pgrad_sq")
+    return out.value
 
 
 def nmf_mm_dense(A: torch.Tensor, F: torch.Tensor, trans: bool, precision="fp32",
@@ -393,6 +414,24 @@ class nmf_init:
         f = ctypes.c_double(0.0)
         _check(_c_objective(self._h, ctypes.byref(f)), "nmf_objective")
         return f.value
+
+    def nmf_set_pgrad(self, on: bool = True) -> None:
+        _check(_c_set_pgrad(self._h, int(bool(on))), "nmf_set_pgrad")
+
+    def nmf_pgrad_history(self, cap: int = 1 << 16):
+        buf = (ctypes.c_double * cap)()
+        cnt = _I64(0)
+        _check(_c_pgrad_history(self._h, ctypes.cast(buf, _P), cap, ctypes.byref(cnt)),
+               "nmf_pgrad_history")
+        return list(buf[:cnt.value])
+
+    def nmf_iterate_until(self, max_iters: int, rel_tol: float):
+        """Returns (iterations run, Delta / Delta(t0) of the last complete iterate)."""
+        done = _I32(0)
+        ratio = ctypes.c_double(0.0)
+        _check(_c_iterate_until(self._h, max_iters, rel_tol, ctypes.byref(done),
+                                ctypes.byref(ratio)), "nmf_iterate_until")
+        return done.value, ratio.value
 
     def nmf_objective_history(self, cap: int = 1 << 16):
         buf = (ctypes.c_double * cap)()

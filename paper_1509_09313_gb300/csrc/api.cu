@@ -3,6 +3,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <math.h>
+
 #include <mutex>
 #include <vector>
 
@@ -237,6 +239,8 @@ struct nmf_handle {
     double *a_sq = nullptr;                     // ||A||^2 (sparse input)
     double *f_hist = nullptr;                   // ring of objective values
     double *f_now = nullptr;
+    double *pgw2 = nullptr, *pgh2 = nullptr;    // rings: squared projected gradient in W, in H
+    double *pg_part = nullptr;
     void *tc_work = nullptr;
     size_t tc_work_bytes = 0;
     int64_t *t_rowptr = nullptr;                // CSR of A^T (sparse input)
@@ -248,6 +252,8 @@ struct nmf_handle {
     bool obj_pending = false;      // f of the last iteration not yet computed
     int64_t f_count = 0;
     int64_t iterations = 0;
+    bool pg_on = false;                         // projected gradient recorded per iterate
+    int64_t pg_base = 0;                        // first recorded iterate
     BppStats reported{};                        // stats already turned into a status
     bool timing = false;
     bool use_graph = false;                     // nmf_iterate captures a CUDA graph
@@ -434,6 +440,11 @@ nmf_status one_iteration(nmf_handle *h)
         }
     }
     NMF_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+    // Stopping measure of the current iterate (W, H), its part in W: this
+    // half-step's Gram and right-hand sides are the iterate's own.
+    if (h->pg_on)
+        NMF_TRY(launch_pgrad_sq(h->GH, c.k, h->V, h->W, c.m, h->pg_part,
+                                h->pgw2 + (h->iterations % F_HIST_CAP), h->stream));
     NMF_TRY(solve_half(h, c.m, h->GH, h->V, h->W, h->pW, warm));
     // H <- argmin_{H >= 0} ||A - W H||: Gram W^T W, right-hand sides (W^T A)^T.
     NMF_TRY(fork_prepare(h->W, c.m, h->GW));
@@ -443,6 +454,10 @@ nmf_status one_iteration(nmf_handle *h)
     }
     NMF_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     NMF_TRY(solve_half(h, c.n, h->GW, h->Y, h->Ht, h->pH, warm));
+    // ... and the new iterate's part in H (W^T W and A^T W of the new W).
+    if (h->pg_on)
+        NMF_TRY(launch_pgrad_sq(h->GW, c.k, h->Y, h->Ht, c.n, h->pg_part,
+                                h->pgh2 + ((h->iterations + 1) % F_HIST_CAP), h->stream));
     h->passive_valid = true;
     if (c.objective_every) {
         if (h->fused_obj) {
@@ -485,6 +500,9 @@ void free_handle(nmf_handle *h)
     cudaFree(h->stats_dev);
     cudaFree(h->gram_part);
     cudaFree(h->obj_part);
+    cudaFree(h->pgw2);
+    cudaFree(h->pgh2);
+    cudaFree(h->pg_part);
     cudaFree(h->a_sq);
     cudaFree(h->f_hist);
     cudaFree(h->f_now);
@@ -578,6 +596,9 @@ extern "C" nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nm
     chk(dalloc(&h->obj_part, (size_t)objective_partials_len()));
     chk(dalloc(&h->f_hist, (size_t)F_HIST_CAP));
     chk(dalloc(&h->f_now, 1));
+    chk(dalloc(&h->pgw2, (size_t)F_HIST_CAP));
+    chk(dalloc(&h->pgh2, (size_t)F_HIST_CAP));
+    chk(dalloc(&h->pg_part, (size_t)pgrad_partials_len()));
     h->fused_obj = c.input_kind == NMF_INPUT_DENSE && c.precision == NMF_PREC_BF16X3 && c.k <= 64;
     if (e == cudaSuccess && c.input_kind == NMF_INPUT_DENSE && c.precision == NMF_PREC_BF16X3) {
         h->tc_work_bytes = mm_tc_work_bytes(c.m, c.n, c.k, 0);
@@ -773,7 +794,114 @@ extern "C" nmf_status nmf_set_factors(nmf_handle *h, const float *W, const float
         NMF_CUDA(cudaMemcpyAsync(h->Ht, Ht, sizeof(float) * (size_t)h->cfg.n * k,
                                  cudaMemcpyDeviceToDevice, h->stream));
     h->passive_valid = false;
+    h->pg_on = false;   // the recorded measures belong to the replaced iterates
     return NMF_OK;
+}
+
+extern "C" nmf_status nmf_set_pgrad(nmf_handle *h, int32_t on)
+{
+    if (!h)
+        return NMF_ERR_INVALID_ARG;
+    if (!on) {
+        h->pg_on = false;
+        return NMF_OK;
+    }
+    if (h->pg_on)
+        return NMF_OK;
+    const nmf_config &c = h->cfg;
+    // The current iterate's part in H needs A^T W and W^T W of the current W
+    // (the iteration forms them only for the next W).
+    const unsigned long long before = launch_count;
+    nmf_status st = mm(h, 1, h->W, h->Y);
+    if (st == NMF_OK)
+        st = launch_gram(h->W, c.m, c.k, h->GW, h->gram_part, h->stream);
+    if (st == NMF_OK)
+        st = launch_pgrad_sq(h->GW, c.k, h->Y, h->Ht, c.n, h->pg_part,
+                             h->pgh2 + (h->iterations % F_HIST_CAP), h->stream);
+    h->launches += (int64_t)(launch_count - before);
+    NMF_TRY(st);
+    h->pg_on = true;
+    h->pg_base = h->iterations;
+    return NMF_OK;
+}
+
+// Delta of recorded iterate t (complete once iteration t + 1 has run).
+static nmf_status pgrad_of(nmf_handle *h, int64_t t, double *out)
+{
+    double w2 = 0.0, h2 = 0.0;
+    const int64_t slot = t % F_HIST_CAP;
+    NMF_CUDA(cudaMemcpyAsync(&w2, h->pgw2 + slot, sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream));
+    NMF_CUDA(cudaMemcpyAsync(&h2, h->pgh2 + slot, sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream));
+    NMF_CUDA(cudaStreamSynchronize(h->stream));
+    *out = sqrt(w2 + h2);
+    return NMF_OK;
+}
+
+extern "C" nmf_status nmf_pgrad_history(nmf_handle *h, double *out, int64_t cap, int64_t *count)
+{
+    if (!h || !count || cap < 0 || (cap > 0 && !out))
+        return NMF_ERR_INVALID_ARG;
+    *count = 0;
+    if (!h->pg_on)
+        return NMF_OK;
+    int64_t avail = h->iterations - h->pg_base;   // complete iterates
+    if (avail > F_HIST_CAP)
+        avail = F_HIST_CAP;
+    const int64_t nout = avail < cap ? avail : cap;
+    const int64_t first = h->iterations - nout;
+    for (int64_t q = 0; q < nout; ++q)
+        NMF_TRY(pgrad_of(h, first + q, out + q));
+    *count = nout;
+    return NMF_OK;
+}
+
+extern "C" nmf_status nmf_iterate_until(nmf_handle *h, int32_t max_iters, double rel_tol,
+                                        int32_t *iters_done, double *ratio)
+{
+    if (!h || max_iters < 0 || !(rel_tol >= 0.0))
+        return NMF_ERR_INVALID_ARG;
+    if (iters_done)
+        *iters_done = 0;
+    if (ratio)
+        *ratio = NAN;
+    NMF_TRY(nmf_set_pgrad(h, 1));
+    double d0 = -1.0;
+    for (int32_t done = 0; done < max_iters;) {
+        NMF_TRY(nmf_iterate(h, 1));
+        done += 1;
+        if (iters_done)
+            *iters_done = done;
+        if (d0 < 0.0)
+            NMF_TRY(pgrad_of(h, h->pg_base, &d0));
+        double dt = 0.0;
+        NMF_TRY(pgrad_of(h, h->iterations - 1, &dt));
+        if (ratio)
+            *ratio = d0 > 0.0 ? dt / d0 : 0.0;
+        if (dt <= rel_tol * d0)
+            break;
+    }
+    return NMF_OK;
+}
+
+extern "C" nmf_status nmf_pgrad_sq(int32_t k, int64_t rows, const double *G, const float *R,
+                                   const float *X, double *out, void *stream)
+{
+    if (bad_k(k) || rows < 0 || !G || !out || (rows > 0 && (!R || !X)))
+        return NMF_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    double *buf = nullptr;   // partials, then the sum
+    NMF_CUDA(cudaMallocAsync(&buf, sizeof(double) * (size_t)(pgrad_partials_len() + 1), s));
+    nmf_status st = launch_pgrad_sq(G, k, R, X, rows, buf, buf + pgrad_partials_len(), s);
+    if (st == NMF_OK &&
+        cudaMemcpyAsync(out, buf + pgrad_partials_len(), sizeof(double), cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess)
+        st = NMF_ERR_CUDA;
+    cudaFreeAsync(buf, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && st == NMF_OK)
+        st = NMF_ERR_CUDA;
+    return st;
 }
 
 extern "C" nmf_status nmf_get_passive(nmf_handle *h, uint64_t *pW, uint64_t *pH)

@@ -101,6 +101,13 @@ nmf_status launch_sq_norm(const float *v, int64_t len, double *partials, double 
 nmf_status launch_local_update(int solver, const double *G, int k, const float *R, float *X,
                                int64_t rows, cudaStream_t s);
 
+// *out = squared projected-gradient norm of the rows of X (grad = X G - R;
+// entries with x = 0 count only where grad < 0). `partials` holds
+// pgrad_partials_len() doubles.
+int pgrad_partials_len();
+nmf_status launch_pgrad_sq(const double *G, int k, const float *R, const float *X, int64_t rows,
+                           double *partials, double *out, cudaStream_t s);
+
 // Batched BPP. Workspace layout is private to bpp.cu; size from bpp_work_bytes.
 size_t bpp_work_bytes(int k);
 struct BppStats {
