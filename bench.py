@@ -264,6 +264,8 @@ def run_ours(args, rank, world, local_rank):
         net = nmf.nmf_mlp_create(k, MLP_HIDDEN, torch.from_numpy(synth.mlp_init(k, MLP_HIDDEN,
                                                                                seed=SEED)).to(dev))
         h.nmf_set_proposal(net, "train", epochs=1, batch=8192, lr=1e-3)
+    if args.pgrad:
+        h.nmf_set_pgrad(True)   # record the stopping measure of every iterate
     h.nmf_iterate(args.warmup)
     if learned:
         h.nmf_set_proposal(net, "use")
@@ -296,6 +298,10 @@ def run_ours(args, rank, world, local_rank):
     status = h.nmf_sync()
     st1 = h.nmf_get_stats()
     f_hist = h.nmf_objective_history()
+    pg_ratio = None
+    if args.pgrad:
+        pg = h.nmf_pgrad_history()
+        pg_ratio = pg[-1] / pg[0] if pg and pg[0] > 0 else None
     if world > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -434,6 +440,7 @@ def run_ours(args, rank, world, local_rank):
                         "status": nmf.nmf_status_str(status),
                         "warmup_status": nmf.nmf_status_str(warm_status)},
                 "objective_last": f_hist[-1] if f_hist else None,
+                "pgrad_ratio_last": pg_ratio,
                 "setup_s": {"generate": t_gen}}
         print(json.dumps(line), flush=True)
 
@@ -449,6 +456,8 @@ def main():
                     help="BPP starting partitions: empty, the previous iteration's, or the "
                          "proposal network's (trained during the warm-up iterations)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dense-large")
+    ap.add_argument("--pgrad", action="store_true",
+                    help="record the projected-gradient stopping measure in every iteration")
     ap.add_argument("--solver", choices=["bpp", "mu", "hals"], default="bpp",
                     help="local update: BPP (Sec. 4.2), MU (Eq. 5) or HALS (Eq. 6)")
     ap.add_argument("--max-rounds", type=int, default=100)
