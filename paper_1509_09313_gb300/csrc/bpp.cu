@@ -224,55 +224,61 @@ __global__ void __launch_bounds__(PREP_THREADS)
     }
 }
 
-// ---------------------------------------------------------------------------
-// Warp-cooperative Cholesky factorisation of a p x p SPD system S, where
-// S[a][b] = Src[idx[a] * ld + idx[b]] (left-looking, lane-per-row). Lw: p x LS
-// workspace receiving L (lower triangle), invd: p reciprocal pivots.
-// Returns false (uniformly across the warp) on a pivot <= tol * S_jj.
-// ---------------------------------------------------------------------------
-template <typename T, typename SrcT, int PT>
-__device__ bool warp_chol_factor(const SrcT *__restrict__ Src, int ld,
-                                 const int *__restrict__ idx, int p, T *__restrict__ Lw, int LS,
-                                 T *__restrict__ invd, T tol, int lane)
+// Row of entry e of a lower triangle stored row by row (e = a (a + 1) / 2 + b,
+// b <= a): the FP32 estimate of the root of a (a + 1) / 2 = e, corrected.
+__device__ __forceinline__ int tri_row(int e)
 {
+    int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    while (a * (a + 1) / 2 > e)
+        --a;
+    while ((a + 1) * (a + 2) / 2 <= e)
+        ++a;
+    return a;
+}
+
+// FP64 Cholesky of S_ab = Src[idx[a] * ld + idx[b]], right-looking: after
+// each pivot the trailing lower triangle is updated with its (a, b) entries
+// spread over the 32 lanes. Output: L in the lower triangle of Lw (row stride
+// LS), invd = 1 / L_jj; false, uniformly across the warp, on a pivot
+// <= tol * S_jj. The FP64 solves are bound by GB300's narrow FP64 pipe (two
+// lanes per clock per SM). The lane-per-row form gave step j to rows a >= j,
+// j FMAs each: p^2 / 2 warp FMA instructions with most lanes idle. The
+// trailing update takes about p^3 / 192 + p.
+__device__ bool warp_chol_factor_rl(const double *__restrict__ Src, int ld,
+                                    const int *__restrict__ idx, int p, double *__restrict__ Lw,
+                                    int LS, double *__restrict__ invd, double tol, int lane)
+{
+    for (int e = lane; e < p * (p + 1) / 2; e += 32) {
+        const int a = tri_row(e), b = e - a * (a + 1) / 2;
+        Lw[a * LS + b] = Src[idx[a] * ld + idx[b]];
+    }
+    __syncwarp();
     for (int j = 0; j < p; ++j) {
-        const int ij = idx[j];
-#pragma unroll
-        for (int t = 0; t < PT; ++t) {
-            const int i = lane + 32 * t;
-            if (i >= j && i < p) {
-                T s = (T)Src[idx[i] * ld + ij];
-                const T *li = Lw + i * LS;
-                const T *lj = Lw + j * LS;
-                for (int c = 0; c < j; ++c)
-                    s -= li[c] * lj[c];
-                Lw[i * LS + j] = s;
-            }
-        }
-        __syncwarp();
-        const T d = Lw[j * LS + j];
-        const T dorig = (T)Src[ij * ld + ij];
+        const double d = Lw[j * LS + j];
+        const double dorig = Src[idx[j] * ld + idx[j]];
         if (!(d > tol * dorig))
             return false;
-        const T l = sqrt(d);
-        const T inv = (T)1 / l;
+        const double l = sqrt(d);
+        const double inv = 1.0 / l;
+        for (int a = j + 1 + lane; a < p; a += 32)
+            Lw[a * LS + j] *= inv;
         __syncwarp();
-#pragma unroll
-        for (int t = 0; t < PT; ++t) {
-            const int i = lane + 32 * t;
-            if (i > j && i < p)
-                Lw[i * LS + j] *= inv;
-        }
         if (lane == 0) {
             Lw[j * LS + j] = l;
             invd[j] = inv;
+        }
+        const int t = p - j - 1;
+        for (int e = lane; e < t * (t + 1) / 2; e += 32) {
+            const int a = tri_row(e), b = e - a * (a + 1) / 2;
+            const int ra = j + 1 + a, rb = j + 1 + b;
+            Lw[ra * LS + rb] -= Lw[ra * LS + j] * Lw[rb * LS + j];
         }
         __syncwarp();
     }
     return true;
 }
 
-// Solve L L^T z = r with the factor from warp_chol_factor; row a of r / z in
+// Solve L L^T z = r with the factor from warp_chol_factor_rl; row a of r / z in
 // lane a % 32, slot a / 32 (shuffle-broadcast substitutions).
 template <typename T, int PT>
 __device__ void warp_chol_subst(int p, const T *__restrict__ Lw, int LS,
@@ -527,8 +533,8 @@ __global__ void __launch_bounds__(BPP_THREADS, 2)
                     const int p = pos;
                     __syncwarp();
                     if (p > 0) {
-                        if (!warp_chol_factor<T, T, PT>(comp ? Ms : Gs, k, widx, p, Lw, LS, invd,
-                                                        (T)PIVOT_TOL64, lane))
+                        if (!warp_chol_factor_rl(comp ? Ms : Gs, k, widx, p, Lw, LS, invd,
+                                                 PIVOT_TOL64, lane))
                             return NMF_ERR_SINGULAR_GRAM;
                         T r[PT];
 #pragma unroll
