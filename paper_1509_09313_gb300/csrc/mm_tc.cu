@@ -323,7 +323,9 @@ __device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_
 {
     const __nv_bfloat162 hb = __floats2bfloat162_rn(v0, v1);
     const float2 hf = __bfloat1622float2(hb);
-    const __nv_bfloat162 lb = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+    // v - hi for both halves in one packed FMA (v + (-1) hi: exact, as v - hi).
+    const float2 d = __ffma2_rn(hf, make_float2(-1.0f, -1.0f), make_float2(v0, v1));
+    const __nv_bfloat162 lb = __floats2bfloat162_rn(d.x, d.y);
     hi = *reinterpret_cast<const uint32_t *>(&hb);
     lo = *reinterpret_cast<const uint32_t *>(&lb);
 }
@@ -566,13 +568,23 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
                     }
                     if (OBJ) {
                         tmem_wait_ld();
-                        float q4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                        // Squared residuals in four chains (entries i mod 4),
+                        // two per packed FP32x2 FMA: e = a + (-1) wh, q += e e.
+                        float2 q01 = make_float2(0.0f, 0.0f), q23 = make_float2(0.0f, 0.0f);
+                        const float2 m1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const float e = a[i] - __uint_as_float(whr[i]);
-                            q4[i & 3] = fmaf(e, e, q4[i & 3]);
+                        for (int i = 0; i < 32; i += 4) {
+                            const float2 e01 = __ffma2_rn(
+                                make_float2(__uint_as_float(whr[i]), __uint_as_float(whr[i + 1])),
+                                m1, make_float2(a[i], a[i + 1]));
+                            const float2 e23 = __ffma2_rn(
+                                make_float2(__uint_as_float(whr[i + 2]),
+                                            __uint_as_float(whr[i + 3])),
+                                m1, make_float2(a[i + 2], a[i + 3]));
+                            q01 = __ffma2_rn(e01, e01, q01);
+                            q23 = __ffma2_rn(e23, e23, q23);
                         }
-                        const float y = ((q4[0] + q4[1]) + (q4[2] + q4[3])) - fc;
+                        const float y = ((q01.x + q01.y) + (q23.x + q23.y)) - fc;
                         const float t = fs + y;
                         fc = (t - fs) - y;
                         fs = t;
