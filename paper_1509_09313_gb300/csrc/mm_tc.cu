@@ -655,6 +655,7 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
         // only at the folds, so registers hold just the partial.
         constexpr int NH = N / 2;               // product columns owned by this warp
         constexpr int CH = NH < 8 ? NH : 8;     // columns per TMEM access
+        static_assert(CH % 2 == 0, "drain columns go in pairs");
         const int dw = warp - 6;
         const int quarter = warp & 3;           // TMEM lane quarter of this warp
         const int half = dw >> 2;               // which half of the columns
@@ -673,8 +674,14 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
                 tmem_ld<CH>(ta + (uint32_t)c0, v);
                 tmem_ld<CH>(ta + (uint32_t)(N + c0), w);
 #pragma unroll
-                for (int i = 0; i < CH; ++i)
-                    part[c0 + i] += v[i] + w[i];
+                for (int i = 0; i < CH; i += 2) {   // part += v + w, two columns per op
+                    const float2 vw =
+                        __fadd2_rn(make_float2(v[i], v[i + 1]), make_float2(w[i], w[i + 1]));
+                    const float2 pt =
+                        __fadd2_rn(make_float2(part[c0 + i], part[c0 + i + 1]), vw);
+                    part[c0 + i] = pt.x;
+                    part[c0 + i + 1] = pt.y;
+                }
             }
         };
         bool folded = false;
@@ -690,13 +697,20 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
                     for (int i = 0; i < CH; ++i)
                         sm[i] = cm[i] = 0.0f;
                 }
+                const float2 m1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
-                for (int i = 0; i < CH; ++i) {
-                    const float y = part[c0 + i] - cm[i];
-                    const float t = sm[i] + y;
-                    cm[i] = (t - sm[i]) - y;
-                    sm[i] = t;
+                for (int i = 0; i < CH; i += 2) {   // Kahan step, two columns per op
+                    const float2 s2 = make_float2(sm[i], sm[i + 1]);
+                    const float2 y = __ffma2_rn(make_float2(cm[i], cm[i + 1]), m1,
+                                                make_float2(part[c0 + i], part[c0 + i + 1]));
+                    const float2 t = __fadd2_rn(s2, y);
+                    const float2 c = __ffma2_rn(y, m1, __ffma2_rn(s2, m1, t));   // (t - s) - y
+                    cm[i] = c.x;
+                    cm[i + 1] = c.y;
+                    sm[i] = t.x;
+                    sm[i + 1] = t.y;
                     part[c0 + i] = 0.0f;
+                    part[c0 + i + 1] = 0.0f;
                 }
                 tmem_st<CH>(ks + (uint32_t)c0, sm);
                 tmem_st<CH>(kc + (uint32_t)c0, cm);
