@@ -68,8 +68,8 @@ FP32_LANES_PER_SM = 128
 MLP_HIDDEN = 256     # width of the proposal network (3k -> 256 -> 256 -> k)
 
 NCU_TRAFFIC = {
-    ("mm_tc_kernel", "dense-large", "bf16x3"): 24.83e9,
-    ("mm_tc_kernel", "dense-medium", "bf16x3"): 1.5516e9,
+    ("mm_tc_kernel", "dense-large", "bf16x3"): 24.81e9,
+    ("mm_tc_kernel", "dense-medium", "bf16x3"): 1.5616e9,
 }
 
 
