@@ -62,9 +62,10 @@ FP32_LANES_PER_SM = 128
 # ncu capture, keyed by (kernel, workload, precision); None until captured or
 # when the kernel changed since. dense-large: the two mm_tc_kernel launches of
 # an iteration captured on the 24000 x 16000 case (A H^T with the objective:
-# 1.5505 GB read + 7.1 MB written; A^T W: 1.5422 GB + 3.2 MB), scaled by the
-# element ratio 16 and averaged: 24.83 GB per launch against 24.61 GB of
-# algorithmic bytes (profiles/mm_tc_kernel_dense-medium.md).
+# 1.5505 GB read + 7.0 MB written; A^T W: 1.5464 GB + 19.2 MB in 6 splits),
+# reads scaled by the element ratio 16, writes by the rows (A H^T 96000 x 50
+# out; A^T W 3 splits of 64000 x 50 there), averaged: 24.81 GB per launch
+# against 24.61 GB of algorithmic bytes (profiles/mm_tc_kernel_dense-medium.md).
 MLP_HIDDEN = 256     # width of the proposal network (3k -> 256 -> 256 -> k)
 
 NCU_TRAFFIC = {
