@@ -243,6 +243,7 @@ struct nmf_handle {
     double *pg_part = nullptr;
     void *tc_work = nullptr;
     size_t tc_work_bytes = 0;
+    void *at_hi = nullptr, *at_lo = nullptr;   // A^T pre-split, tile-major (dense BF16x3)
     int64_t *t_rowptr = nullptr;                // CSR of A^T (sparse input)
     int32_t *t_colidx = nullptr;
     float *t_vals = nullptr;
@@ -342,9 +343,13 @@ nmf_status mm(nmf_handle *h, int trans, const float *F, float *out)
             return launch_spmm(h->A.rowptr, h->A.colidx, h->A.vals, c.m, F, c.k, out, h->stream);
         return launch_spmm(h->t_rowptr, h->t_colidx, h->t_vals, c.n, F, c.k, out, h->stream);
     }
-    if (c.precision == NMF_PREC_BF16X3)
+    if (c.precision == NMF_PREC_BF16X3) {
+        if (trans == 1 && h->at_hi)
+            return launch_mm_tc_presplit(h->at_hi, h->at_lo, c.m, c.n, F, c.k, out, h->tc_work,
+                                         h->tc_work_bytes, h->stream);
         return launch_mm_tc(h->A.dense, c.m, c.n, h->A.lda, F, c.k, trans, out, h->tc_work,
                             h->tc_work_bytes, h->stream);
+    }
     return launch_mm_simt(h->A.dense, c.m, c.n, h->A.lda, F, c.k, trans, out, h->stream);
 }
 
@@ -500,6 +505,8 @@ void free_handle(nmf_handle *h)
     cudaFree(h->stats_dev);
     cudaFree(h->gram_part);
     cudaFree(h->obj_part);
+    cudaFree(h->at_hi);
+    cudaFree(h->at_lo);
     cudaFree(h->pgw2);
     cudaFree(h->pgh2);
     cudaFree(h->pg_part);
@@ -606,6 +613,19 @@ extern "C" nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nm
         if (b1 > h->tc_work_bytes)
             h->tc_work_bytes = b1;
         chk(cudaMalloc(&h->tc_work, h->tc_work_bytes ? h->tc_work_bytes : 16));
+        // A^T split into BF16 hi / lo once (4 bytes per element of A): A^T W
+        // then needs no per-call transpose and split. Without the memory the
+        // handle splits A on the fly in every A^T W pass instead.
+        if (e == cudaSuccess) {
+            const size_t bytes = mm_tc_presplit_bytes(c.m, c.n);
+            if (cudaMalloc(&h->at_hi, bytes) != cudaSuccess ||
+                cudaMalloc(&h->at_lo, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                cudaFree(h->at_hi);
+                cudaFree(h->at_lo);
+                h->at_hi = h->at_lo = nullptr;
+            }
+        }
     }
     if (e == cudaSuccess && c.input_kind == NMF_INPUT_CSR) {
         chk(dalloc(&h->t_rowptr, (size_t)c.n + 1));
@@ -626,6 +646,9 @@ extern "C" nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nm
                                  cudaMemcpyDeviceToDevice, h->stream));
         NMF_CUDA(cudaMemcpyAsync(h->Ht, Ht0, sizeof(float) * (size_t)c.n * k,
                                  cudaMemcpyDeviceToDevice, h->stream));
+        if (h->at_hi)
+            NMF_TRY(launch_mm_tc_presplit_make(A->dense, c.m, c.n, A->lda, h->at_hi, h->at_lo,
+                                               h->stream));
         if (c.input_kind == NMF_INPUT_CSR) {
             unsigned long long *cursor = nullptr;
             NMF_CUDA(cudaMallocAsync(&cursor, sizeof(unsigned long long) * (size_t)c.n,

@@ -30,6 +30,7 @@
 //              of the row. trans = 1: the tile is transposed (thread = output
 //              row), so the four warps first read the whole tile into
 //              registers, meet at an mbarrier, then write hi and lo tiles.
+//              A pre-split transpose (TRANS = 2, below) leaves them idle.
 //   warps 6-13 drain the TMEM accumulators (tcgen05.ld) into registers; two
 //              warps per TMEM lane quarter, each owning half of the columns.
 //   warp 14    (objective only) issues the W H tile MMAs.
@@ -59,6 +60,17 @@
 // reading A again. A relative bias b of W H shifts f by about S b with
 // S = 2 mean(r) mean(WH) / mean(r^2) (|S| <= 4 on the dense workloads), far
 // inside the 1e-5 tolerance.
+//
+// Pre-split transpose (TRANS = 2): a handle on dense A keeps A^T split into
+// BF16 hi and lo copies (made once by mm_tc_presplit_kernel with the split
+// warps' arithmetic, +4 bytes per element of A), stored tile by tile: each
+// 128-row x 64-K operand tile is 16 contiguous KB already in the K-major
+// 128-byte-swizzled shared-memory layout, the K-blocks of a row block in
+// order. A^T W then reads 4 bytes per element as before, as one contiguous
+// stream per CTA fetched by plain bulk copies: no transpose, no split and
+// no in-place barrier per K-block, and bitwise the same products. (A
+// row-major n x m copy read through a tensor map was slower on tall A: its
+// 128 rows per tile lie m * 2 bytes apart.)
 //
 // F (H^T or W) is split once per call by mm_tc_split_kernel into a padded
 // N x Qp BF16 pair (the workspace); k > 64 is processed in 64-column chunks.
@@ -187,6 +199,16 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+// Untiled bulk copy global -> shared (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
+                                          uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
         : "memory");
 }
 
@@ -355,6 +377,9 @@ struct TcArgs {
     float *out;             // grid.y == 1: the output; else partials [split][P][k]
     double *obj_partials;   // per-CTA sums of squared residuals (OBJ)
     int *err;
+    // TRANS = 2: A^T pre-split, tile-major (see mm_tc_presplit_kernel).
+    const unsigned char *at_hi, *at_lo;
+    int64_t at_kbs;         // K-blocks per 128-row block of tiles
 };
 
 // -------------------------------------------------------------------- kernel
@@ -448,8 +473,17 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
                     // Two 128-byte-swizzled halves of 32 columns each.
                     tma_load_2d(dst, &tmA, q0, (int)p0, full(s));
                     tma_load_2d(dst + L::F32_BYTES / 2, &tmA, q0 + 32, (int)p0, full(s));
-                } else {
+                } else if (TRANS == 1) {
                     tma_load_2d(dst, &tmA, (int)p0, q0, full(s));
+                } else {
+                    // Pre-split A^T: each hi / lo tile is 16 contiguous KB in
+                    // global memory, already in the K-major swizzled operand
+                    // layout the split warps would write.
+                    const size_t toff =
+                        ((size_t)blockIdx.x * (size_t)args.at_kbs + (size_t)(kb0 + kb)) *
+                        (size_t)L::A_BYTES;
+                    bulk_load(dst, args.at_hi + toff, L::A_BYTES, full(s));
+                    bulk_load(dst + L::A_BYTES, args.at_lo + toff, L::A_BYTES, full(s));
                 }
                 tma_load_2d(dst + L::F32_BYTES, &tmBhi, q0, 0, full(s));
                 tma_load_2d(dst + L::F32_BYTES + L::B_BYTES, &tmBlo, q0, 0, full(s));
@@ -474,7 +508,7 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
                 const int s = kb % S, u = kb / S;
                 const int b = kb & 1, ub = kb >> 1;
                 if (!mbar_wait_fast(acc_empty(b), (ub & 1) ^ 1, abort) ||
-                    !mbar_wait_fast(a_full(s), u & 1, abort))
+                    !mbar_wait_fast(TRANS == 2 ? full(s) : a_full(s), u & 1, abort))
                     break;
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * 2 * N);
@@ -526,7 +560,7 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
                 mma_commit(empty(s));
             }
         }
-    } else if (warp >= 2 && warp < 6) {
+    } else if (TRANS != 2 && warp >= 2 && warp < 6) {
         // ---------------------------------------------------- split (warps 2-5)
         const int ct = threadIdx.x - 64;        // 0..127
         const int quarter = warp & 3;           // TMEM lane quarter of this warp
@@ -805,6 +839,40 @@ __global__ void mm_tc_split_kernel(const float *__restrict__ F, int64_t Q, int k
 // X (rows x k, float32 row-major, k <= 64) -> BF16 hi / lo rows of 64
 // (zero-padded columns and rows up to rows_p): the objective's K-major
 // operands W [i][r] and H^T [j][r].
+// A (m x n FP32, row stride lda) -> A^T split into BF16 hi / lo, hi = bf16(v),
+// lo = bf16(v - hi) exactly as split2, tile-major: element (row p = A's
+// column j, K index q = A's row i) of the Pp x Qp padded A^T lies in tile
+// (p / 128) * kbs + q / 64, at byte (p % 128) * 128 + ((q % 64 / 8) ^
+// (p % 8)) * 16 + (q % 8) * 2 of it (the SW128 K-major operand layout); the
+// padding is zero. 32 x 32 element blocks through shared memory.
+__global__ void __launch_bounds__(256)
+    mm_tc_presplit_kernel(const float *__restrict__ A, int64_t m, int64_t n, int64_t lda,
+                          int64_t Qp, int64_t Pp, int64_t kbs, unsigned char *__restrict__ hi_t,
+                          unsigned char *__restrict__ lo_t)
+{
+    __shared__ float tile[32][33];
+    const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t i = i0 + r, j = j0 + tx;
+        tile[r][tx] = (i < m && j < n) ? A[i * lda + j] : 0.0f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t p = j0 + r, q = i0 + tx;
+        if (p < Pp && q < Qp) {
+            const float v = tile[tx][r];
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            const float d = __fmaf_rn(__bfloat162float(h), -1.0f, v);
+            const int pr = (int)(p & 127), qq = (int)(q & 63);
+            const size_t off = ((size_t)(p >> 7) * (size_t)kbs + (size_t)(q >> 6)) * 16384 +
+                               (size_t)(pr * 128 + ((((qq >> 3) ^ (pr & 7))) << 4) + (qq & 7) * 2);
+            *reinterpret_cast<__nv_bfloat16 *>(hi_t + off) = h;
+            *reinterpret_cast<__nv_bfloat16 *>(lo_t + off) = __float2bfloat16_rn(d);
+        }
+    }
+}
+
 __global__ void mm_tc_split_rows_kernel(const float *__restrict__ X, int64_t rows, int k,
                                         int64_t rows_p, __nv_bfloat16 *__restrict__ hi,
                                         __nv_bfloat16 *__restrict__ lo)
@@ -979,12 +1047,19 @@ size_t mm_tc_work_bytes(int64_t m, int64_t n, int k, int trans)
     return a > b ? a : b;
 }
 
+namespace {
+
 // Products, and with W / f_dev given (trans = 0, k <= 64) the fused
-// objective f(W, H) with H^T = F written to *f_dev.
-nmf_status launch_mm_tc_obj(const float *A, int64_t m, int64_t n, int64_t lda, const float *F,
-                            int k, int trans, float *out, const float *W, double *f_dev,
-                            void *work, size_t work_bytes, cudaStream_t s)
+// objective f(W, H) with H^T = F written to *f_dev; with at_hi / at_lo given
+// (trans = 1) A^T W from the pre-split transpose instead of A.
+nmf_status launch_mm_tc_impl(const float *A, int64_t m, int64_t n, int64_t lda, const float *F,
+                             int k, int trans, float *out, const float *W, double *f_dev,
+                             void *work, size_t work_bytes, cudaStream_t s,
+                             const void *at_hi, const void *at_lo)
 {
+    const bool presplit = at_hi != nullptr;
+    if (presplit && (trans != 1 || !at_lo))
+        return NMF_ERR_INVALID_ARG;
     const int64_t P = trans ? n : m;
     const int64_t Q = trans ? m : n;
     const bool obj = f_dev != nullptr;
@@ -998,7 +1073,10 @@ nmf_status launch_mm_tc_obj(const float *A, int64_t m, int64_t n, int64_t lda, c
         return NMF_OK;
     }
     // TMA needs a 16-byte-aligned base and row pitch; coordinates must fit int32.
-    if ((reinterpret_cast<uintptr_t>(A) & 15) || (lda % 4) || P > INT32_MAX || Q > INT32_MAX)
+    if (P > INT32_MAX || Q > INT32_MAX)
+        return NMF_ERR_INVALID_ARG;
+    if (presplit ? ((reinterpret_cast<uintptr_t>(at_hi) | reinterpret_cast<uintptr_t>(at_lo)) & 15)
+                 : ((reinterpret_cast<uintptr_t>(A) & 15) || (lda % 4)))
         return NMF_ERR_INVALID_ARG;
     const TcWork wl = tc_work(m, n, k, trans, obj);
     if (!work || work_bytes < wl.total)
@@ -1010,13 +1088,14 @@ nmf_status launch_mm_tc_obj(const float *A, int64_t m, int64_t n, int64_t lda, c
     NMF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     __nv_bfloat16 *bhi = reinterpret_cast<__nv_bfloat16 *>(wb + wl.f_off);
     CUtensorMap maps[5];
-    bool ok = trans == 0
-                  ? make_map_2d(&maps[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)Q,
-                                (uint64_t)P, (uint64_t)lda * 4, 32, TC_BM,
-                                CU_TENSOR_MAP_SWIZZLE_128B)
-                  : make_map_2d(&maps[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)P,
-                                (uint64_t)Q, (uint64_t)lda * 4, TC_BM, TC_BK,
-                                CU_TENSOR_MAP_SWIZZLE_NONE);
+    bool ok = true;
+    if (!presplit)   // (the pre-split A^T is read by plain bulk copies, no map)
+        ok = trans == 0 ? make_map_2d(&maps[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)Q,
+                                      (uint64_t)P, (uint64_t)lda * 4, 32, TC_BM,
+                                      CU_TENSOR_MAP_SWIZZLE_128B)
+                        : make_map_2d(&maps[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)P,
+                                      (uint64_t)Q, (uint64_t)lda * 4, TC_BM, TC_BK,
+                                      CU_TENSOR_MAP_SWIZZLE_NONE);
     if (!ok)
         return NMF_ERR_CUDA;
     TcArgs a;
@@ -1026,6 +1105,9 @@ nmf_status launch_mm_tc_obj(const float *A, int64_t m, int64_t n, int64_t lda, c
     a.out = out;
     a.err = err;
     a.obj_partials = reinterpret_cast<double *>(wb + wl.part_off);
+    a.at_hi = static_cast<const unsigned char *>(at_hi);
+    a.at_lo = static_cast<const unsigned char *>(at_lo);
+    a.at_kbs = Qp / TC_BK;
     if (obj) {
         __nv_bfloat16 *whi = reinterpret_cast<__nv_bfloat16 *>(wb + wl.w_off);
         __nv_bfloat16 *wlo = whi + (size_t)Pp * 64;
@@ -1036,7 +1118,7 @@ nmf_status launch_mm_tc_obj(const float *A, int64_t m, int64_t n, int64_t lda, c
             !make_map_2d(&maps[4], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, wlo, 64, (uint64_t)Pp, 128,
                          64, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B))
             return NMF_ERR_CUDA;
-    } else {
+    } else if (!presplit) {
         maps[3] = maps[4] = maps[0];   // unused
     }
     for (int col0 = 0; col0 < k; col0 += 64) {
@@ -1051,6 +1133,8 @@ nmf_status launch_mm_tc_obj(const float *A, int64_t m, int64_t n, int64_t lda, c
             !make_map_2d(&maps[2], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, blo, (uint64_t)Qp, (uint64_t)N,
                          (uint64_t)Qp * 2, TC_BK, (uint32_t)N, CU_TENSOR_MAP_SWIZZLE_128B))
             return NMF_ERR_CUDA;
+        if (presplit)
+            maps[0] = maps[3] = maps[4] = maps[1];   // unused by TRANS = 2
         a.col0 = col0;
         a.kc = kc;
         const bool fuse = obj && col0 == 0;
@@ -1062,7 +1146,7 @@ nmf_status launch_mm_tc_obj(const float *A, int64_t m, int64_t n, int64_t lda, c
         a.out = grid_y > 1 ? partial : out;
         nmf_status st;
         if (trans)
-            st = launch_tc_n<1, 0>(N, maps, a, s);
+            st = presplit ? launch_tc_n<2, 0>(N, maps, a, s) : launch_tc_n<1, 0>(N, maps, a, s);
         else if (fuse)
             st = launch_tc_n<0, 1>(N, maps, a, s);
         else
@@ -1081,12 +1165,51 @@ nmf_status launch_mm_tc_obj(const float *A, int64_t m, int64_t n, int64_t lda, c
     return NMF_OK;
 }
 
+}  // namespace
+
+nmf_status launch_mm_tc_obj(const float *A, int64_t m, int64_t n, int64_t lda, const float *F,
+                            int k, int trans, float *out, const float *W, double *f_dev,
+                            void *work, size_t work_bytes, cudaStream_t s)
+{
+    return launch_mm_tc_impl(A, m, n, lda, F, k, trans, out, W, f_dev, work, work_bytes, s,
+                             nullptr, nullptr);
+}
+
 nmf_status launch_mm_tc(const float *A, int64_t m, int64_t n, int64_t lda, const float *F,
                         int k, int trans, float *out, void *work, size_t work_bytes,
                         cudaStream_t s)
 {
-    return launch_mm_tc_obj(A, m, n, lda, F, k, trans, out, nullptr, nullptr, work, work_bytes,
-                            s);
+    return launch_mm_tc_impl(A, m, n, lda, F, k, trans, out, nullptr, nullptr, work, work_bytes,
+                             s, nullptr, nullptr);
+}
+
+size_t mm_tc_presplit_bytes(int64_t m, int64_t n)
+{
+    return (size_t)(cdiv(n, TC_BM) * TC_BM) * (size_t)(cdiv(m, TC_BK) * TC_BK) * 2;
+}
+
+nmf_status launch_mm_tc_presplit_make(const float *A, int64_t m, int64_t n, int64_t lda,
+                                      void *at_hi, void *at_lo, cudaStream_t s)
+{
+    if (m == 0 || n == 0)
+        return NMF_OK;
+    const int64_t Qp = cdiv(m, TC_BK) * TC_BK, Pp = cdiv(n, TC_BM) * TC_BM;
+    const dim3 grid((unsigned)cdiv(Pp, 32), (unsigned)cdiv(Qp, 32));
+    if (grid.y > 65535u)
+        return NMF_ERR_INVALID_ARG;
+    mm_tc_presplit_kernel<<<grid, dim3(32, 8), 0, s>>>(A, m, n, lda, Qp, Pp, Qp / TC_BK,
+                                                        static_cast<unsigned char *>(at_hi),
+                                                        static_cast<unsigned char *>(at_lo));
+    NMF_LAUNCHED("mm_tc_presplit_kernel");
+    return NMF_OK;
+}
+
+nmf_status launch_mm_tc_presplit(const void *at_hi, const void *at_lo, int64_t m, int64_t n,
+                                 const float *W, int k, float *out, void *work,
+                                 size_t work_bytes, cudaStream_t s)
+{
+    return launch_mm_tc_impl(nullptr, m, n, 0, W, k, 1, out, nullptr, nullptr, work, work_bytes,
+                             s, at_hi, at_lo);
 }
 
 }  // namespace nmf
