@@ -244,6 +244,7 @@ struct nmf_handle {
     void *tc_work = nullptr;
     size_t tc_work_bytes = 0;
     void *at_hi = nullptr, *at_lo = nullptr;   // A^T pre-split, tile-major (dense BF16x3)
+    void *ar_hi = nullptr, *ar_lo = nullptr;   // A pre-split, tile-major (dense BF16x3)
     int64_t *t_rowptr = nullptr;                // CSR of A^T (sparse input)
     int32_t *t_colidx = nullptr;
     float *t_vals = nullptr;
@@ -344,9 +345,10 @@ nmf_status mm(nmf_handle *h, int trans, const float *F, float *out)
         return launch_spmm(h->t_rowptr, h->t_colidx, h->t_vals, c.n, F, c.k, out, h->stream);
     }
     if (c.precision == NMF_PREC_BF16X3) {
-        if (trans == 1 && h->at_hi)
-            return launch_mm_tc_presplit(h->at_hi, h->at_lo, c.m, c.n, F, c.k, out, h->tc_work,
-                                         h->tc_work_bytes, h->stream);
+        void *hi = trans ? h->at_hi : h->ar_hi, *lo = trans ? h->at_lo : h->ar_lo;
+        if (hi)
+            return launch_mm_tc_presplit(hi, lo, c.m, c.n, F, c.k, trans, out, nullptr, nullptr,
+                                         h->tc_work, h->tc_work_bytes, h->stream);
         return launch_mm_tc(h->A.dense, c.m, c.n, h->A.lda, F, c.k, trans, out, h->tc_work,
                             h->tc_work_bytes, h->stream);
     }
@@ -356,12 +358,22 @@ nmf_status mm(nmf_handle *h, int trans, const float *F, float *out)
 // f(W, H) into *f_dev. Sparse input: after an H half-step (after_h) Y holds
 // A^T W and GW = W^T W for the current W; otherwise both are formed here (Y
 // and GW are scratch between iterations).
+// A H^T into V with f(W, H) of the current factors fused (dense BF16x3).
+nmf_status mm_obj(nmf_handle *h, double *f_dev)
+{
+    const nmf_config &c = h->cfg;
+    if (h->ar_hi)
+        return launch_mm_tc_presplit(h->ar_hi, h->ar_lo, c.m, c.n, h->Ht, c.k, 0, h->V, h->W,
+                                     f_dev, h->tc_work, h->tc_work_bytes, h->stream);
+    return launch_mm_tc_obj(h->A.dense, c.m, c.n, h->A.lda, h->Ht, c.k, 0, h->V, h->W, f_dev,
+                            h->tc_work, h->tc_work_bytes, h->stream);
+}
+
 nmf_status objective_into(nmf_handle *h, double *f_dev, bool after_h = false)
 {
     const nmf_config &c = h->cfg;
     if (h->fused_obj)
-        return launch_mm_tc_obj(h->A.dense, c.m, c.n, h->A.lda, h->Ht, c.k, 0, h->V, h->W,
-                                f_dev, h->tc_work, h->tc_work_bytes, h->stream);
+        return mm_obj(h, f_dev);
     if (c.input_kind == NMF_INPUT_CSR) {
         if (!after_h) {
             NMF_TRY(mm(h, 1, h->W, h->Y));
@@ -437,8 +449,7 @@ nmf_status one_iteration(nmf_handle *h)
         if (h->obj_pending) {
             // The previous iterate's f(W, H) rides on this A H^T pass.
             double *slot = h->f_hist + ((h->f_count - 1) % F_HIST_CAP);
-            NMF_TRY(launch_mm_tc_obj(h->A.dense, c.m, c.n, h->A.lda, h->Ht, c.k, 0, h->V, h->W,
-                                     slot, h->tc_work, h->tc_work_bytes, h->stream));
+            NMF_TRY(mm_obj(h, slot));
             h->obj_pending = false;
         } else {
             NMF_TRY(mm(h, 0, h->Ht, h->V));
@@ -507,6 +518,8 @@ void free_handle(nmf_handle *h)
     cudaFree(h->obj_part);
     cudaFree(h->at_hi);
     cudaFree(h->at_lo);
+    cudaFree(h->ar_hi);
+    cudaFree(h->ar_lo);
     cudaFree(h->pgw2);
     cudaFree(h->pgh2);
     cudaFree(h->pg_part);
@@ -613,19 +626,21 @@ extern "C" nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nm
         if (b1 > h->tc_work_bytes)
             h->tc_work_bytes = b1;
         chk(cudaMalloc(&h->tc_work, h->tc_work_bytes ? h->tc_work_bytes : 16));
-        // A^T split into BF16 hi / lo once (4 bytes per element of A): A^T W
-        // then needs no per-call transpose and split. Without the memory the
-        // handle splits A on the fly in every A^T W pass instead.
-        if (e == cudaSuccess) {
-            const size_t bytes = mm_tc_presplit_bytes(c.m, c.n);
-            if (cudaMalloc(&h->at_hi, bytes) != cudaSuccess ||
-                cudaMalloc(&h->at_lo, bytes) != cudaSuccess) {
+        // A and A^T split into BF16 hi / lo once (4 bytes per element of A
+        // each): the products then need no per-call split (nor transpose).
+        // Without the memory the handle splits A on the fly in every pass.
+        auto alloc_pair = [&](void **hi, void **lo, size_t bytes) {
+            if (cudaMalloc(hi, bytes) != cudaSuccess || cudaMalloc(lo, bytes) != cudaSuccess) {
                 cudaGetLastError();
-                cudaFree(h->at_hi);
-                cudaFree(h->at_lo);
-                h->at_hi = h->at_lo = nullptr;
+                cudaFree(*hi);
+                cudaFree(*lo);
+                *hi = *lo = nullptr;
             }
-        }
+        };
+        if (e == cudaSuccess)
+            alloc_pair(&h->at_hi, &h->at_lo, mm_tc_presplit_bytes(c.n, c.m));
+        if (e == cudaSuccess && h->at_hi)
+            alloc_pair(&h->ar_hi, &h->ar_lo, mm_tc_presplit_bytes(c.m, c.n));
     }
     if (e == cudaSuccess && c.input_kind == NMF_INPUT_CSR) {
         chk(dalloc(&h->t_rowptr, (size_t)c.n + 1));
@@ -647,7 +662,10 @@ extern "C" nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nm
         NMF_CUDA(cudaMemcpyAsync(h->Ht, Ht0, sizeof(float) * (size_t)c.n * k,
                                  cudaMemcpyDeviceToDevice, h->stream));
         if (h->at_hi)
-            NMF_TRY(launch_mm_tc_presplit_make(A->dense, c.m, c.n, A->lda, h->at_hi, h->at_lo,
+            NMF_TRY(launch_mm_tc_presplit_make(A->dense, c.m, c.n, A->lda, 1, h->at_hi, h->at_lo,
+                                               h->stream));
+        if (h->ar_hi)
+            NMF_TRY(launch_mm_tc_presplit_make(A->dense, c.m, c.n, A->lda, 0, h->ar_hi, h->ar_lo,
                                                h->stream));
         if (c.input_kind == NMF_INPUT_CSR) {
             unsigned long long *cursor = nullptr;

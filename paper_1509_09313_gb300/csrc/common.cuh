@@ -79,16 +79,17 @@ nmf_status launch_mm_tc_obj(const float *A, int64_t m, int64_t n, int64_t lda, c
                             int k, int trans, float *out, const float *W, double *f_dev,
                             void *work, size_t work_bytes, cudaStream_t s);
 
-// A^T W from A^T pre-split into BF16 hi / lo copies (tile-major, each
-// mm_tc_presplit_bytes(m, n) bytes), made once by launch_mm_tc_presplit_make:
-// bitwise the same result as launch_mm_tc(trans = 1) without the per-call
-// transpose and split.
-size_t mm_tc_presplit_bytes(int64_t m, int64_t n);
+// Products from A pre-split into BF16 hi / lo copies (tile-major, each
+// mm_tc_presplit_bytes(rows, K) bytes: trans = 0 rows m, K n; trans = 1 rows
+// n, K m), made once by launch_mm_tc_presplit_make. trans = 1 gives bitwise
+// the result of launch_mm_tc; trans = 0 too, and with W / f_dev the objective
+// from hi + lo (within 2^-18 relative of A) instead of A.
+size_t mm_tc_presplit_bytes(int64_t rows, int64_t K);
 nmf_status launch_mm_tc_presplit_make(const float *A, int64_t m, int64_t n, int64_t lda,
-                                      void *at_hi, void *at_lo, cudaStream_t s);
-nmf_status launch_mm_tc_presplit(const void *at_hi, const void *at_lo, int64_t m, int64_t n,
-                                 const float *W, int k, float *out, void *work,
-                                 size_t work_bytes, cudaStream_t s);
+                                      int trans, void *hi, void *lo, cudaStream_t s);
+nmf_status launch_mm_tc_presplit(const void *hi, const void *lo, int64_t m, int64_t n,
+                                 const float *F, int k, int trans, float *out, const float *W,
+                                 double *f_dev, void *work, size_t work_bytes, cudaStream_t s);
 
 // CSR SpMM: out (rows x k) = S F.
 nmf_status launch_spmm(const int64_t *rowptr, const int32_t *colidx, const float *vals,

@@ -389,7 +389,10 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
                  const __grid_constant__ CUtensorMap tmBlo, const __grid_constant__ CUtensorMap tmWhi,
                  const __grid_constant__ CUtensorMap tmWlo, const TcArgs args)
 {
-    static_assert(!OBJ || TRANS == 0, "the objective rides on the A H^T pass");
+    static_assert(!OBJ || TRANS == 0 || TRANS == 3, "the objective rides on the A H^T pass");
+    // Pre-split A (TRANS = 3) with the objective: the residual warps read each
+    // stage too and release it with the MMA commits.
+    constexpr int EMPTY_ARRIVALS = 1 + OBJ + (TRANS == 3 && OBJ ? 4 : 0);
     using L = TcLayout<N, OBJ>;
     constexpr int S = L::STAGES;
     extern __shared__ unsigned char smem_dyn[];
@@ -416,7 +419,7 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
     if (threadIdx.x == 0) {
         for (int i = 0; i < S; ++i) {
             mbar_init(full(i), 1);
-            mbar_init(empty(i), OBJ ? 2 : 1);   // product MMAs (+ objective MMAs)
+            mbar_init(empty(i), EMPTY_ARRIVALS);   // product MMAs (+ objective)
             mbar_init(a_full(i), 4);
             mbar_init(readb(i), 4);
         }
@@ -476,9 +479,9 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
                 } else if (TRANS == 1) {
                     tma_load_2d(dst, &tmA, (int)p0, q0, full(s));
                 } else {
-                    // Pre-split A^T: each hi / lo tile is 16 contiguous KB in
-                    // global memory, already in the K-major swizzled operand
-                    // layout the split warps would write.
+                    // Pre-split A^T (TRANS = 2) or A (3): each hi / lo tile is 16
+                    // contiguous KB in global memory, already in the K-major
+                    // swizzled operand layout the split warps would write.
                     const size_t toff =
                         ((size_t)blockIdx.x * (size_t)args.at_kbs + (size_t)(kb0 + kb)) *
                         (size_t)L::A_BYTES;
@@ -508,7 +511,7 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
                 const int s = kb % S, u = kb / S;
                 const int b = kb & 1, ub = kb >> 1;
                 if (!mbar_wait_fast(acc_empty(b), (ub & 1) ^ 1, abort) ||
-                    !mbar_wait_fast(TRANS == 2 ? full(s) : a_full(s), u & 1, abort))
+                    !mbar_wait_fast(TRANS >= 2 ? full(s) : a_full(s), u & 1, abort))
                     break;
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * 2 * N);
@@ -560,7 +563,7 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
                 mma_commit(empty(s));
             }
         }
-    } else if (TRANS != 2 && warp >= 2 && warp < 6) {
+    } else if ((TRANS <= 1 || (TRANS == 3 && OBJ)) && warp >= 2 && warp < 6) {
         // ---------------------------------------------------- split (warps 2-5)
         const int ct = threadIdx.x - 64;        // 0..127
         const int quarter = warp & 3;           // TMEM lane quarter of this warp
@@ -575,6 +578,64 @@ __global__ void __launch_bounds__(TcLayout<N, OBJ>::THREADS, 1)
                 break;
             unsigned char *st = smem + s * L::STAGE_BYTES;
             const int b1 = kb & 1, u1 = kb >> 1;
+            if (TRANS == 3) {
+                // Residuals only: the stage holds A's hi and lo tiles (row r
+                // = this thread's TMEM lane, K-major, 128-byte swizzled); a =
+                // hi + lo, the value the products use (within 2^-18 of A).
+                const int r = quarter * 32 + lane;
+                if (!mbar_wait(obj_full(b1), u1 & 1, abort))
+                    break;
+                tc_fence_after();
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t whr[32];
+                    tmem_ld32_nowait(tq + (uint32_t)(4 * N + b1 * 64 + h * 32), whr);
+                    float a[32];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const uint4 qh = *reinterpret_cast<const uint4 *>(st + sw128_off(r, 4 * h + c));
+                        const uint4 ql = *reinterpret_cast<const uint4 *>(st + L::A_BYTES +
+                                                                          sw128_off(r, 4 * h + c));
+                        const uint32_t hw[4] = {qh.x, qh.y, qh.z, qh.w};
+                        const uint32_t lw[4] = {ql.x, ql.y, ql.z, ql.w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float2 sum = __fadd2_rn(
+                                make_float2(__uint_as_float(hw[j] << 16),
+                                            __uint_as_float(hw[j] & 0xffff0000u)),
+                                make_float2(__uint_as_float(lw[j] << 16),
+                                            __uint_as_float(lw[j] & 0xffff0000u)));
+                            a[8 * c + 2 * j] = sum.x;
+                            a[8 * c + 2 * j + 1] = sum.y;
+                        }
+                    }
+                    tmem_wait_ld();
+                    float2 q01 = make_float2(0.0f, 0.0f), q23 = make_float2(0.0f, 0.0f);
+                    const float2 m1 = make_float2(-1.0f, -1.0f);
+#pragma unroll
+                    for (int i = 0; i < 32; i += 4) {
+                        const float2 e01 = __ffma2_rn(
+                            make_float2(__uint_as_float(whr[i]), __uint_as_float(whr[i + 1])), m1,
+                            make_float2(a[i], a[i + 1]));
+                        const float2 e23 = __ffma2_rn(
+                            make_float2(__uint_as_float(whr[i + 2]), __uint_as_float(whr[i + 3])),
+                            m1, make_float2(a[i + 2], a[i + 3]));
+                        q01 = __ffma2_rn(e01, e01, q01);
+                        q23 = __ffma2_rn(e23, e23, q23);
+                    }
+                    const float y = ((q01.x + q01.y) + (q23.x + q23.y)) - fc;
+                    const float t = fs + y;
+                    fc = (t - fs) - y;
+                    fs = t;
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(obj_empty(b1));
+                    mbar_arrive(empty(s));   // this stage's A is read
+                }
+                continue;
+            }
             if (TRANS == 0) {
                 // Two swizzled halves of 128 rows (p) x 32 floats (q). Each
                 // thread owns row r (= its TMEM lane) and rewrites the 128
@@ -839,12 +900,39 @@ __global__ void mm_tc_split_kernel(const float *__restrict__ F, int64_t Q, int k
 // X (rows x k, float32 row-major, k <= 64) -> BF16 hi / lo rows of 64
 // (zero-padded columns and rows up to rows_p): the objective's K-major
 // operands W [i][r] and H^T [j][r].
-// A (m x n FP32, row stride lda) -> A^T split into BF16 hi / lo, hi = bf16(v),
-// lo = bf16(v - hi) exactly as split2, tile-major: element (row p = A's
-// column j, K index q = A's row i) of the Pp x Qp padded A^T lies in tile
-// (p / 128) * kbs + q / 64, at byte (p % 128) * 128 + ((q % 64 / 8) ^
-// (p % 8)) * 16 + (q % 8) * 2 of it (the SW128 K-major operand layout); the
-// padding is zero. 32 x 32 element blocks through shared memory.
+// Pre-split operand copies, hi = bf16(v), lo = bf16(v - hi) exactly as
+// split2, tile-major: element (row p, K index q) of the Pp x Qp padded
+// operand lies in tile (p / 128) * kbs + q / 64, at byte (p % 128) * 128 +
+// ((q % 64 / 8) ^ (p % 8)) * 16 + (q % 8) * 2 of it (the SW128 K-major
+// operand layout); the padding is zero.
+__device__ __forceinline__ void presplit_store(unsigned char *__restrict__ hi_t,
+                                               unsigned char *__restrict__ lo_t, int64_t p,
+                                               int64_t q, int64_t kbs, float v)
+{
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const float d = __fmaf_rn(__bfloat162float(h), -1.0f, v);
+    const int pr = (int)(p & 127), qq = (int)(q & 63);
+    const size_t off = ((size_t)(p >> 7) * (size_t)kbs + (size_t)(q >> 6)) * 16384 +
+                       (size_t)(pr * 128 + (((qq >> 3) ^ (pr & 7)) << 4) + (qq & 7) * 2);
+    *reinterpret_cast<__nv_bfloat16 *>(hi_t + off) = h;
+    *reinterpret_cast<__nv_bfloat16 *>(lo_t + off) = __float2bfloat16_rn(d);
+}
+
+// A (m x n FP32, row stride lda) as the operand of A H^T: p = A's row i,
+// q = A's column j.
+__global__ void __launch_bounds__(256)
+    mm_tc_presplit_rows_kernel(const float *__restrict__ A, int64_t m, int64_t n, int64_t lda,
+                               int64_t Qp, int64_t Pp, int64_t kbs,
+                               unsigned char *__restrict__ hi_t, unsigned char *__restrict__ lo_t)
+{
+    const int64_t p = blockIdx.x;   // one row per block column
+    const int64_t q = (int64_t)blockIdx.y * 256 + threadIdx.x;
+    if (q < Qp && p < Pp)
+        presplit_store(hi_t, lo_t, p, q, kbs, (p < m && q < n) ? A[p * lda + q] : 0.0f);
+}
+
+// A as the operand of A^T W: p = A's column j, q = A's row i; 32 x 32
+// element blocks through shared memory.
 __global__ void __launch_bounds__(256)
     mm_tc_presplit_kernel(const float *__restrict__ A, int64_t m, int64_t n, int64_t lda,
                           int64_t Qp, int64_t Pp, int64_t kbs, unsigned char *__restrict__ hi_t,
@@ -860,16 +948,8 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
         const int64_t p = j0 + r, q = i0 + tx;
-        if (p < Pp && q < Qp) {
-            const float v = tile[tx][r];
-            const __nv_bfloat16 h = __float2bfloat16_rn(v);
-            const float d = __fmaf_rn(__bfloat162float(h), -1.0f, v);
-            const int pr = (int)(p & 127), qq = (int)(q & 63);
-            const size_t off = ((size_t)(p >> 7) * (size_t)kbs + (size_t)(q >> 6)) * 16384 +
-                               (size_t)(pr * 128 + ((((qq >> 3) ^ (pr & 7))) << 4) + (qq & 7) * 2);
-            *reinterpret_cast<__nv_bfloat16 *>(hi_t + off) = h;
-            *reinterpret_cast<__nv_bfloat16 *>(lo_t + off) = __float2bfloat16_rn(d);
-        }
+        if (p < Pp && q < Qp)
+            presplit_store(hi_t, lo_t, p, q, kbs, tile[tx][r]);
     }
 }
 
@@ -1058,7 +1138,7 @@ nmf_status launch_mm_tc_impl(const float *A, int64_t m, int64_t n, int64_t lda, 
                              const void *at_hi, const void *at_lo)
 {
     const bool presplit = at_hi != nullptr;
-    if (presplit && (trans != 1 || !at_lo))
+    if (presplit && !at_lo)
         return NMF_ERR_INVALID_ARG;
     const int64_t P = trans ? n : m;
     const int64_t Q = trans ? m : n;
@@ -1133,8 +1213,11 @@ nmf_status launch_mm_tc_impl(const float *A, int64_t m, int64_t n, int64_t lda, 
             !make_map_2d(&maps[2], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, blo, (uint64_t)Qp, (uint64_t)N,
                          (uint64_t)Qp * 2, TC_BK, (uint32_t)N, CU_TENSOR_MAP_SWIZZLE_128B))
             return NMF_ERR_CUDA;
-        if (presplit)
-            maps[0] = maps[3] = maps[4] = maps[1];   // unused by TRANS = 2
+        if (presplit) {                  // TRANS = 2 / 3 read A by plain bulk copies
+            maps[0] = maps[1];
+            if (!obj)
+                maps[3] = maps[4] = maps[1];
+        }
         a.col0 = col0;
         a.kc = kc;
         const bool fuse = obj && col0 == 0;
@@ -1148,9 +1231,9 @@ nmf_status launch_mm_tc_impl(const float *A, int64_t m, int64_t n, int64_t lda, 
         if (trans)
             st = presplit ? launch_tc_n<2, 0>(N, maps, a, s) : launch_tc_n<1, 0>(N, maps, a, s);
         else if (fuse)
-            st = launch_tc_n<0, 1>(N, maps, a, s);
+            st = presplit ? launch_tc_n<3, 1>(N, maps, a, s) : launch_tc_n<0, 1>(N, maps, a, s);
         else
-            st = launch_tc_n<0, 0>(N, maps, a, s);
+            st = presplit ? launch_tc_n<3, 0>(N, maps, a, s) : launch_tc_n<0, 0>(N, maps, a, s);
         NMF_TRY(st);
         if (grid_y > 1) {
             mm_tc_reduce_kernel<<<(unsigned)cdiv(P * kc, 256), 256, 0, s>>>(partial, grid_y, P, k,
@@ -1183,33 +1266,41 @@ nmf_status launch_mm_tc(const float *A, int64_t m, int64_t n, int64_t lda, const
                              s, nullptr, nullptr);
 }
 
-size_t mm_tc_presplit_bytes(int64_t m, int64_t n)
+size_t mm_tc_presplit_bytes(int64_t rows, int64_t K)
 {
-    return (size_t)(cdiv(n, TC_BM) * TC_BM) * (size_t)(cdiv(m, TC_BK) * TC_BK) * 2;
+    return (size_t)(cdiv(rows, TC_BM) * TC_BM) * (size_t)(cdiv(K, TC_BK) * TC_BK) * 2;
 }
 
 nmf_status launch_mm_tc_presplit_make(const float *A, int64_t m, int64_t n, int64_t lda,
-                                      void *at_hi, void *at_lo, cudaStream_t s)
+                                      int trans, void *hi, void *lo, cudaStream_t s)
 {
     if (m == 0 || n == 0)
         return NMF_OK;
-    const int64_t Qp = cdiv(m, TC_BK) * TC_BK, Pp = cdiv(n, TC_BM) * TC_BM;
-    const dim3 grid((unsigned)cdiv(Pp, 32), (unsigned)cdiv(Qp, 32));
-    if (grid.y > 65535u)
-        return NMF_ERR_INVALID_ARG;
-    mm_tc_presplit_kernel<<<grid, dim3(32, 8), 0, s>>>(A, m, n, lda, Qp, Pp, Qp / TC_BK,
-                                                        static_cast<unsigned char *>(at_hi),
-                                                        static_cast<unsigned char *>(at_lo));
-    NMF_LAUNCHED("mm_tc_presplit_kernel");
+    const int64_t P = trans ? n : m, Q = trans ? m : n;
+    const int64_t Pp = cdiv(P, TC_BM) * TC_BM, Qp = cdiv(Q, TC_BK) * TC_BK;
+    unsigned char *h = static_cast<unsigned char *>(hi), *l = static_cast<unsigned char *>(lo);
+    if (trans) {
+        const dim3 grid((unsigned)cdiv(Pp, 32), (unsigned)cdiv(Qp, 32));
+        if (grid.y > 65535u)
+            return NMF_ERR_INVALID_ARG;
+        mm_tc_presplit_kernel<<<grid, dim3(32, 8), 0, s>>>(A, m, n, lda, Qp, Pp, Qp / TC_BK, h, l);
+        NMF_LAUNCHED("mm_tc_presplit_kernel");
+    } else {
+        const dim3 grid((unsigned)Pp, (unsigned)cdiv(Qp, 256));
+        if (Pp > 2147483647 || cdiv(Qp, 256) > 65535)
+            return NMF_ERR_INVALID_ARG;
+        mm_tc_presplit_rows_kernel<<<grid, 256, 0, s>>>(A, m, n, lda, Qp, Pp, Qp / TC_BK, h, l);
+        NMF_LAUNCHED("mm_tc_presplit_rows_kernel");
+    }
     return NMF_OK;
 }
 
-nmf_status launch_mm_tc_presplit(const void *at_hi, const void *at_lo, int64_t m, int64_t n,
-                                 const float *W, int k, float *out, void *work,
-                                 size_t work_bytes, cudaStream_t s)
+nmf_status launch_mm_tc_presplit(const void *hi, const void *lo, int64_t m, int64_t n,
+                                 const float *F, int k, int trans, float *out, const float *W,
+                                 double *f_dev, void *work, size_t work_bytes, cudaStream_t s)
 {
-    return launch_mm_tc_impl(nullptr, m, n, 0, W, k, 1, out, nullptr, nullptr, work, work_bytes,
-                             s, at_hi, at_lo);
+    return launch_mm_tc_impl(nullptr, m, n, 0, F, k, trans, out, W, f_dev, work, work_bytes, s,
+                             hi, lo);
 }
 
 }  // namespace nmf
