@@ -61,16 +61,17 @@ FP32_LANES_PER_SM = 128
 # DRAM traffic per launch (read + write bytes) of the dominant kernel from one
 # ncu capture, keyed by (kernel, workload, precision); None until captured or
 # when the kernel changed since. dense-large: the two mm_tc_kernel launches of
-# an iteration captured on the 24000 x 16000 case (A H^T with the objective:
-# 1.5505 GB read + 7.0 MB written; A^T W: 1.5464 GB + 19.2 MB in 6 splits),
-# reads scaled by the element ratio 16, writes by the rows (A H^T 96000 x 50
-# out; A^T W 3 splits of 64000 x 50 there), averaged: 24.81 GB per launch
-# against 24.61 GB of algorithmic bytes (profiles/mm_tc_kernel_dense-medium.md).
+# an iteration captured on the 24000 x 16000 case (A H^T with the objective,
+# from the pre-split A: 1.5545 GB read + 7.3 MB written; A^T W from the
+# pre-split A^T: 1.5464 GB + 18.8 MB in 6 splits), reads scaled by the element
+# ratio 16, writes by the rows (A H^T 96000 x 50 out; A^T W 3 splits of
+# 64000 x 50 there), averaged: 24.84 GB per launch against 24.61 GB of
+# algorithmic bytes (profiles/mm_tc_kernel_dense-medium.md).
 MLP_HIDDEN = 256     # width of the proposal network (3k -> 256 -> 256 -> k)
 
 NCU_TRAFFIC = {
-    ("mm_tc_kernel", "dense-large", "bf16x3"): 24.81e9,
-    ("mm_tc_kernel", "dense-medium", "bf16x3"): 1.5616e9,
+    ("mm_tc_kernel", "dense-large", "bf16x3"): 24.84e9,
+    ("mm_tc_kernel", "dense-medium", "bf16x3"): 1.5635e9,
 }
 
 
