@@ -223,6 +223,9 @@ typedef struct nmf_config {
     int32_t objective_every;   /* 1: f after every iteration (history kept);
                                   0: only on nmf_objective() */
     int32_t solver;            /* nmf_solver (0, BPP, when zero-initialised) */
+    int32_t no_split_copies;   /* dense BF16x3: 0 (default) keeps BF16 hi / lo copies of A
+                                  and A^T (+8 bytes per element of A) so the products need
+                                  no per-pass split; 1 splits A in every pass (same products) */
 } nmf_config;
 
 /* The input matrix. Its device buffers are BORROWED: the caller keeps them

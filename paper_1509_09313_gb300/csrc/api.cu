@@ -637,7 +637,7 @@ extern "C" nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nm
                 *hi = *lo = nullptr;
             }
         };
-        if (e == cudaSuccess)
+        if (e == cudaSuccess && !c.no_split_copies)
             alloc_pair(&h->at_hi, &h->at_lo, mm_tc_presplit_bytes(c.n, c.m));
         if (e == cudaSuccess && h->at_hi)
             alloc_pair(&h->ar_hi, &h->ar_lo, mm_tc_presplit_bytes(c.m, c.n));

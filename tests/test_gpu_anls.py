@@ -124,6 +124,28 @@ def test_sparse_objective_standalone(nmf):
     h.nmf_destroy()
 
 
+def test_split_copies_give_the_same_products(nmf):
+    # The pre-split BF16 copies of A and A^T hold exactly the hi / lo values the
+    # in-pass split forms, so the factors of a BF16x3 run are bitwise the same
+    # with and without them; only the fused objective changes (its residuals
+    # use hi + lo, within 2^-18 of A).
+    m, n, k, T = 3000, 2000, 24, 6
+    A = synth.dense_planted(m, n, k, 0.02, seed=11)
+    W0, Ht0 = synth.init_factors(m, n, k, seed=11)
+    out = []
+    for copies in (True, False):
+        h = nmf.nmf_init(dev(A), dev(W0), dev(Ht0), precision="bf16x3", start="warm",
+                         split_copies=copies)
+        h.nmf_iterate(T)
+        assert h.nmf_sync() == nmf.NMF_OK
+        W, Ht = h.nmf_get_factors()
+        out.append((W.cpu().numpy(), Ht.cpu().numpy(), np.array(h.nmf_objective_history())))
+        h.nmf_destroy()
+    (W1, H1, f1), (W2, H2, f2) = out
+    assert np.array_equal(W1, W2) and np.array_equal(H1, H2)
+    assert np.abs(f1 - f2).max() <= 1e-7 * f2.max()
+
+
 def test_checkpoint_resume(nmf):
     m, n, k = 600, 400, 8
     A = synth.dense_planted(m, n, k, 0.01, seed=5)
