@@ -741,7 +741,17 @@ template <int KW>
 nmf_status launch_modes(const SolveParams &P, cudaStream_t s)
 {
     NMF_TRY(launch_solve32(P, s));
-    NMF_TRY((launch_solve<KW, (KW + 1) / 2, 1>(P, 0, s)));
+    // Mode 1 (FP64): an FP32 pass first predicts each right-hand side's
+    // partition into pout, and the FP64 solves start from it (their answer
+    // does not depend on the start; they need fewer rounds).
+    SolveParams P1 = P;
+    if (P.pout && P.max_rounds >= 2 * PREDICT_ROUNDS) {   // (a tight cap keeps its meaning)
+        SolveParams Q = P;
+        Q.predict = 1;
+        NMF_TRY(launch_solve32(Q, s));
+        P1.pin = P.pout;
+    }
+    NMF_TRY((launch_solve<KW, (KW + 1) / 2, 1>(P1, 0, s)));
     NMF_TRY((launch_solve<KW, KW, 2>(P, 0, s)));
     return launch_solve<KW, (KW + 1) / 2, 1>(P, 1, s);
 }
@@ -791,6 +801,7 @@ SolveParams solve_params(int k, int64_t nrhs, const double *G, const float *B, f
     P.rounds_out = rounds_out;
     P.status_out = status_out;
     P.counters = reinterpret_cast<unsigned long long *>(w + L.counters);
+    P.predict = 0;
     P.defer = reinterpret_cast<int64_t *>(w + L.defer);
     P.stats = stats_dev;
     const BppShape sh = shape_for(k);

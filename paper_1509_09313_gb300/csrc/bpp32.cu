@@ -252,10 +252,12 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
 {
     constexpr int RS = 32 * KW;
     constexpr int PT = (KW + 1) / 2;
-    if (P.flags[0] != 0)
+    if (P.predict ? P.flags[0] != 1 : P.flags[0] != 0)
         return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int k = P.k, k4 = (k + 3) & ~3;
+    const int max_rounds = P.predict ? PREDICT_ROUNDS : P.max_rounds;
+    unsigned long long *counter = &P.counters[P.predict ? CNT_PREDICT : CNT_WORK];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *Gs = reinterpret_cast<float *>(smem_raw);
     float *Ms = Gs + k4 * RS;
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
     for (;;) {
         unsigned long long j0 = 0;
         if (lane == 0)
-            j0 = atomicAdd(&P.counters[CNT_WORK], (unsigned long long)P.chunk);
+            j0 = atomicAdd(counter, (unsigned long long)P.chunk);
         j0 = __shfl_sync(FULL, j0, 0);
         if (j0 >= (unsigned long long)P.nrhs)
             break;
@@ -480,7 +482,7 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
                     }
                     if (nV == 0)
                         break;
-                    if (rounds >= P.max_rounds) {
+                    if (rounds >= max_rounds) {
                         status = NMF_ERR_NOT_CONVERGED;
                         break;
                     }
@@ -519,6 +521,31 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
                     if (__any_sync(FULL, nf) && status == NMF_OK)
                         status = NMF_ERR_NONFINITE;
                 }
+            }
+            if (P.predict) {
+                // Only the partition reached seeds the FP64 solves; where the
+                // FP32 system was singular, the starting one (given or empty).
+                if (P.pout) {
+                    unsigned bm[KW];
+#pragma unroll
+                    for (int s = 0; s < KW; ++s) {
+                        bool f = inF[s];
+                        if (status == DEFERRED) {
+                            const int i = lane + 32 * s;
+                            f = P.pin && i < k && ((P.pin[j * P.nwords + (i >> 6)] >> (i & 63)) & 1ull);
+                        }
+                        bm[s] = __ballot_sync(FULL, f);
+                    }
+                    if (lane == 0) {
+#pragma unroll
+                        for (int w = 0; w < (KW + 1) / 2; ++w) {
+                            const uint64_t lo = bm[2 * w];
+                            const uint64_t hi = (2 * w + 1 < KW) ? bm[2 * w + 1] : 0u;
+                            P.pout[j * P.nwords + w] = lo | (hi << 32);
+                        }
+                    }
+                }
+                continue;
             }
             if (status == DEFERRED) {
                 if (lane == 0) {

@@ -18,7 +18,10 @@ constexpr float FEAS_TOL32 = 9.5367431640625e-07f;  // 2^-20
 constexpr int DEFER_CAP = 512;
 
 // Work counters (one array of 64-bit words, zeroed by the prep kernel).
-enum Counter { CNT_WORK = 0, CNT_DEFERRED = 1, CNT_DEFER_WORK = 2, CNT_WORDS = 4 };
+enum Counter { CNT_WORK = 0, CNT_DEFERRED = 1, CNT_DEFER_WORK = 2, CNT_PREDICT = 3, CNT_WORDS = 4 };
+
+// Rounds allowed to the FP32 predictor of an FP64 half-step's partitions.
+constexpr int PREDICT_ROUNDS = 8;
 
 struct SolveParams {
     int k, nwords, max_rounds;
@@ -37,6 +40,10 @@ struct SolveParams {
     unsigned long long *counters;  // CNT_WORDS words
     int64_t *defer;                // DEFER_CAP indices
     BppStats *stats;
+    // predict = 1: an FP64 (mode 1) half-step's FP32 pass that only writes
+    // passive sets (pout) for the FP64 solves to start from; no X, rounds,
+    // status or statistics, at most PREDICT_ROUNDS rounds, its own counter.
+    int predict;
 };
 
 __device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
