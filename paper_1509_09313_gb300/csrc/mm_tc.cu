@@ -904,52 +904,77 @@ __global__ void mm_tc_split_kernel(const float *__restrict__ F, int64_t Q, int k
 // split2, tile-major: element (row p, K index q) of the Pp x Qp padded
 // operand lies in tile (p / 128) * kbs + q / 64, at byte (p % 128) * 128 +
 // ((q % 64 / 8) ^ (p % 8)) * 16 + (q % 8) * 2 of it (the SW128 K-major
-// operand layout); the padding is zero.
-__device__ __forceinline__ void presplit_store(unsigned char *__restrict__ hi_t,
+// operand layout); the padding is zero. Each thread writes whole 16-byte
+// chunks (8 consecutive q of one row p) of both copies.
+__device__ __forceinline__ void presplit_chunk(unsigned char *__restrict__ hi_t,
                                                unsigned char *__restrict__ lo_t, int64_t p,
-                                               int64_t q, int64_t kbs, float v)
+                                               int64_t q8, int64_t kbs, const float (&v)[8])
 {
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const float d = __fmaf_rn(__bfloat162float(h), -1.0f, v);
-    const int pr = (int)(p & 127), qq = (int)(q & 63);
-    const size_t off = ((size_t)(p >> 7) * (size_t)kbs + (size_t)(q >> 6)) * 16384 +
-                       (size_t)(pr * 128 + (((qq >> 3) ^ (pr & 7)) << 4) + (qq & 7) * 2);
-    *reinterpret_cast<__nv_bfloat16 *>(hi_t + off) = h;
-    *reinterpret_cast<__nv_bfloat16 *>(lo_t + off) = __float2bfloat16_rn(d);
+    uint4 hi, lo;
+    split8(v, hi, lo);
+    const int pr = (int)(p & 127), cc = (int)((q8 & 63) >> 3);
+    const size_t off = ((size_t)(p >> 7) * (size_t)kbs + (size_t)(q8 >> 6)) * 16384 +
+                       (size_t)(pr * 128 + ((cc ^ (pr & 7)) << 4));
+    *reinterpret_cast<uint4 *>(hi_t + off) = hi;
+    *reinterpret_cast<uint4 *>(lo_t + off) = lo;
 }
 
-// A (m x n FP32, row stride lda) as the operand of A H^T: p = A's row i,
-// q = A's column j.
+// A (m x n FP32, row stride lda a multiple of 4, 16-byte-aligned base) as the
+// operand of A H^T: p = A's row i, q = A's column j. One chunk per thread,
+// grid-stride over the Pp x Qp / 8 chunks (consecutive threads: consecutive
+// chunks of a row, so reads and writes are coalesced).
 __global__ void __launch_bounds__(256)
     mm_tc_presplit_rows_kernel(const float *__restrict__ A, int64_t m, int64_t n, int64_t lda,
                                int64_t Qp, int64_t Pp, int64_t kbs,
                                unsigned char *__restrict__ hi_t, unsigned char *__restrict__ lo_t)
 {
-    const int64_t p = blockIdx.x;   // one row per block column
-    const int64_t q = (int64_t)blockIdx.y * 256 + threadIdx.x;
-    if (q < Qp && p < Pp)
-        presplit_store(hi_t, lo_t, p, q, kbs, (p < m && q < n) ? A[p * lda + q] : 0.0f);
+    const int64_t cpr = Qp >> 3;   // chunks per row
+    const int64_t total = Pp * cpr;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = e / cpr, q8 = (e - p * cpr) << 3;
+        float v[8];
+        if (p < m && q8 + 8 <= n) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(A + p * lda + q8);
+            const float4 a1 = *reinterpret_cast<const float4 *>(A + p * lda + q8 + 4);
+            v[0] = a0.x; v[1] = a0.y; v[2] = a0.z; v[3] = a0.w;
+            v[4] = a1.x; v[5] = a1.y; v[6] = a1.z; v[7] = a1.w;
+        } else {
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                v[t] = (p < m && q8 + t < n) ? A[p * lda + q8 + t] : 0.0f;
+        }
+        presplit_chunk(hi_t, lo_t, p, q8, kbs, v);
+    }
 }
 
-// A as the operand of A^T W: p = A's column j, q = A's row i; 32 x 32
-// element blocks through shared memory.
+// A as the operand of A^T W: p = A's column j, q = A's row i. 64 x 64 element
+// blocks of A through shared memory (read along j), each thread then writes
+// the chunks of 8 consecutive i of one column j.
 __global__ void __launch_bounds__(256)
     mm_tc_presplit_kernel(const float *__restrict__ A, int64_t m, int64_t n, int64_t lda,
                           int64_t Qp, int64_t Pp, int64_t kbs, unsigned char *__restrict__ hi_t,
                           unsigned char *__restrict__ lo_t)
 {
-    __shared__ float tile[32][33];
-    const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
-    for (int r = ty; r < 32; r += 8) {
-        const int64_t i = i0 + r, j = j0 + tx;
-        tile[r][tx] = (i < m && j < n) ? A[i * lda + j] : 0.0f;
+    __shared__ float tile[64][65];
+    const int64_t i0 = (int64_t)blockIdx.y * 64, j0 = (int64_t)blockIdx.x * 64;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < 64 * 64; e += 256) {
+        const int r = e >> 6, c = e & 63;
+        const int64_t i = i0 + r, j = j0 + c;
+        tile[r][c] = (i < m && j < n) ? A[i * lda + j] : 0.0f;
     }
     __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-        const int64_t p = j0 + r, q = i0 + tx;
-        if (p < Pp && q < Qp)
-            presplit_store(hi_t, lo_t, p, q, kbs, tile[tx][r]);
+    for (int e = tid; e < 64 * 8; e += 256) {   // (column c, chunk g of 8 rows)
+        const int c = e >> 3, g = e & 7;
+        const int64_t p = j0 + c, q8 = i0 + 8 * g;
+        if (p < Pp && q8 < Qp) {
+            float v[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                v[t] = tile[8 * g + t][c];
+            presplit_chunk(hi_t, lo_t, p, q8, kbs, v);
+        }
     }
 }
 
@@ -1280,16 +1305,18 @@ nmf_status launch_mm_tc_presplit_make(const float *A, int64_t m, int64_t n, int6
     const int64_t Pp = cdiv(P, TC_BM) * TC_BM, Qp = cdiv(Q, TC_BK) * TC_BK;
     unsigned char *h = static_cast<unsigned char *>(hi), *l = static_cast<unsigned char *>(lo);
     if (trans) {
-        const dim3 grid((unsigned)cdiv(Pp, 32), (unsigned)cdiv(Qp, 32));
+        const dim3 grid((unsigned)cdiv(Pp, 64), (unsigned)cdiv(Qp, 64));
         if (grid.y > 65535u)
             return NMF_ERR_INVALID_ARG;
-        mm_tc_presplit_kernel<<<grid, dim3(32, 8), 0, s>>>(A, m, n, lda, Qp, Pp, Qp / TC_BK, h, l);
+        mm_tc_presplit_kernel<<<grid, 256, 0, s>>>(A, m, n, lda, Qp, Pp, Qp / TC_BK, h, l);
         NMF_LAUNCHED("mm_tc_presplit_kernel");
     } else {
-        const dim3 grid((unsigned)Pp, (unsigned)cdiv(Qp, 256));
-        if (Pp > 2147483647 || cdiv(Qp, 256) > 65535)
+        if ((reinterpret_cast<uintptr_t>(A) & 15) || (lda % 4))
             return NMF_ERR_INVALID_ARG;
-        mm_tc_presplit_rows_kernel<<<grid, 256, 0, s>>>(A, m, n, lda, Qp, Pp, Qp / TC_BK, h, l);
+        const int64_t blocks = cdiv(Pp * (Qp / 8), 256);
+        const int64_t cap = 16 * (int64_t)sm_count();
+        mm_tc_presplit_rows_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(
+            A, m, n, lda, Qp, Pp, Qp / TC_BK, h, l);
         NMF_LAUNCHED("mm_tc_presplit_rows_kernel");
     }
     return NMF_OK;
