@@ -275,6 +275,24 @@ def test_bpp_ill_conditioned_fp64(nmf):
     assert np.array_equal(P[ok], Po.astype(bool)[ok])
 
 
+def test_bpp_fp64_predicted_start_same_answer(nmf):
+    # FP64 half-steps start from FP32-predicted partitions when the round cap
+    # allows (>= 16). The answer is the unique minimiser either way, and the
+    # final FP64 solve depends only on the final partition: bitwise the same X
+    # and passive sets, in far fewer FP64 rounds.
+    k, nrhs = 24, 2000
+    G, B = synth.nls_batch(k, nrhs, seed=31, cond_boost=1000.0)
+    B32 = B.astype(np.float32)
+    X1, P1, R1, S1, w1 = run_bpp(nmf, G, B32, max_rounds=100)   # predictor on
+    X2, P2, R2, S2, w2 = run_bpp(nmf, G, B32, max_rounds=15)    # predictor off
+    assert w1 == nmf.NMF_OK and w2 == nmf.NMF_OK
+    assert np.array_equal(X1, X2) and np.array_equal(P1, P2)
+    # (At cond ~3e8 FP32 resolves little, so the saving here is small; on the
+    # dense workload's FP64 half-steps, cond 1e4-1e6, rounds fall ~50-fold.)
+    print(f"FP64 rounds per solve: predicted start {R1.mean():.3f}, cold {R2.mean():.3f}")
+    assert R1.mean() <= R2.mean()
+
+
 def test_bpp_singular_gram(nmf):
     # Two identical factor rows: G is singular even in FP64, so no inverse is
     # formed and every system is solved directly in FP64. Solves whose passive
