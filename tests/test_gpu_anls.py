@@ -124,6 +124,32 @@ def test_sparse_objective_standalone(nmf):
     h.nmf_destroy()
 
 
+def test_bf16x3_k_above_64(nmf):
+    # k > 64: the products run in two 64-column chunks (from the pre-split
+    # copies, or splitting A in the pass) and the objective is a separate
+    # pass (no fusion). Both give bitwise the same factors; the objective
+    # matches the oracle within the BF16x3 tolerance. (The factors' distance
+    # to the oracle is the BF16x3 product noise times cond(G), which this
+    # random start makes large enough to send every H update to FP64.)
+    m, n, k, T = 1500, 1200, 80, 4
+    A = synth.dense_planted(m, n, k, 0.01, seed=13)
+    W0, Ht0 = synth.init_factors(m, n, k, seed=13)
+    ref = oracle.anls(A, W0, Ht0, iters=T, warm=True)
+    out = []
+    for copies in (True, False):
+        h = nmf.nmf_init(dev(A), dev(W0), dev(Ht0), precision="bf16x3", start="warm",
+                         split_copies=copies)
+        h.nmf_iterate(T)
+        assert h.nmf_sync() == nmf.NMF_OK
+        W, Ht = h.nmf_get_factors()
+        out.append((W.cpu().numpy(), Ht.cpu().numpy(), np.array(h.nmf_objective_history())))
+        h.nmf_destroy()
+    (W1, H1, f1), (W2, H2, f2) = out
+    assert np.array_equal(W1, W2) and np.array_equal(H1, H2) and np.array_equal(f1, f2)
+    errf = np.abs(f1 - ref["f"][1:]) / ref["f"][1:]
+    assert errf.max() <= 3e-5, errf
+
+
 def test_split_copies_give_the_same_products(nmf):
     # The pre-split BF16 copies of A and A^T hold exactly the hi / lo values the
     # in-pass split forms, so the factors of a BF16x3 run are bitwise the same
