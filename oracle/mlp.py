@@ -3,8 +3,8 @@
 TEST INFRASTRUCTURE ONLY: imported by tests/ and nothing on the product path.
 The paper has no counterpart: the proposal only chooses the starting partition
 of block principal pivoting (Sec. 4.2), which then runs to the KKT point of
-Eq. 4 as always, so the answer of every solve is unchanged and BPP stays the
-judge of each proposal. Plain numpy in FP64, one line per step of the
+Eq. 4 as always, so the answer of every solve is unchanged and BPP's own
+tests decide whether each proposal is optimal. Plain numpy in FP64, one line per step of the
 definition below; the weights are used after rounding to BF16, as the GPU
 uses them.
 

@@ -391,7 +391,7 @@ __host__ __device__ inline size_t mats_bytes(int k, int mode)
 // FP64 solves. KW = index slots per lane (k <= 32 KW); PT = compact-system
 // rows per lane (pmax <= 32 PT). The kernel of each MODE returns at once
 // unless the prep kernel chose that mode, so the host never waits for the
-// verdict. With list_pass set (MODE 1 only) it is the second pass of mode 0:
+// decision. With list_pass set (MODE 1 only) it is the second pass of mode 0:
 // it re-solves, from their starting partitions, the right-hand sides that the
 // FP32 kernel deferred (all of them if more than DEFER_CAP were).
 template <int KW, int PT, int MODE>

@@ -1,7 +1,7 @@
 // Learned passive-set proposal for block principal pivoting (no counterpart in
 // the paper: it only picks the starting partition of the BPP solves of Eq. 3,
 // Sec. 4.2, which then run to the KKT point of Eq. 4 as before, so every
-// answer is unchanged and BPP judges every proposal).
+// answer is unchanged and BPP's own tests decide on every proposal).
 //
 // Per right-hand side (G, g, x_p = the previous iterate of that factor row):
 //   d_i = sqrt(G_ii) (1 where G_ii <= 0), s = max_i |g_i| / d_i (1 if 0),
