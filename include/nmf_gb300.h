@@ -113,7 +113,8 @@ typedef struct nmf_nls_desc {
     int64_t nrhs;              /* number of right-hand sides (>= 0) */
     const double *G;           /* device, k x k float64, symmetric PSD */
     const float *B;            /* device, nrhs x k float32 (one RHS per row) */
-    float *X;                  /* device, nrhs x k float32 output */
+    float *X;                  /* device, nrhs x k float32 output; must not
+                                  overlap B (NMF_ERR_INVALID_ARG) */
     const uint64_t *passive_in;/* device, nullable: nrhs x ceil(k/64) bitmasks
                                   (bit i of word i/64 set = index i passive);
                                   non-null selects a warm start */
@@ -130,14 +131,30 @@ typedef struct nmf_nls_desc {
 nmf_status nmf_nls_bpp(const nmf_nls_desc *d, void *stream);
 
 /* Launch-shape autotuner for the batched solve (an interface of this library,
- * no counterpart in the paper): times the solve kernel's candidate shapes
- * (warps per CTA x right-hand sides per grab of the work counter) on this
- * batch and keeps the fastest for d->k; every later solve of that k in the
- * process (nmf_nls_bpp, handles) uses it. All shapes give bit-identical
- * results. X receives the solution; passive_out, rounds_out and status_out
- * are not written. Synchronises `stream`; *warps and *chunk (host, nullable)
+ * no counterpart in the paper): times the solve kernels' candidate shapes
+ * (warps per CTA x right-hand sides per grab of the work counter, with and
+ * without the group-tile pass for the all-passive group) on this batch and
+ * keeps the fastest for d->k; every later solve of that k in the process
+ * (nmf_nls_bpp, handles) uses it. All shapes give bit-identical results. X
+ * receives the solution; passive_out, rounds_out and status_out are not
+ * written. Synchronises `stream`; *warps, *chunk and *group (host, nullable)
  * get the chosen shape. */
-nmf_status nmf_nls_bpp_tune(const nmf_nls_desc *d, void *stream, int32_t *warps, int32_t *chunk);
+nmf_status nmf_nls_bpp_tune(const nmf_nls_desc *d, void *stream, int32_t *warps, int32_t *chunk,
+                            int32_t *group);
+
+/* Sets the launch shape of every later solve of this k in the process, as the
+ * tuner would (an interface of this library; results do not depend on it):
+ * warps per CTA 1..16 (the FP64 solves use at most 8), right-hand sides per
+ * grab of the work counter 1..1024, and group = 1 to run the group-tile pass
+ * first in FP32 half-steps (right-hand sides whose first candidate partition
+ * is all usable indices are solved together by tile products with the
+ * preparation's inverse; the rest go to the per-warp solves), 0 not to.
+ * Default {8, 8, 1}. Host-side only; NMF_ERR_INVALID_ARG outside these
+ * ranges. */
+nmf_status nmf_nls_bpp_set_shape(int32_t k, int32_t warps, int32_t chunk, int32_t group);
+
+/* Reads the launch shape solves of this k use (host pointers, nullable). */
+nmf_status nmf_nls_bpp_get_shape(int32_t k, int32_t *warps, int32_t *chunk, int32_t *group);
 
 /* Allocation-free variant of nmf_nls_bpp (no counterpart in the paper; an
  * interface of this library). Same arguments, computation and results as

@@ -114,7 +114,11 @@ _c_csr_transpose = _sig("nmf_csr_transpose", [_P, _P, _P, _I64, _I64, _I64, _P, 
 _c_nls_bpp = _sig("nmf_nls_bpp", [ctypes.POINTER(nmf_nls_desc), _P])
 _c_nls_bpp_noalloc = _sig("nmf_nls_bpp_noalloc", [ctypes.POINTER(nmf_nls_desc), _P])
 _c_nls_bpp_tune = _sig("nmf_nls_bpp_tune", [ctypes.POINTER(nmf_nls_desc), _P,
-                                            ctypes.POINTER(_I32), ctypes.POINTER(_I32)])
+                                            ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                                            ctypes.POINTER(_I32)])
+_c_nls_bpp_set_shape = _sig("nmf_nls_bpp_set_shape", [_I32, _I32, _I32, _I32])
+_c_nls_bpp_get_shape = _sig("nmf_nls_bpp_get_shape", [_I32, ctypes.POINTER(_I32),
+                                                      ctypes.POINTER(_I32), ctypes.POINTER(_I32)])
 _c_objective_dense = _sig("nmf_objective_dense",
                           [_P, _I64, _I64, _I64, _P, _P, _I32, _I32,
                            ctypes.POINTER(ctypes.c_double), _P])
@@ -145,7 +149,8 @@ _c_mlp_train = _sig("nmf_mlp_train", [_P, _P, _P, _I64, _I64, ctypes.c_float, _P
 _c_set_proposal = _sig("nmf_set_proposal", [_P, _P, _I32, _I32, _I64, ctypes.c_float])
 
 EXPORTED = ["nmf_status_str", "nmf_gram", "nmf_mm_dense", "nmf_mm_csr", "nmf_csr_transpose",
-            "nmf_nls_bpp", "nmf_nls_bpp_noalloc", "nmf_nls_bpp_tune", "nmf_objective_dense", "nmf_init", "nmf_iterate", "nmf_sync",
+            "nmf_nls_bpp", "nmf_nls_bpp_noalloc", "nmf_nls_bpp_tune", "nmf_nls_bpp_set_shape",
+            "nmf_nls_bpp_get_shape", "nmf_objective_dense", "nmf_init", "nmf_iterate", "nmf_sync",
             "nmf_objective", "nmf_objective_history", "nmf_get_factors", "nmf_set_factors",
             "nmf_get_passive", "nmf_get_stats", "nmf_set_timing", "nmf_set_graph", "nmf_destroy",
             "nmf_mlp_param_count", "nmf_mlp_create", "nmf_mlp_get_params", "nmf_mlp_destroy",
@@ -303,8 +308,9 @@ def nmf_nls_bpp_noalloc(G: torch.Tensor, B: torch.Tensor, passive_in: torch.Tens
 
 def nmf_nls_bpp_tune(G: torch.Tensor, B: torch.Tensor, passive_in: torch.Tensor | None = None,
                      max_rounds: int = 100, stream=None):
-    """Autotune the solve kernel's launch shape for k on this batch (kept for
-    every later solve of that k). Returns (warps per CTA, RHS per grab, X)."""
+    """Autotune the solve kernels' launch shape for k on this batch (kept for
+    every later solve of that k). Returns (warps per CTA, RHS per grab,
+    group-tile pass on, X)."""
     _dev(G, torch.float64, "G")
     _dev(B, torch.float32, "B")
     nrhs, k = B.shape
@@ -313,10 +319,23 @@ def nmf_nls_bpp_tune(G: torch.Tensor, B: torch.Tensor, passive_in: torch.Tensor 
         _dev(passive_in, torch.int64, "passive_in")
     d = nmf_nls_desc(k, nrhs, _ptr(G), _ptr(B), _ptr(X), _ptr(passive_in), None, None, None,
                      max_rounds)
-    w, c = _I32(0), _I32(0)
-    _check(_c_nls_bpp_tune(ctypes.byref(d), _stream(stream), ctypes.byref(w), ctypes.byref(c)),
-           "nmf_nls_bpp_tune")
-    return w.value, c.value, X
+    w, c, g = _I32(0), _I32(0), _I32(0)
+    _check(_c_nls_bpp_tune(ctypes.byref(d), _stream(stream), ctypes.byref(w), ctypes.byref(c),
+                           ctypes.byref(g)), "nmf_nls_bpp_tune")
+    return w.value, c.value, g.value, X
+
+
+def nmf_nls_bpp_set_shape(k: int, warps: int, chunk: int, group: int) -> None:
+    """Launch shape of every later solve of this k (results do not depend on it)."""
+    _check(_c_nls_bpp_set_shape(k, warps, chunk, group), "nmf_nls_bpp_set_shape")
+
+
+def nmf_nls_bpp_get_shape(k: int) -> tuple[int, int, int]:
+    """(warps per CTA, right-hand sides per grab, group-tile pass on) for k."""
+    w, c, g = _I32(0), _I32(0), _I32(0)
+    _check(_c_nls_bpp_get_shape(k, ctypes.byref(w), ctypes.byref(c), ctypes.byref(g)),
+           "nmf_nls_bpp_get_shape")
+    return w.value, c.value, g.value
 
 
 def _nls_bpp(fn, name, G, B, passive_in, max_rounds, outputs, stream):

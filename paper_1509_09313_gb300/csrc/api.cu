@@ -145,6 +145,8 @@ extern "C" nmf_status nmf_nls_bpp(const nmf_nls_desc *d, void *stream)
         return NMF_ERR_INVALID_ARG;
     if (d->nrhs > 0 && (!d->B || !d->X))
         return NMF_ERR_INVALID_ARG;
+    if (ranges_overlap(d->B, d->X, sizeof(float) * (size_t)d->nrhs * d->k))
+        return NMF_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
     TempBuf w(s), st(s);
     NMF_CUDA(w.alloc(bpp_work_bytes(d->k)));
@@ -160,24 +162,40 @@ extern "C" nmf_status nmf_nls_bpp(const nmf_nls_desc *d, void *stream)
 }
 
 extern "C" nmf_status nmf_nls_bpp_tune(const nmf_nls_desc *d, void *stream, int32_t *warps,
-                                       int32_t *chunk)
+                                       int32_t *chunk, int32_t *group)
 {
     if (!d || bad_k(d->k) || d->nrhs < 1 || d->max_rounds < 0 || !d->G || !d->B || !d->X)
+        return NMF_ERR_INVALID_ARG;
+    if (ranges_overlap(d->B, d->X, sizeof(float) * (size_t)d->nrhs * d->k))
         return NMF_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
     TempBuf w(s), st(s);
     NMF_CUDA(w.alloc(bpp_work_bytes(d->k)));
     NMF_CUDA(st.alloc(sizeof(BppStats)));
     NMF_CUDA(cudaMemsetAsync(st.p, 0, sizeof(BppStats), s));
-    int wv = 0, cv = 0;
+    int wv = 0, cv = 0, gv = 0;
     NMF_TRY(bpp_tune(d->k, d->nrhs, d->G, d->B, d->X, d->passive_in, d->max_rounds, w.p,
-                     static_cast<BppStats *>(st.p), s, &wv, &cv));
+                     static_cast<BppStats *>(st.p), s, &wv, &cv, &gv));
     NMF_CUDA(cudaStreamSynchronize(s));
     if (warps)
         *warps = wv;
     if (chunk)
         *chunk = cv;
+    if (group)
+        *group = gv;
     return NMF_OK;
+}
+
+extern "C" nmf_status nmf_nls_bpp_set_shape(int32_t k, int32_t warps, int32_t chunk,
+                                            int32_t group)
+{
+    return bpp_set_shape(k, warps, chunk, group);
+}
+
+extern "C" nmf_status nmf_nls_bpp_get_shape(int32_t k, int32_t *warps, int32_t *chunk,
+                                            int32_t *group)
+{
+    return bpp_get_shape(k, warps, chunk, group);
 }
 
 extern "C" nmf_status nmf_objective_dense(const float *A, int64_t m, int64_t n, int64_t lda,

@@ -740,6 +740,11 @@ nmf_status launch_solve(const SolveParams &P, int list_pass, cudaStream_t s)
 template <int KW>
 nmf_status launch_modes(const SolveParams &P, cudaStream_t s)
 {
+    // Mode 0 (FP32): the group-tile pass for the all-passive group first,
+    // then the per-warp solves of what it left.
+    if (P.group) {
+        NMF_TRY(launch_group32(P, s));
+    }
     NMF_TRY(launch_solve32(P, s));
     // Mode 1 (FP64): an FP32 pass first predicts each right-hand side's
     // partition into pout, and the FP64 solves start from it (their answer
@@ -748,6 +753,7 @@ nmf_status launch_modes(const SolveParams &P, cudaStream_t s)
     if (P.pout && P.max_rounds >= 2 * PREDICT_ROUNDS) {   // (a tight cap keeps its meaning)
         SolveParams Q = P;
         Q.predict = 1;
+        Q.group = 0;
         NMF_TRY(launch_solve32(Q, s));
         P1.pin = P.pout;
     }
@@ -762,11 +768,13 @@ size_t bpp_work_bytes(int k) { return layout(k).total; }
 
 namespace {
 
-// Launch shape of the solve kernel per k (warps per CTA, right-hand sides per
-// grab of the work counter): {8, 8} until bpp_tune has measured the batch.
-// Every shape computes the same results (each right-hand side is one warp's).
+// Launch shape of the solve kernels per k (warps per CTA, right-hand sides per
+// grab of the work counter, whether the group-tile pass runs first):
+// {8, 8, on} until bpp_tune has measured the batch or the caller set one.
+// Every shape computes the same results: a right-hand side's arithmetic does
+// not depend on where it runs.
 struct BppShape {
-    int warps = BPP_WARPS, chunk = 8;
+    int warps = BPP_WARPS, chunk = 8, group = 1;
 };
 std::mutex g_shape_mu;
 BppShape g_shape[NMF_MAX_K + 1];
@@ -807,6 +815,7 @@ SolveParams solve_params(int k, int64_t nrhs, const double *G, const float *B, f
     const BppShape sh = shape_for(k);
     P.warps = sh.warps;
     P.chunk = sh.chunk;
+    P.group = sh.group;
     return P;
 }
 
@@ -860,9 +869,10 @@ nmf_status launch_bpp_solve(int k, int64_t nrhs, const double *G, const float *B
 // the solution.
 nmf_status bpp_tune(int k, int64_t nrhs, const double *G, const float *B, float *X,
                     const uint64_t *passive_in, int max_rounds, void *work, BppStats *stats_dev,
-                    cudaStream_t s, int *warps_out, int *chunk_out)
+                    cudaStream_t s, int *warps_out, int *chunk_out, int *group_out)
 {
-    static const BppShape cand[] = {{16, 4}, {16, 8}, {8, 1}, {8, 4}, {8, 8}, {8, 32}, {4, 16}};
+    static const BppShape cand[] = {{16, 4, 1}, {16, 8, 1}, {8, 1, 1},  {8, 4, 1},
+                                    {8, 8, 1},  {8, 32, 1}, {4, 16, 1}, {8, 8, 0}};
     NMF_TRY(launch_bpp_prep(k, G, work, stats_dev, s));
     SolveParams P = solve_params(k, nrhs, G, B, X, passive_in, nullptr, nullptr, nullptr,
                                  max_rounds, work, stats_dev);
@@ -878,6 +888,7 @@ nmf_status bpp_tune(int k, int64_t nrhs, const double *G, const float *B, float 
     for (const BppShape &c : cand) {
         P.warps = c.warps;
         P.chunk = c.chunk;
+        P.group = c.group;
         float ms = 0.0f;
         for (int rep = 0; rep < 2 && st == NMF_OK; ++rep) {
             // The prep kernel resets the work counter; re-run it per solve.
@@ -909,6 +920,34 @@ nmf_status bpp_tune(int k, int64_t nrhs, const double *G, const float *B, float 
         *warps_out = best.warps;
     if (chunk_out)
         *chunk_out = best.chunk;
+    if (group_out)
+        *group_out = best.group;
+    return NMF_OK;
+}
+
+nmf_status bpp_set_shape(int k, int warps, int chunk, int group)
+{
+    if (k < 1 || k > NMF_MAX_K || warps < 1 || warps > 16 || chunk < 1 || chunk > 1024 ||
+        (group != 0 && group != 1))
+        return NMF_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_shape_mu);
+    g_shape[k].warps = warps;
+    g_shape[k].chunk = chunk;
+    g_shape[k].group = group;
+    return NMF_OK;
+}
+
+nmf_status bpp_get_shape(int k, int *warps, int *chunk, int *group)
+{
+    if (k < 1 || k > NMF_MAX_K)
+        return NMF_ERR_INVALID_ARG;
+    const BppShape sh = shape_for(k);
+    if (warps)
+        *warps = sh.warps;
+    if (chunk)
+        *chunk = sh.chunk;
+    if (group)
+        *group = sh.group;
     return NMF_OK;
 }
 

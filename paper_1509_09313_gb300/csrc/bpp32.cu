@@ -254,6 +254,9 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
     constexpr int PT = (KW + 1) / 2;
     if (P.predict ? P.flags[0] != 1 : P.flags[0] != 0)
         return;
+    const bool group = P.group && !P.predict;
+    if (group && P.counters[CNT_PENDING] == 0)
+        return;   // the group-tile pass solved them all
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int k = P.k, k4 = (k + 3) & ~3;
     const int max_rounds = P.predict ? PREDICT_ROUNDS : P.max_rounds;
@@ -335,6 +338,22 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
                             f = (wv >> (i & 63)) & 1ull;
                         }
                         inF[s] = f && usable[s];
+                    }
+                }
+                if (group && nU > 0) {
+                    // The group-tile pass took this right-hand side when its
+                    // first candidate partition is all of U (the same test),
+                    // and marked it only if it could not finish it.
+                    bool out = false;
+#pragma unroll
+                    for (int s = 0; s < KW; ++s)
+                        out |= usable[s] && !(P.pin ? inF[s] : (y[s] < -ytol * dsq[s]));
+                    if (!__any_sync(FULL, out) && (P.pin || max_rounds >= 1)) {
+                        uint32_t mark = 0;
+                        if (lane == 0)
+                            mark = reinterpret_cast<const uint32_t *>(P.X)[j * k];
+                        if (__shfl_sync(FULL, mark, 0) != GROUP_PENDING)
+                            continue;   // solved by the group-tile pass
                     }
                 }
 

@@ -18,7 +18,18 @@ constexpr float FEAS_TOL32 = 9.5367431640625e-07f;  // 2^-20
 constexpr int DEFER_CAP = 512;
 
 // Work counters (one array of 64-bit words, zeroed by the prep kernel).
-enum Counter { CNT_WORK = 0, CNT_DEFERRED = 1, CNT_DEFER_WORK = 2, CNT_PREDICT = 3, CNT_WORDS = 4 };
+enum Counter {
+    CNT_WORK = 0,
+    CNT_DEFERRED = 1,
+    CNT_DEFER_WORK = 2,
+    CNT_PREDICT = 3,
+    CNT_PENDING = 4,   // right-hand sides the group-tile pass left to the per-warp kernel
+    CNT_WORDS = 5
+};
+
+// Bits of the NaN the group-tile pass writes to X[j][0] of a right-hand side
+// it leaves to the per-warp kernel (a solved X never holds a NaN).
+constexpr uint32_t GROUP_PENDING = 0x7fc0a5a5u;
 
 // Rounds allowed to the FP32 predictor of an FP64 half-step's partitions.
 constexpr int PREDICT_ROUNDS = 8;
@@ -44,6 +55,9 @@ struct SolveParams {
     // passive sets (pout) for the FP64 solves to start from; no X, rounds,
     // status or statistics, at most PREDICT_ROUNDS rounds, its own counter.
     int predict;
+    // group = 1: the group-tile pass ran first; the per-warp kernel solves
+    // only the right-hand sides it marked GROUP_PENDING.
+    int group;
 };
 
 __device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
@@ -59,6 +73,10 @@ __device__ __forceinline__ T warp_max(T v)
 // FP32 solve kernel (mode 0): launched for every half-step, returns at once
 // unless the prep kernel chose mode 0.
 nmf_status launch_solve32(const SolveParams &P, cudaStream_t s);
+
+// Group-tile pass for the all-passive group (mode 0; returns at once
+// otherwise). X must not overlap B.
+nmf_status launch_group32(const SolveParams &P, cudaStream_t s);
 
 }  // namespace bpp
 }  // namespace nmf

@@ -54,6 +54,8 @@ extern "C" nmf_status nmf_nls_bpp_noalloc(const nmf_nls_desc *d, void *stream)
         return NMF_ERR_INVALID_ARG;
     if (d->nrhs > 0 && (!d->B || !d->X))
         return NMF_ERR_INVALID_ARG;
+    if (nmf::ranges_overlap(d->B, d->X, sizeof(float) * (size_t)d->nrhs * d->k))
+        return NMF_ERR_INVALID_ARG;
     const size_t work = nmf::bpp_work_bytes(d->k);
     const size_t stats_off = (work + 255) & ~size_t(255);
     if (stats_off + sizeof(nmf::BppStats) > NMF_NOALLOC_SCRATCH_BYTES)

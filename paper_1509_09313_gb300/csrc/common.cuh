@@ -55,6 +55,13 @@ inline int sm_count()
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// True when [a, a + bytes) and [b, b + bytes) share a byte.
+inline bool ranges_overlap(const void *a, const void *b, size_t bytes)
+{
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return bytes > 0 && x < y + bytes && y < x + bytes;
+}
+
 // ---------------------------------------------------------------------------
 // Internal launchers (all asynchronous on `s`).
 // ---------------------------------------------------------------------------
@@ -139,7 +146,10 @@ nmf_status launch_bpp_prep(int k, const double *G, void *work, BppStats *stats_d
 // for k (used by every later solve of that k); X receives the solution.
 nmf_status bpp_tune(int k, int64_t nrhs, const double *G, const float *B, float *X,
                     const uint64_t *passive_in, int max_rounds, void *work, BppStats *stats_dev,
-                    cudaStream_t s, int *warps_out, int *chunk_out);
+                    cudaStream_t s, int *warps_out, int *chunk_out, int *group_out);
+// The launch shape every later solve of k uses (see nmf_nls_bpp_set_shape).
+nmf_status bpp_set_shape(int k, int warps, int chunk, int group);
+nmf_status bpp_get_shape(int k, int *warps, int *chunk, int *group);
 nmf_status launch_bpp_solve(int k, int64_t nrhs, const double *G, const float *B, float *X,
                             const uint64_t *passive_in, uint64_t *passive_out, int32_t *rounds_out,
                             int8_t *status_out, int max_rounds, void *work, BppStats *stats_dev,

@@ -58,3 +58,40 @@ def test_python_binding_exports_same_names():
     src = open(os.path.join(ROOT, "paper_1509_09313_gb300", "__init__.py")).read()
     for n in declared_functions():
         assert n in src, n
+
+
+def test_launch_shape_set_and_get(lib):
+    # Host-only state: the shape later solves of k use.
+    I = ctypes.c_int32
+    lib.nmf_nls_bpp_set_shape.argtypes = [I, I, I, I]
+    lib.nmf_nls_bpp_get_shape.argtypes = [I] + [ctypes.POINTER(I)] * 3
+    w, c, g = I(0), I(0), I(0)
+    assert lib.nmf_nls_bpp_get_shape(50, ctypes.byref(w), ctypes.byref(c), ctypes.byref(g)) == 0
+    assert (w.value, c.value, g.value) == (8, 8, 1)        # the default
+    assert lib.nmf_nls_bpp_set_shape(50, 16, 4, 0) == 0
+    lib.nmf_nls_bpp_get_shape(50, ctypes.byref(w), ctypes.byref(c), ctypes.byref(g))
+    assert (w.value, c.value, g.value) == (16, 4, 0)
+    for bad in [(0, 8, 8, 1), (129, 8, 8, 1), (50, 0, 8, 1), (50, 17, 8, 1),
+                (50, 8, 0, 1), (50, 8, 1025, 1), (50, 8, 8, 2), (50, 8, 8, -1)]:
+        assert lib.nmf_nls_bpp_set_shape(*bad) == 1, bad
+    assert lib.nmf_nls_bpp_get_shape(0, None, None, None) == 1
+    assert lib.nmf_nls_bpp_set_shape(50, 8, 8, 1) == 0
+
+
+class NlsDesc(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("nrhs", ctypes.c_int64), ("G", ctypes.c_void_p),
+                ("B", ctypes.c_void_p), ("X", ctypes.c_void_p), ("passive_in", ctypes.c_void_p),
+                ("passive_out", ctypes.c_void_p), ("rounds_out", ctypes.c_void_p),
+                ("status_out", ctypes.c_void_p), ("max_rounds", ctypes.c_int32)]
+
+
+@pytest.mark.parametrize("fn", ["nmf_nls_bpp", "nmf_nls_bpp_noalloc"])
+def test_nls_rejects_overlapping_x_and_b(lib, fn):
+    # X must not overlap B: checked on the host before anything is launched
+    # (the pointers below are never dereferenced).
+    f = getattr(lib, fn)
+    f.argtypes = [ctypes.POINTER(NlsDesc), ctypes.c_void_p]
+    k, nrhs = 10, 100
+    for x_off in (0, 4 * k * nrhs - 4, -(4 * k * nrhs - 4)):
+        d = NlsDesc(k, nrhs, 0x10000, 0x200000, 0x200000 + x_off, None, None, None, None, 10)
+        assert f(ctypes.byref(d), None) == 1, x_off

@@ -315,6 +315,90 @@ def test_bpp_singular_gram(nmf):
     assert (np.abs((X * Y)[good]).sum(axis=1) <= 1e-9 * (scale[good] * np.abs(X[good]).max(axis=1) + 1e-30)).all()
 
 
+class shape_of:
+    """Sets the launch shape of solves of k inside a with-block, then restores it."""
+
+    def __init__(self, nmf, k, warps, chunk, group):
+        self.nmf, self.k, self.new = nmf, k, (warps, chunk, group)
+
+    def __enter__(self):
+        self.old = self.nmf.nmf_nls_bpp_get_shape(self.k)
+        self.nmf.nmf_nls_bpp_set_shape(self.k, *self.new)
+
+    def __exit__(self, *exc):
+        self.nmf.nmf_nls_bpp_set_shape(self.k, *self.old)
+
+
+def group_cases(k):
+    """Batches that reach every branch of the group-tile pass: all solutions
+    positive (every right-hand side in the all-passive group, cold and warm),
+    non-negative right-hand sides with mixed signs in the solution (in the
+    group, then left to the per-warp solves), signed right-hand sides (few in
+    the group), non-finite rows, round caps 0 and 1, a zero diagonal (an
+    unusable index) and an FP64 half-step (the pass stays off)."""
+    nrhs = 1237                                   # not a multiple of the 32- or 64-wide tiles
+    rng = np.random.default_rng(900 + k)
+    G, _ = synth.nls_batch(k, 1, seed=800 + k)
+    Xt = rng.uniform(0.1, 1.0, (nrhs, k))
+    Bpos = (Xt @ G).astype(np.float32)
+    _, Bu = synth.nls_batch(k, nrhs, seed=800 + k, signed_rhs=False)
+    _, Bs = synth.nls_batch(k, nrhs, seed=800 + k)
+    nanB = Bpos.copy()
+    nanB[[0, 5, 64, 1236], min(3, k - 1)] = np.nan
+    all_in = np.ones((nrhs, k), bool)
+    part = all_in.copy()
+    part[::3, 0] = False
+    Gz = G.copy()
+    z = min(2, k - 1)
+    Gz[z, :] = 0.0
+    Gz[:, z] = 0.0
+    Bz = Bpos.copy()
+    Bz[:, z] = 0.0
+    Gi, Bi = synth.nls_batch(k, nrhs, seed=700 + k, cond_boost=1000.0)
+    cases = [("positive", G, Bpos, None, 100), ("positive-warm", G, Bpos, all_in, 100),
+             ("warm-partial", G, Bpos, part, 100), ("unsigned", G, Bu.astype(np.float32), None, 100),
+             ("signed", G, Bs.astype(np.float32), None, 100), ("nonfinite", G, nanB, None, 100),
+             ("cap0", G, Bpos, None, 0), ("cap1", G, Bu.astype(np.float32), None, 1),
+             ("fp64", Gi, Bi.astype(np.float32), None, 100)]
+    if k > 1:
+        cases.append(("zero-diagonal", Gz, Bz, None, 100))
+    return cases
+
+
+@pytest.mark.parametrize("k", [1, 5, 10, 33, 50, 64, 65, 100, 128])
+def test_bpp_group_pass_bitwise_equal(nmf, k):
+    # The group-tile pass forms each entry with the same operations in the same
+    # order as the per-warp kernel: the same X bits, passive sets, rounds and
+    # statuses with the pass on or off, on every path.
+    for name, G, B32, warm, cap in group_cases(k):
+        pin = None if warm is None else nmf.bool_to_passive(torch.from_numpy(warm)).numpy()
+        outs = []
+        for group in (0, 1):
+            with shape_of(nmf, k, 8, 8, group):
+                outs.append(run_bpp(nmf, G, B32, passive_in=pin, max_rounds=cap))
+        (X0, P0, R0, S0, w0), (X1, P1, R1, S1, w1) = outs
+        print(f"k={k} {name}: statuses {np.bincount(S0.astype(np.int64))} rounds {R0.mean():.2f}")
+        assert np.array_equal(X1, X0, equal_nan=True), name
+        assert np.array_equal(P1, P0) and np.array_equal(R1, R0), name
+        assert np.array_equal(S1, S0) and w1 == w0, name
+        if name == "positive":   # every solve in the group: one full exchange, all passive
+            assert (R1 == 1).all() and (S1 == 0).all() and P1.all()
+
+
+def test_bpp_group_pass_matches_oracle(nmf):
+    # Positive solutions from a cold start: the group-tile pass solves every
+    # right-hand side; compare with the FP64 oracle.
+    k, nrhs = 40, 3000
+    rng = np.random.default_rng(5)
+    G, _ = synth.nls_batch(k, 1, seed=41)
+    B32 = (rng.uniform(0.1, 1.0, (nrhs, k)) @ G).astype(np.float32)
+    X, P, R, S, worst = run_bpp(nmf, G, B32)
+    Xo, Po, Ro, So, wo = oracle.bpp(G, B32.astype(np.float64))
+    assert worst == nmf.NMF_OK and (R == Ro).all() and np.array_equal(P, Po.astype(bool))
+    err = np.linalg.norm(X - Xo) / np.linalg.norm(Xo)
+    assert err <= 20 * np.linalg.cond(G) * 6e-8, err
+
+
 def test_bpp_empty_batch(nmf):
     G, B = synth.nls_batch(10, 1, seed=1)
     r = nmf.nmf_nls_bpp(dev(G), torch.empty((0, 10), dtype=torch.float32, device="cuda"))

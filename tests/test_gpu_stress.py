@@ -87,12 +87,12 @@ def test_stress_one_launch_million_rhs(nmf):
     R = r["rounds"][idx].cpu().numpy()
     assert (R[ok] == Ro[ok]).mean() >= 0.98
     # Autotuned launch shape for k = 100: same bits, timed again.
-    warps, chunk, Xt = nmf.nmf_nls_bpp_tune(G, B)
+    warps, chunk, group, Xt = nmf.nmf_nls_bpp_tune(G, B)
     assert torch.equal(Xt, r["X"])
     e0.record()
     r2 = nmf.nmf_nls_bpp(G, B)
     e1.record()
     torch.cuda.synchronize()
-    print(f"tuned shape: {warps} warps per CTA, {chunk} RHS per grab: "
+    print(f"tuned shape: {warps} warps per CTA, {chunk} RHS per grab, group pass {group}: "
           f"{e0.elapsed_time(e1):.2f} ms")
     assert torch.equal(r2["X"], r["X"]) and torch.equal(r2["passive"], r["passive"])
