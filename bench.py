@@ -45,6 +45,14 @@ WORKLOADS = {
 }
 # Sparse workloads: number of uniform position draws (duplicates merged).
 SPARSE_DRAWS = {"sparse-large": 20000000, "sparse-medium": 2000000}
+# The batched-NLS stress workload: one step is one nmf_nls_bpp call on the
+# whole batch (its metric is right-hand sides per second, not iterations).
+STRESS = "bpp-stress"
+STRESS_ROWS, STRESS_K, STRESS_NRHS = 200000, 100, 1000000
+STRESS_DESC = ("batched NLS: 1000000 right-hand sides, k=100; G = W^T W of W 200000x100 "
+               "U[0,1) with 30% zeros; b drawn as W^T a for a U[0,1)^200000 (CLT form)")
+STRESS_METRIC = "BPP right-hand sides/s"
+STRESS_CPU_SAMPLE = 300000
 SEED = 1509
 METRIC = "ANLS-BPP iterations/s"
 
@@ -194,8 +202,171 @@ def oracle_sample_sparse(m, n, k, draws, steps, warm: bool, csr, solver="bpp"):
     return 1.0 / (dt * scale), sample, orc.num_threads(), dt
 
 
+def stress_oracle_sample(G, B, n):
+    """The FP64 oracle (as it stands) on the first n right-hand sides of the
+    stress batch. Returns (right-hand sides per second, sample text, threads,
+    seconds)."""
+    import oracle
+    Gh = G.cpu().numpy()
+    Bs = B[:n].double().cpu().numpy()
+    oracle.bpp(Gh, Bs[:100])                    # warm-up
+    t0 = time.perf_counter()
+    oracle.bpp(Gh, Bs)
+    dt = time.perf_counter() - t0
+    return (n / dt, f"oracle BPP on the first {n} right-hand sides of the same batch",
+            oracle.num_threads(), dt)
+
+
+def run_stress_reference(args, world):
+    import torch
+
+    from synth import torch_gen
+    G, B = torch_gen.stress_batch_device(torch.device("cpu"), STRESS_ROWS, STRESS_K,
+                                         max(STRESS_CPU_SAMPLE // 10, 1000))
+    steps = max(1, args.steps)
+    total_n, total_s = 0, 0.0
+    for _ in range(steps):
+        v, sample, cores, dt = stress_oracle_sample(G, B, B.shape[0])
+        total_n += B.shape[0]
+        total_s += dt
+    value = total_n / total_s
+    line = {"impl": "reference", "metric": STRESS_METRIC, "value": value, "unit": "RHS/s",
+            "n_gpus": world, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * STRESS_NRHS / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": STRESS_DESC},
+            "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": cores, "kind": "oracle",
+                             "sample": sample + f", {steps} times"},
+            "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_stress(args, rank, world, local_rank):
+    """Times K nmf_nls_bpp calls on the stress batch (one call = one step)."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1509_09313_gb300 as nmf
+    from synth import torch_gen
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    k, nrhs = STRESS_K, STRESS_NRHS
+    t_gen = time.perf_counter()
+    G, B = torch_gen.stress_batch_device(dev, STRESS_ROWS, k, nrhs)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    r = None
+    for _ in range(args.warmup):
+        r = nmf.nmf_nls_bpp(G, B, max_rounds=args.max_rounds)
+    torch.cuda.synchronize()
+    barrier()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    l0 = nmf.nmf_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    nvtx = getattr(torch.cuda, "nvtx", None)
+    if nvtx is not None:
+        nvtx.range_push("timed")    # lets ncu select exactly the timed launches
+    for _ in range(args.steps):
+        r = nmf.nmf_nls_bpp(G, B, max_rounds=args.max_rounds)
+    if nvtx is not None:
+        nvtx.range_pop()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    launches = nmf.nmf_kernel_launches() - l0
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * nrhs * args.steps / (ms / 1000.0)
+
+    # Algorithmic work of the last call: per right-hand side and exchange
+    # round, 2|F|^2 + 2|F|(k - |F|) flops (a solve through a factor of G_FF
+    # and y = G x - g off F), |F| taken from the final passive set. Bytes: B
+    # in, X, passive sets, rounds and statuses out.
+    rounds = r["rounds"].double()
+    f = nmf.passive_to_bool(r["passive"], k).double().sum(dim=1)
+    flops = float((rounds * (2 * f * f + 2 * f * (k - f))).sum().item())
+    nbytes = 4.0 * nrhs * k * 2 + (8 + 4 + 1) * nrhs
+    step_s = ms / 1000.0 / args.steps
+    pk, pk_kind = peaks()
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = flops / step_s / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "kernel": "bpp_group_kernel",
+            "timed": "the whole nmf_nls_bpp call (all its kernels)",
+            "peak_source": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                           f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max clock)",
+            "achieved_gbs": nbytes / step_s / 1e9, "hbm_frac": nbytes / step_s / 1e9 / pk["hbm_gbs"],
+            "traffic": None}
+
+    e2e = None
+    if not args.no_e2e:
+        B_host = torch.empty((nrhs, k), dtype=torch.float32, pin_memory=True)
+        B_host.copy_(B)
+        X_host = torch.empty((nrhs, k), dtype=torch.float32, pin_memory=True)
+        B_dev = torch.empty_like(B)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            B_dev.copy_(B_host, non_blocking=True)
+            r2 = nmf.nmf_nls_bpp(G, B_dev, max_rounds=args.max_rounds)
+            X_host.copy_(r2["X"], non_blocking=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        barrier()
+        if world > 1:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * nrhs * args.steps / dt, "unit": "RHS/s",
+               "h2d_bytes_per_step": 4 * nrhs * k, "d2h_bytes_per_step": 4 * nrhs * k,
+               "note": "upload B, nmf_nls_bpp, download X, every step"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sample, cores, _ = stress_oracle_sample(G, B, STRESS_CPU_SAMPLE)
+        cpu = {"value": v, "unit": "RHS/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": STRESS_METRIC, "value": value, "unit": "RHS/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": STRESS_DESC, "seed": SEED,
+                           "launch_shape": list(nmf.nmf_nls_bpp_get_shape(k)),
+                           "l2": f"inputs larger than L2 (B = {4 * nrhs * k / 1e9:.1f} GB)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": launches,
+                "bpp": {"rounds_per_rhs": float(rounds.mean().item()),
+                        "passive_per_rhs": float(f.mean().item()),
+                        "status": nmf.nmf_status_str(r["worst"])},
+                "setup_s": {"generate": t_gen}}
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
+        return
+    if args.workload == STRESS:
+        import oracle
+        oracle.build()
+        run_stress_reference(args, world)
         return
     m, n, k, sigma, desc = WORKLOADS[args.workload]
     import oracle
@@ -457,7 +628,8 @@ def main():
     ap.add_argument("--start", choices=["cold", "warm", "learned"], default="warm",
                     help="BPP starting partitions: empty, the previous iteration's, or the "
                          "proposal network's (trained during the warm-up iterations)")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dense-large")
+    ap.add_argument("--workload", choices=sorted(list(WORKLOADS) + [STRESS]),
+                    default="dense-large")
     ap.add_argument("--pgrad", action="store_true",
                     help="record the projected-gradient stopping measure in every iteration")
     ap.add_argument("--solver", choices=["bpp", "mu", "hals"], default="bpp",
@@ -482,7 +654,10 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    run_ours(args, rank, world, local_rank)
+    if args.workload == STRESS:
+        run_stress(args, rank, world, local_rank)
+    else:
+        run_ours(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -50,6 +50,10 @@ typedef enum nmf_status {
 /* Human-readable name of a status code (static string, never NULL). */
 const char *nmf_status_str(nmf_status s);
 
+/* CUDA kernels this process has launched through the library so far (every
+ * entry point and handle; host-side counter, no synchronisation). */
+int64_t nmf_kernel_launches(void);
+
 /* Arithmetic used for the two m*n*k products (A H^T and W^T A) and for the
  * objective:
  *   NMF_PREC_FP32   plain FP32 FMAs on the SIMT pipes;

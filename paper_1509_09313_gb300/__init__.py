@@ -117,6 +117,7 @@ _c_nls_bpp_tune = _sig("nmf_nls_bpp_tune", [ctypes.POINTER(nmf_nls_desc), _P,
                                             ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                                             ctypes.POINTER(_I32)])
 _c_nls_bpp_set_shape = _sig("nmf_nls_bpp_set_shape", [_I32, _I32, _I32, _I32])
+_c_kernel_launches = _sig("nmf_kernel_launches", [], _I64)
 _c_nls_bpp_get_shape = _sig("nmf_nls_bpp_get_shape", [_I32, ctypes.POINTER(_I32),
                                                       ctypes.POINTER(_I32), ctypes.POINTER(_I32)])
 _c_objective_dense = _sig("nmf_objective_dense",
@@ -148,7 +149,7 @@ _c_mlp_gradient = _sig("nmf_mlp_gradient", [_P, _P, _P, _I64, _P, _P, _P])
 _c_mlp_train = _sig("nmf_mlp_train", [_P, _P, _P, _I64, _I64, ctypes.c_float, _P, _P])
 _c_set_proposal = _sig("nmf_set_proposal", [_P, _P, _I32, _I32, _I64, ctypes.c_float])
 
-EXPORTED = ["nmf_status_str", "nmf_gram", "nmf_mm_dense", "nmf_mm_csr", "nmf_csr_transpose",
+EXPORTED = ["nmf_status_str", "nmf_kernel_launches", "nmf_gram", "nmf_mm_dense", "nmf_mm_csr", "nmf_csr_transpose",
             "nmf_nls_bpp", "nmf_nls_bpp_noalloc", "nmf_nls_bpp_tune", "nmf_nls_bpp_set_shape",
             "nmf_nls_bpp_get_shape", "nmf_objective_dense", "nmf_init", "nmf_iterate", "nmf_sync",
             "nmf_objective", "nmf_objective_history", "nmf_get_factors", "nmf_set_factors",
@@ -161,6 +162,11 @@ EXPORTED = ["nmf_status_str", "nmf_gram", "nmf_mm_dense", "nmf_mm_csr", "nmf_csr
 
 def nmf_status_str(status: int) -> str:
     return _lib.nmf_status_str(int(status)).decode()
+
+
+def nmf_kernel_launches() -> int:
+    """CUDA kernels this process has launched through the library so far."""
+    return int(_c_kernel_launches())
 
 
 def _check(status: int, what: str):

@@ -52,6 +52,8 @@ struct TempBuf {
 
 }  // namespace
 
+extern "C" int64_t nmf_kernel_launches(void) { return (int64_t)launch_count; }
+
 extern "C" const char *nmf_status_str(nmf_status s)
 {
     switch (s) {

@@ -82,6 +82,18 @@ WorkLayout layout(int k)
     return w;
 }
 
+// Row of entry e of a lower triangle stored row by row (e = a (a + 1) / 2 + b,
+// b <= a): the FP32 estimate of the root of a (a + 1) / 2 = e, corrected.
+__device__ __forceinline__ int tri_row(int e)
+{
+    int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    while (a * (a + 1) / 2 > e)
+        --a;
+    while ((a + 1) * (a + 2) / 2 <= e)
+        ++a;
+    return a;
+}
+
 // ---------------------------------------------------------------------------
 // Prep: FP64 Cholesky of G_UU, its inverse and the scaled cond_1; one CTA.
 // flags[0] = mode (0 FP32, 1 FP64 with M, 2 FP64 without M), flags[1] = |U|.
@@ -95,9 +107,14 @@ __global__ void __launch_bounds__(PREP_THREADS)
                     unsigned long long *__restrict__ counters, BppStats *__restrict__ stats)
 {
     extern __shared__ double sm[];
-    double *L = sm;                                   // u x u, later M (u x u)
+    // L: u x u, the Cholesky factor in its lower triangle (diagonal included)
+    // and, once formed, L^{-1} transposed in its strict upper triangle:
+    // (L^{-1})_ac for a > c at L[c * u + a]; rdiag holds (L^{-1})_aa = 1 / L_aa.
+    double *L = sm;
     double *dsq = L + k * k;                          // sqrt(G_aa), a < u
-    int *uidx = reinterpret_cast<int *>(dsq + k);     // k
+    double *rdiag = dsq + k;                          // 1 / L_aa
+    double *gdiag = rdiag + k;                        // G_aa
+    int *uidx = reinterpret_cast<int *>(gdiag + k);   // k
     __shared__ int s_u, s_ok;
     __shared__ unsigned long long s_norm[2];
     const int tid = threadIdx.x;
@@ -129,29 +146,36 @@ __global__ void __launch_bounds__(PREP_THREADS)
         const int a = e / u, b = e % u;
         L[a * u + b] = G[uidx[a] * k + uidx[b]];
     }
+    for (int a = tid; a < u; a += PREP_THREADS) {
+        gdiag[a] = G[uidx[a] * k + uidx[a]];
+        dsq[a] = sqrt(gdiag[a]);
+    }
     __syncthreads();
     // Right-looking Cholesky on the lower triangle.
     for (int j = 0; j < u; ++j) {
         if (tid == 0) {
             const double d = L[j * u + j];
-            const double dorig = G[uidx[j] * k + uidx[j]];
-            if (!(d > PIVOT_TOL64 * dorig))
+            if (!(d > PIVOT_TOL64 * gdiag[j])) {
                 s_ok = 0;
-            else
-                L[j * u + j] = sqrt(d);
+            } else {
+                const double l = sqrt(d);
+                L[j * u + j] = l;
+                rdiag[j] = 1.0 / l;
+            }
         }
         __syncthreads();
         if (!s_ok)
             break;
-        const double ljj = L[j * u + j];
+        const double rj = rdiag[j];
         for (int i = j + 1 + tid; i < u; i += PREP_THREADS)
-            L[i * u + j] /= ljj;
+            L[i * u + j] *= rj;
         __syncthreads();
+        // Trailing lower triangle (a >= b > j), entries numbered row by row.
         const int t = u - j - 1;
-        for (int e = tid; e < t * t; e += PREP_THREADS) {
-            const int a = j + 1 + e / t, b = j + 1 + e % t;
-            if (b <= a)
-                L[a * u + b] -= L[a * u + j] * L[b * u + j];
+        for (int e = tid; e < t * (t + 1) / 2; e += PREP_THREADS) {
+            const int ra = tri_row(e), rb = e - ra * (ra + 1) / 2;
+            const int a = j + 1 + ra, b = j + 1 + rb;
+            L[a * u + b] = fma(-L[a * u + j], L[b * u + j], L[a * u + b]);
         }
         __syncthreads();
     }
@@ -163,56 +187,46 @@ __global__ void __launch_bounds__(PREP_THREADS)
         }
         return;
     }
-    // Columns of L^{-1} by forward substitution, staged in M64 (u x u).
-    double *Linv = M64;
+    // Columns of L^{-1} by forward substitution, one column per thread, into
+    // the strict upper triangle of L (transposed).
     for (int c = tid; c < u; c += PREP_THREADS) {
-        for (int a = 0; a < c; ++a)
-            Linv[a * u + c] = 0.0;
-        Linv[c * u + c] = 1.0 / L[c * u + c];
         for (int a = c + 1; a < u; ++a) {
-            double s = 0.0;
-            for (int b = c; b < a; ++b)
-                s -= L[a * u + b] * Linv[b * u + c];
-            Linv[a * u + c] = s / L[a * u + a];
+            double s = -L[a * u + c] * rdiag[c];
+            for (int b = c + 1; b < a; ++b)
+                s = fma(-L[a * u + b], L[c * u + b], s);
+            L[c * u + a] = s * rdiag[a];
         }
     }
     __syncthreads();
-    // M = Linv^T Linv : M[a][b] = sum_{c >= max(a,b)} Linv[c][a] Linv[c][b].
-    for (int e = tid; e < u * u; e += PREP_THREADS) {
-        const int a = e / u, b = e % u;
-        const int c0 = a > b ? a : b;
-        double s = 0.0;
-        for (int c = c0; c < u; ++c)
-            s += Linv[c * u + a] * Linv[c * u + b];
-        L[a * u + b] = s;
+    // M = L^{-T} L^{-1}: M_ab = sum_{c >= max(a, b)} (L^{-1})_ca (L^{-1})_cb,
+    // for a <= b, written to both triangles of M64 and M32.
+    for (int e = tid; e < u * (u + 1) / 2; e += PREP_THREADS) {
+        const int b = tri_row(e), a = e - b * (b + 1) / 2;   // a <= b
+        double s = (a == b ? rdiag[b] : L[a * u + b]) * rdiag[b];
+        for (int c = b + 1; c < u; ++c)
+            s = fma(L[a * u + c], L[b * u + c], s);
+        const int ga = uidx[a], gb = uidx[b];
+        M64[ga * k + gb] = s;
+        M64[gb * k + ga] = s;
+        M32[ga * k + gb] = (float)s;
+        M32[gb * k + ga] = (float)s;
     }
     __syncthreads();
     // Scaled cond_1 = max column sum of |G_ac| / (d_a d_c) times max column
     // sum of |M_ac| d_a d_c, d_a = sqrt(G_aa). Non-negative doubles order like
     // their bit patterns, so an integer max reduces them.
-    for (int a = tid; a < u; a += PREP_THREADS)
-        dsq[a] = sqrt(G[uidx[a] * k + uidx[a]]);
-    __syncthreads();
     for (int c = tid; c < u; c += PREP_THREADS) {
         double sg = 0.0, sm2 = 0.0;
         for (int a = 0; a < u; ++a) {
             sg += fabs(G[uidx[a] * k + uidx[c]]) / dsq[a];
-            sm2 += fabs(L[a * u + c]) * dsq[a];
+            sm2 += fabs(M64[uidx[a] * k + uidx[c]]) * dsq[a];
         }
         sg /= dsq[c];
         sm2 *= dsq[c];
         atomicMax(&s_norm[0], (unsigned long long)__double_as_longlong(sg));
         atomicMax(&s_norm[1], (unsigned long long)__double_as_longlong(sm2));
     }
-    for (int e = tid; e < k * k; e += PREP_THREADS)
-        M64[e] = 0.0;
     __syncthreads();
-    for (int e = tid; e < u * u; e += PREP_THREADS) {
-        const int a = e / u, b = e % u;
-        const double v = L[a * u + b];
-        M64[uidx[a] * k + uidx[b]] = v;
-        M32[uidx[a] * k + uidx[b]] = (float)v;
-    }
     if (tid == 0) {
         const double cond = __longlong_as_double((long long)s_norm[0]) *
                             __longlong_as_double((long long)s_norm[1]);
@@ -224,17 +238,6 @@ __global__ void __launch_bounds__(PREP_THREADS)
     }
 }
 
-// Row of entry e of a lower triangle stored row by row (e = a (a + 1) / 2 + b,
-// b <= a): the FP32 estimate of the root of a (a + 1) / 2 = e, corrected.
-__device__ __forceinline__ int tri_row(int e)
-{
-    int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-    while (a * (a + 1) / 2 > e)
-        --a;
-    while ((a + 1) * (a + 2) / 2 <= e)
-        ++a;
-    return a;
-}
 
 // FP64 Cholesky of S_ab = Src[idx[a] * ld + idx[b]], right-looking: after
 // each pivot the trailing lower triangle is updated with its (a, b) entries
@@ -836,7 +839,7 @@ nmf_status launch_bpp_prep(int k, const double *G, void *work, BppStats *stats_d
 {
     const SolveParams P = solve_params(k, 0, G, nullptr, nullptr, nullptr, nullptr, nullptr,
                                        nullptr, 0, work, stats_dev);
-    const size_t prep_smem = sizeof(double) * ((size_t)k * k + k) + sizeof(int) * (size_t)k;
+    const size_t prep_smem = sizeof(double) * ((size_t)k * k + 3 * k) + sizeof(int) * (size_t)k;
     static int prep_configured = 0;
     if ((int)prep_smem > 48 * 1024 && (int)prep_smem > prep_configured) {
         NMF_CUDA(cudaFuncSetAttribute(bpp_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

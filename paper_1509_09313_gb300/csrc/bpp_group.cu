@@ -35,7 +35,8 @@ namespace nmf {
 namespace bpp {
 namespace {
 
-constexpr int GT_THREADS = 256;
+constexpr int GT_THREADS = 512;
+constexpr int PF_MAX = 64 * 128 / GT_THREADS;   // tile elements per thread (TR k4 <= 64 x 128)
 constexpr size_t SMEM_LIMIT_GT = 226 * 1024;   // leaves room for the static arrays
 
 // Dt[i][r] = sum_j Mat[j][i] St[j][r] for i < k4, r < TR, over j < k4 (rows
@@ -63,7 +64,8 @@ __device__ __forceinline__ void tile_product(const float *__restrict__ Mat, int 
                 e[rr][h] = make_float2(0.0f, 0.0f);
                 o[rr][h] = make_float2(0.0f, 0.0f);
             }
-        for (int j = 0; j < k4; j += 2) {
+#pragma unroll 2
+        for (int j = 0; j < k4; j += 2) {   // k4 / 2 is even
             const float4 a0 = *reinterpret_cast<const float4 *>(St + j * TRS + r0);
             const float4 b0 = *reinterpret_cast<const float4 *>(Mat + j * k4 + i0);
             const float4 a1 = *reinterpret_cast<const float4 *>(St + (j + 1) * TRS + r0);
@@ -155,6 +157,24 @@ __global__ void __launch_bounds__(GT_THREADS)
 
     unsigned long long st_rhs = 0, st_rounds = 0, st_max = 0, st_nf = 0, pending = 0;
     const int64_t ntiles = cdiv(P.nrhs, (int64_t)TR);
+    // The right-hand sides of the next tile are read into registers while the
+    // current one is computed (element e = tid + GT_THREADS m of the tile,
+    // row e / k4, index e % k4).
+    float pf[PF_MAX];
+    int64_t pf_tile = -1;
+    auto prefetch = [&](int64_t t) {
+        pf_tile = t;
+        if (t >= ntiles)
+            return;
+        const int64_t t0 = t * TR;
+        const int tnr = (int)min((int64_t)TR, P.nrhs - t0);
+#pragma unroll
+        for (int m = 0; m < PF_MAX; ++m) {
+            const int e = tid + GT_THREADS * m;
+            const int r = e / k4, i = e - r * k4;
+            pf[m] = e < TR * k4 && r < tnr && i < k ? P.B[(t0 + r) * k + i] : 0.0f;
+        }
+    };
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t j0 = tile * TR;
         const int nr = (int)min((int64_t)TR, P.nrhs - j0);
@@ -179,10 +199,16 @@ __global__ void __launch_bounds__(GT_THREADS)
                 continue;
             }
         }
-        for (int e = tid; e < TR * k4; e += GT_THREADS) {
+        if (pf_tile != tile)
+            prefetch(tile);
+#pragma unroll
+        for (int m = 0; m < PF_MAX; ++m) {
+            const int e = tid + GT_THREADS * m;
             const int r = e / k4, i = e - r * k4;
-            Bt[i * TRS + r] = r < nr && i < k ? P.B[(j0 + r) * k + i] : 0.0f;
+            if (e < TR * k4)
+                Bt[i * TRS + r] = pf[m];
         }
+        prefetch(tile + gridDim.x);
         __syncthreads();
         // Which right-hand sides start from F = U: Q threads per right-hand
         // side, each over the indices i = q (mod Q).

@@ -14,8 +14,8 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import (GOLDEN, TID_H0, TID_NOISE_U1, TID_NOISE_U2, TID_W0, stream_state,
-               uniform_matrix)
+from . import (DEFAULT_SEED, GOLDEN, TID_H0, TID_NOISE_U1, TID_NOISE_U2, TID_STRESS_A, TID_W0,
+               stream_state, stress_factor, uniform_matrix)
 
 
 def _i64(u) -> int:
@@ -77,3 +77,27 @@ def normal_device(seed: int, tensor_pair, rows: int, cols: int, device: torch.de
     u1 = _uniform(seed, tensor_pair[0], idx, True)
     u2 = _uniform(seed, tensor_pair[1], idx, False)
     return torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * np.pi * u2)
+
+
+def stress_batch_device(device: torch.device, rows: int = 200000, k: int = 100,
+                        nrhs: int = 1000000, seed: int = DEFAULT_SEED):
+    """The batched-NLS stress inputs: G = W^T W of W = ``synth.stress_factor``
+    (rows x k) and nrhs right-hand sides drawn from the distribution of W^T a
+    for a uniform in [0, 1)^rows (central limit theorem: mean W^T 1 / 2,
+    covariance G / 12), b = W^T 1 / 2 + L z / sqrt(12) with G = L L^T and z
+    standard normal. Forming W^T a itself would cost 2 rows k nrhs flops.
+    Returns (G float64 k x k, B float32 nrhs x k), both on `device`. The
+    factor L is taken on the host (input generation only)."""
+    W = torch.from_numpy(stress_factor(rows, k, seed=seed)).to(device).double()
+    G = W.T @ W
+    mean = 0.5 * W.sum(dim=0)
+    L = torch.linalg.cholesky(G.cpu()).to(device)
+    B = torch.empty((nrhs, k), dtype=torch.float32, device=device)
+    pair = (TID_STRESS_A, TID_NOISE_U2)
+    step = 100000
+    for r0 in range(0, nrhs, step):
+        r1 = min(nrhs, r0 + step)
+        z = normal_device(seed, pair, r1 - r0, k, device, row0=r0)
+        B[r0:r1] = (mean + z @ L.T / np.sqrt(12.0)).float()
+        del z
+    return G.contiguous(), B

@@ -5,8 +5,8 @@ The Gram is G = W^T W of W (200000 x 100, uniform [0, 1) with 30% of the
 entries zeroed). Right-hand sides b = W^T a with a uniform in [0, 1)^200000
 would cost 2e13 flops to form, so they are drawn from the distribution they
 follow by the central limit theorem: mean W^T 1 / 2, covariance G / 12, i.e.
-b = W^T 1 / 2 + L z / sqrt(12) with G = L L^T and z standard normal. G and the
-right-hand sides are formed with plain PyTorch FP64 ops (test inputs only).
+b = W^T 1 / 2 + L z / sqrt(12) with G = L L^T and z standard normal
+(``synth.torch_gen.stress_batch_device``, plain PyTorch FP64 ops).
 
 The launch is timed (printed); every status must be OK; a sample of 10^4
 right-hand sides is compared with the FP64 oracle: values within the FP32
@@ -34,23 +34,9 @@ def nmf():
     return lib
 
 
-def _stress_inputs(dev):
-    W = torch.from_numpy(synth.stress_factor(ROWS, K)).to(dev).double()
-    G = W.T @ W
-    mean = 0.5 * W.sum(dim=0)
-    L = torch.linalg.cholesky(G)
-    B = torch.empty((NRHS, K), dtype=torch.float32, device=dev)
-    pair = (synth.TID_STRESS_A, synth.TID_NOISE_U2)
-    for r0 in range(0, NRHS, 100000):
-        z = torch_gen.normal_device(synth.DEFAULT_SEED, pair, 100000, K, dev, row0=r0)
-        B[r0:r0 + 100000] = (mean + z @ L.T / np.sqrt(12.0)).float()
-        del z
-    return G.contiguous(), B
-
-
 def test_stress_one_launch_million_rhs(nmf):
     dev = torch.device("cuda")
-    G, B = _stress_inputs(dev)
+    G, B = torch_gen.stress_batch_device(dev, ROWS, K, NRHS)
     torch.cuda.synchronize()
     nmf.nmf_nls_bpp(G, B)                      # warm-up (module load, attributes)
     torch.cuda.synchronize()
