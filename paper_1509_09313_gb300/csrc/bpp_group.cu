@@ -175,29 +175,50 @@ __global__ void __launch_bounds__(GT_THREADS)
             pf[m] = e < TR * k4 && r < tnr && i < k ? P.B[(t0 + r) * k + i] : 0.0f;
         }
     };
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // Tiles are taken in spans of SPT consecutive tiles (GT_THREADS
+    // right-hand sides). With a warm start the passive sets decide membership
+    // without reading B: one thread per right-hand side of the span, one
+    // round of loads for SPT tiles.
+    const int SPT = GT_THREADS / TR;
+    const int64_t nspans = cdiv(ntiles, (int64_t)SPT);
+    const bool pretest = P.pin || P.max_rounds < 1 || nU == 0;
+    __shared__ int tcount[GT_THREADS / 32];   // members per tile of the span (SPT <= 16)
+    auto next_tile = [&](int64_t t) {         // the tile this CTA takes after t
+        return (t + 1) % SPT != 0 ? t + 1 : t + 1 - SPT + (int64_t)gridDim.x * SPT;
+    };
+    for (int64_t sp = blockIdx.x; sp < nspans; sp += gridDim.x) {
+      int memb = 0;
+      if (pretest) {
+          __syncthreads();   // the previous span's counts are no longer read
+          if (tid < SPT)
+              tcount[tid] = 0;
+          __syncthreads();
+          const int64_t j = sp * GT_THREADS + tid;
+          if (j < P.nrhs && nU > 0 && P.pin) {
+              memb = 1;
+              for (int w = 0; w < P.nwords; ++w)
+                  if ((P.pin[j * P.nwords + w] & umask[w]) != umask[w])
+                      memb = 0;
+          }
+          if (memb)
+              atomicAdd(&tcount[tid / TR], 1);
+          __syncthreads();
+      }
+      for (int ts = 0; ts < SPT; ++ts) {
+        const int64_t tile = sp * SPT + ts;
+        if (tile >= ntiles)
+            break;
         const int64_t j0 = tile * TR;
         const int nr = (int)min((int64_t)TR, P.nrhs - j0);
         // A tile with fewer members than half its width costs more as tile
         // products than as per-warp solves: its members are marked and left.
         const int min_members = (nr + 1) / 2;
-        if (P.pin || P.max_rounds < 1 || nU == 0) {
-            // Warm start: the passive sets decide without reading B.
-            int c = 0;
-            if (tid < nr && nU > 0 && P.pin) {
-                const int64_t j = j0 + tid;
-                c = 1;
-                for (int w = 0; w < P.nwords; ++w)
-                    if ((P.pin[j * P.nwords + w] & umask[w]) != umask[w])
-                        c = 0;
-            }
-            if (__syncthreads_count(c) < min_members) {
-                if (c)
-                    reinterpret_cast<uint32_t *>(P.X)[(j0 + tid) * k] = GROUP_PENDING;
-                if (tid == 0)
-                    pending += nr;
-                continue;
-            }
+        if (pretest && tcount[ts] < min_members) {
+            if (memb && tid / TR == ts)
+                reinterpret_cast<uint32_t *>(P.X)[(sp * GT_THREADS + tid) * k] = GROUP_PENDING;
+            if (tid == 0)
+                pending += nr;
+            continue;
         }
         if (pf_tile != tile)
             prefetch(tile);
@@ -208,7 +229,7 @@ __global__ void __launch_bounds__(GT_THREADS)
             if (e < TR * k4)
                 Bt[i * TRS + r] = pf[m];
         }
-        prefetch(tile + gridDim.x);
+        prefetch(next_tile(tile));
         __syncthreads();
         // Which right-hand sides start from F = U: Q threads per right-hand
         // side, each over the indices i = q (mod Q).
@@ -324,6 +345,7 @@ __global__ void __launch_bounds__(GT_THREADS)
             pending += 1;
         }
         __syncthreads();   // the tile buffers are reused
+      }
     }
     if (pending)
         atomicAdd(&P.counters[CNT_PENDING], pending);
@@ -357,9 +379,9 @@ nmf_status launch_group32(const SolveParams &P, cudaStream_t s)
     if (per_sm < 1)
         return NMF_ERR_INVALID_ARG;
     int64_t blocks = (int64_t)per_sm * sm_count();
-    const int64_t tiles = cdiv(P.nrhs, (int64_t)TR);
-    if (tiles < blocks)
-        blocks = tiles < 1 ? 1 : tiles;
+    const int64_t spans = cdiv(P.nrhs, (int64_t)GT_THREADS);   // GT_THREADS / TR tiles each
+    if (spans < blocks)
+        blocks = spans < 1 ? 1 : spans;
     bpp_group_kernel<<<(unsigned)blocks, GT_THREADS, smem, s>>>(P, TR);
     NMF_LAUNCHED("bpp_group_kernel");
     return NMF_OK;
