@@ -1,7 +1,7 @@
 """Whole ANLS iterations on the GPU (C-ABI handle) against the FP64 oracle run
 from the same seeded inputs and starting point.
 
-Tolerances (the benchmark spec): relative objective <= 1e-5 and relative factor error
+Tolerances: relative objective <= 1e-5 and relative factor error
 (Frobenius) <= 1e-4 after the fixed iteration count; the GPU objective must be
 non-increasing up to 1e-6 relative (each half-step is an exact minimisation,
 Eq. 2).
