@@ -717,12 +717,8 @@ nmf_status launch_solve(const SolveParams &P, int list_pass, cudaStream_t s)
     const size_t smem = bytes(nwarps);
     if (smem > SMEM_LIMIT)
         return NMF_ERR_INVALID_ARG;
-    static int configured_bytes = 0;
-    if ((int)smem > configured_bytes) {
-        NMF_CUDA(cudaFuncSetAttribute(bpp_solve_kernel<KW, PT, MODE>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured_bytes = (int)smem;
-    }
+    static SmemOptIn opt_in;
+    NMF_TRY(ensure_smem(bpp_solve_kernel<KW, PT, MODE>, opt_in, smem));
     int per_sm = 0;
     NMF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &per_sm, bpp_solve_kernel<KW, PT, MODE>, nwarps * 32, smem));
@@ -840,12 +836,8 @@ nmf_status launch_bpp_prep(int k, const double *G, void *work, BppStats *stats_d
     const SolveParams P = solve_params(k, 0, G, nullptr, nullptr, nullptr, nullptr, nullptr,
                                        nullptr, 0, work, stats_dev);
     const size_t prep_smem = sizeof(double) * ((size_t)k * k + 3 * k) + sizeof(int) * (size_t)k;
-    static int prep_configured = 0;
-    if ((int)prep_smem > 48 * 1024 && (int)prep_smem > prep_configured) {
-        NMF_CUDA(cudaFuncSetAttribute(bpp_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)prep_smem));
-        prep_configured = (int)prep_smem;
-    }
+    static SmemOptIn opt_in;
+    NMF_TRY(ensure_smem(bpp_prep_kernel, opt_in, prep_smem));
     bpp_prep_kernel<<<1, PREP_THREADS, prep_smem, s>>>(
         G, k, const_cast<float *>(P.G32), const_cast<float *>(P.M32),
         const_cast<double *>(P.M64), const_cast<uint32_t *>(P.usable_words),

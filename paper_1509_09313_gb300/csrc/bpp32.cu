@@ -635,12 +635,8 @@ nmf_status launch32(const SolveParams &P, cudaStream_t s)
     const size_t smem = bytes(nwarps);
     if (smem > SMEM_LIMIT32)
         return NMF_ERR_INVALID_ARG;
-    static int configured_bytes = 0;
-    if ((int)smem > configured_bytes) {
-        NMF_CUDA(cudaFuncSetAttribute(bpp_solve32_kernel<KW>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured_bytes = (int)smem;
-    }
+    static SmemOptIn opt_in;
+    NMF_TRY(ensure_smem(bpp_solve32_kernel<KW>, opt_in, smem));
     int per_sm = 0;
     NMF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bpp_solve32_kernel<KW>,
                                                            nwarps * 32, smem));

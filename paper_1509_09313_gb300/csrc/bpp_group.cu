@@ -367,12 +367,8 @@ nmf_status launch_group32(const SolveParams &P, cudaStream_t s)
     const size_t smem = group_smem(P.k, TR);
     if (smem > SMEM_LIMIT_GT)
         return NMF_ERR_INVALID_ARG;
-    static int configured_bytes = 0;
-    if ((int)smem > configured_bytes) {
-        NMF_CUDA(cudaFuncSetAttribute(bpp_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-        configured_bytes = (int)smem;
-    }
+    static SmemOptIn opt_in;
+    NMF_TRY(ensure_smem(bpp_group_kernel, opt_in, smem));
     int per_sm = 0;
     NMF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bpp_group_kernel, GT_THREADS,
                                                            smem));

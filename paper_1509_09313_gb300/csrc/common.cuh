@@ -55,6 +55,29 @@ inline int sm_count()
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// A kernel's dynamic shared-memory opt-in is a per-device attribute: each
+// launch site keeps the largest size it has set on each device and sets it
+// again only when a launch needs more (or on a device it has not seen).
+struct SmemOptIn {
+    static constexpr int MAX_DEVICES = 64;
+    int bytes[MAX_DEVICES] = {};
+};
+
+template <typename Kernel>
+inline nmf_status ensure_smem(Kernel kernel, SmemOptIn &cache, size_t bytes)
+{
+    if (bytes <= 48 * 1024)
+        return NMF_OK;
+    int dev = 0;
+    NMF_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < SmemOptIn::MAX_DEVICES && (int)bytes <= cache.bytes[dev])
+        return NMF_OK;
+    NMF_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    if (dev >= 0 && dev < SmemOptIn::MAX_DEVICES)
+        cache.bytes[dev] = (int)bytes;
+    return NMF_OK;
+}
+
 // True when [a, a + bytes) and [b, b + bytes) share a byte.
 inline bool ranges_overlap(const void *a, const void *b, size_t bytes)
 {

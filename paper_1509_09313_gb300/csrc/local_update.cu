@@ -186,12 +186,8 @@ nmf_status launch_lu(const double *G, int k, const float *R, float *X, int64_t r
                      double *partials, int max_parts, int *nparts, cudaStream_t s)
 {
     const size_t smem = sizeof(float) * (size_t)(((k + 3) & ~3) + LU_WARPS) * 32 * KW;
-    static int configured = 0;
-    if ((int)smem > 48 * 1024 && (int)smem > configured) {
-        NMF_CUDA(cudaFuncSetAttribute(local_update_kernel<KW, OP>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured = (int)smem;
-    }
+    static SmemOptIn opt_in;
+    NMF_TRY(ensure_smem(local_update_kernel<KW, OP>, opt_in, smem));
     int per_sm = 0;
     NMF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &per_sm, local_update_kernel<KW, OP>, LU_WARPS * 32, smem));

@@ -1066,12 +1066,8 @@ nmf_status launch_tc(const CUtensorMap (&maps)[5], const TcArgs &a, cudaStream_t
 {
     using L = TcLayout<N, OBJ>;
     const int smem = L::BYTES + 1024;
-    static int configured = 0;
-    if (!configured) {
-        NMF_CUDA(cudaFuncSetAttribute(mm_tc_kernel<N, TRANS, OBJ>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        configured = 1;
-    }
+    static SmemOptIn opt_in;
+    NMF_TRY(ensure_smem(mm_tc_kernel<N, TRANS, OBJ>, opt_in, (size_t)smem));
     const int nkb = (int)cdiv(a.Q, TC_BK);
     const dim3 grid((unsigned)cdiv(a.P, TC_BM), (unsigned)cdiv(nkb, a.kb_per_split));
     mm_tc_kernel<N, TRANS, OBJ><<<grid, L::THREADS, smem, s>>>(maps[0], maps[1], maps[2], maps[3],
