@@ -247,6 +247,11 @@ typedef struct nmf_config {
     int32_t no_split_copies;   /* dense BF16x3: 0 (default) keeps BF16 hi / lo copies of A
                                   and A^T (+8 bytes per element of A) so the products need
                                   no per-pass split; 1 splits A in every pass (same products) */
+    int32_t no_fused_products; /* CSR with BPP: 0 (default) forms each right-hand side
+                                  (row of A H^T or A^T W) inside the FP32 solves, in the
+                                  SpMM's order, instead of a separate SpMM pass (same
+                                  results); 1 runs the SpMM first. The projected-gradient
+                                  record and a proposal network always use the SpMM pass */
 } nmf_config;
 
 /* The input matrix. Its device buffers are BORROWED: the caller keeps them

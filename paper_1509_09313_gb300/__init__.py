@@ -73,7 +73,8 @@ class nmf_nls_desc(ctypes.Structure):
 class nmf_config(ctypes.Structure):
     _fields_ = [("m", _I64), ("n", _I64), ("k", _I32), ("input_kind", _I32),
                 ("precision", _I32), ("start_mode", _I32), ("max_bpp_rounds", _I32),
-                ("objective_every", _I32), ("solver", _I32), ("no_split_copies", _I32)]
+                ("objective_every", _I32), ("solver", _I32), ("no_split_copies", _I32),
+                ("no_fused_products", _I32)]
 
 
 class nmf_matrix(ctypes.Structure):
@@ -390,7 +391,8 @@ class nmf_init:
 
     def __init__(self, A, W0: torch.Tensor, Ht0: torch.Tensor, precision="fp32",
                  start="cold", max_bpp_rounds: int = 100, objective_every: bool = True,
-                 shape=None, stream=None, solver="bpp", split_copies: bool = True):
+                 shape=None, stream=None, solver="bpp", split_copies: bool = True,
+                 fused_products: bool = True):
         _dev(W0, torch.float32, "W0")
         _dev(Ht0, torch.float32, "Ht0")
         m, k = W0.shape
@@ -420,7 +422,7 @@ class nmf_init:
         cfg = nmf_config(m, n, k, kind, _prec(precision),
                          NMF_START_WARM if start == "warm" else NMF_START_COLD,
                          max_bpp_rounds, int(bool(objective_every)), SOLVERS[solver],
-                         int(not split_copies))
+                         int(not split_copies), int(not fused_products))
         self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
         h = _P()
         _check(_c_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.byref(mat), _ptr(W0), _ptr(Ht0),

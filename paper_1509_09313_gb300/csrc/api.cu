@@ -413,7 +413,7 @@ nmf_status objective_into(nmf_handle *h, double *f_dev, bool after_h = false)
 // X before the update; it proposes the starting partition (use) or learns from
 // the final one (train). MU and HALS: one step of Eq. 5 or Eq. 6.
 nmf_status solve_half(nmf_handle *h, int64_t rows, const double *G, const float *R, float *X,
-                      uint64_t *passive, bool warm)
+                      uint64_t *passive, bool warm, const CsrGather *gather = nullptr)
 {
     const nmf_config &c = h->cfg;
     if (c.solver != NMF_SOLVER_BPP) {
@@ -432,7 +432,7 @@ nmf_status solve_half(nmf_handle *h, int64_t rows, const double *G, const float 
         PhaseTimer t(h, 2);
         NMF_TRY(launch_bpp_solve(c.k, rows, G, R, X, (use || warm) ? passive : nullptr, passive,
                                  nullptr, nullptr, c.max_bpp_rounds, h->bpp_work, h->stats_dev,
-                                 h->stream));
+                                 h->stream, gather));
     }
     if (train) {
         PhaseTimer t(h, 4);
@@ -462,9 +462,16 @@ nmf_status one_iteration(nmf_handle *h)
         NMF_CUDA(cudaEventRecord(h->ev_join, h->side));
         return NMF_OK;
     };
+    // Sparse BPP half-steps gather their right-hand sides inside the solves
+    // (written to V / Y as they go) unless something reads them first: the
+    // stopping measure or a proposal network.
+    const bool fuse = c.input_kind == NMF_INPUT_CSR && c.solver == NMF_SOLVER_BPP &&
+                      !c.no_fused_products && !h->pg_on && !h->mlp;
+    const CsrGather gather_w{h->A.rowptr, h->A.colidx, h->A.vals, h->Ht};
+    const CsrGather gather_h{h->t_rowptr, h->t_colidx, h->t_vals, h->W};
     // W <- argmin_{W >= 0} ||A - W H||: Gram H H^T, right-hand sides A H^T.
     NMF_TRY(fork_prepare(h->Ht, c.n, h->GH));
-    {
+    if (!fuse) {
         PhaseTimer t(h, 1);
         if (h->obj_pending) {
             // The previous iterate's f(W, H) rides on this A H^T pass.
@@ -481,15 +488,15 @@ nmf_status one_iteration(nmf_handle *h)
     if (h->pg_on)
         NMF_TRY(launch_pgrad_sq(h->GH, c.k, h->V, h->W, c.m, h->pg_part,
                                 h->pgw2 + (h->iterations % F_HIST_CAP), h->stream));
-    NMF_TRY(solve_half(h, c.m, h->GH, h->V, h->W, h->pW, warm));
+    NMF_TRY(solve_half(h, c.m, h->GH, h->V, h->W, h->pW, warm, fuse ? &gather_w : nullptr));
     // H <- argmin_{H >= 0} ||A - W H||: Gram W^T W, right-hand sides (W^T A)^T.
     NMF_TRY(fork_prepare(h->W, c.m, h->GW));
-    {
+    if (!fuse) {
         PhaseTimer t(h, 1);
         NMF_TRY(mm(h, 1, h->W, h->Y));
     }
     NMF_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-    NMF_TRY(solve_half(h, c.n, h->GW, h->Y, h->Ht, h->pH, warm));
+    NMF_TRY(solve_half(h, c.n, h->GW, h->Y, h->Ht, h->pH, warm, fuse ? &gather_h : nullptr));
     // ... and the new iterate's part in H (W^T W and A^T W of the new W).
     if (h->pg_on)
         NMF_TRY(launch_pgrad_sq(h->GW, c.k, h->Y, h->Ht, c.n, h->pg_part,
@@ -584,6 +591,9 @@ extern "C" nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nm
     if (c.start_mode != NMF_START_COLD && c.start_mode != NMF_START_WARM)
         return NMF_ERR_INVALID_ARG;
     if (c.solver != NMF_SOLVER_BPP && c.solver != NMF_SOLVER_MU && c.solver != NMF_SOLVER_HALS)
+        return NMF_ERR_INVALID_ARG;
+    if ((c.no_split_copies != 0 && c.no_split_copies != 1) ||
+        (c.no_fused_products != 0 && c.no_fused_products != 1))
         return NMF_ERR_INVALID_ARG;
     if (c.input_kind == NMF_INPUT_DENSE) {
         if (!A->dense || A->lda < c.n)

@@ -741,10 +741,15 @@ nmf_status launch_modes(const SolveParams &P, cudaStream_t s)
 {
     // Mode 0 (FP32): the group-tile pass for the all-passive group first,
     // then the per-warp solves of what it left.
-    if (P.group) {
+    if (P.group && !P.fused) {
         NMF_TRY(launch_group32(P, s));
     }
     NMF_TRY(launch_solve32(P, s));
+    if (P.fused) {
+        // FP64 half-step: the right-hand sides are formed here instead.
+        NMF_TRY(launch_spmm_unless_fp32(P.gat.rowptr, P.gat.colidx, P.gat.vals, P.nrhs, P.gat.F,
+                                        P.k, const_cast<float *>(P.B), P.flags, s));
+    }
     // Mode 1 (FP64): an FP32 pass first predicts each right-hand side's
     // partition into pout, and the FP64 solves start from it (their answer
     // does not depend on the start; they need fewer rounds).
@@ -753,6 +758,7 @@ nmf_status launch_modes(const SolveParams &P, cudaStream_t s)
         SolveParams Q = P;
         Q.predict = 1;
         Q.group = 0;
+        Q.fused = 0;
         NMF_TRY(launch_solve32(Q, s));
         P1.pin = P.pout;
     }
@@ -809,6 +815,8 @@ SolveParams solve_params(int k, int64_t nrhs, const double *G, const float *B, f
     P.status_out = status_out;
     P.counters = reinterpret_cast<unsigned long long *>(w + L.counters);
     P.predict = 0;
+    P.fused = 0;
+    P.gat = CsrGather{nullptr, nullptr, nullptr, nullptr};
     P.defer = reinterpret_cast<int64_t *>(w + L.defer);
     P.stats = stats_dev;
     const BppShape sh = shape_for(k);
@@ -849,12 +857,16 @@ nmf_status launch_bpp_prep(int k, const double *G, void *work, BppStats *stats_d
 nmf_status launch_bpp_solve(int k, int64_t nrhs, const double *G, const float *B, float *X,
                             const uint64_t *passive_in, uint64_t *passive_out, int32_t *rounds_out,
                             int8_t *status_out, int max_rounds, void *work, BppStats *stats_dev,
-                            cudaStream_t s)
+                            cudaStream_t s, const CsrGather *gather)
 {
     if (nrhs == 0)
         return NMF_OK;
-    const SolveParams P = solve_params(k, nrhs, G, B, X, passive_in, passive_out, rounds_out,
-                                       status_out, max_rounds, work, stats_dev);
+    SolveParams P = solve_params(k, nrhs, G, B, X, passive_in, passive_out, rounds_out,
+                                 status_out, max_rounds, work, stats_dev);
+    if (gather) {
+        P.fused = 1;
+        P.gat = *gather;
+    }
     return launch_solves(P, s);
 }
 

@@ -254,7 +254,8 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
     constexpr int PT = (KW + 1) / 2;
     if (P.predict ? P.flags[0] != 1 : P.flags[0] != 0)
         return;
-    const bool group = P.group && !P.predict;
+    const bool fused = P.fused && !P.predict;
+    const bool group = P.group && !P.predict && !fused;   // no group-tile pass before fused solves
     if (group && P.counters[CNT_PENDING] == 0)
         return;   // the group-tile pass solved them all
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -305,10 +306,43 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
             bool inF[KW];
             bool bad = false, have_u = false;
             float gmax = 0.0f;
+            if (fused) {
+                // b_j = (S F)_j: the row's stored entries in order, 32 at a
+                // time, broadcast by shuffle (the SpMM kernel's sum order).
+#pragma unroll
+                for (int s = 0; s < KW; ++s)
+                    g[s] = 0.0f;
+                const int64_t beg = P.gat.rowptr[j], end = P.gat.rowptr[j + 1];
+                for (int64_t p0 = beg; p0 < end; p0 += 32) {
+                    const int64_t p = p0 + lane;
+                    const int c = p < end ? P.gat.colidx[p] : 0;
+                    const float v = p < end ? P.gat.vals[p] : 0.0f;
+                    const int cnt = (int)min((int64_t)32, end - p0);
+                    for (int l = 0; l < cnt; ++l) {
+                        const int64_t cl = __shfl_sync(FULL, c, l);
+                        const float vl = __shfl_sync(FULL, v, l);
+                        const float *frow = P.gat.F + cl * k;
+#pragma unroll
+                        for (int s = 0; s < KW; ++s) {
+                            const int i = lane + 32 * s;
+                            if (i < k)
+                                g[s] = fmaf(vl, frow[i], g[s]);
+                        }
+                    }
+                }
+                float *Bw = const_cast<float *>(P.B);   // the caller's right-hand-side buffer
+#pragma unroll
+                for (int s = 0; s < KW; ++s) {
+                    const int i = lane + 32 * s;
+                    if (i < k)
+                        Bw[j * k + i] = g[s];
+                }
+            }
 #pragma unroll
             for (int s = 0; s < KW; ++s) {
                 const int i = lane + 32 * s;
-                g[s] = i < k ? P.B[j * k + i] : 0.0f;
+                if (!fused)
+                    g[s] = i < k ? P.B[j * k + i] : 0.0f;
                 bad |= !isfinite(g[s]);
                 gmax = fmaxf(gmax, fabsf(g[s]) / dsq[s]);
                 u[s] = 0.0f;

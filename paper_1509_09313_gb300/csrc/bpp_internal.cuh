@@ -58,6 +58,13 @@ struct SolveParams {
     // group = 1: the group-tile pass ran first; the per-warp kernel solves
     // only the right-hand sides it marked GROUP_PENDING.
     int group;
+    // fused = 1 (sparse ANLS): B is not formed beforehand. The FP32
+    // per-warp kernel gathers b_j = (S F)_j from the CSR matrix S and F
+    // (gat) in the same order as the SpMM kernel, writes it to B, then solves
+    // it; in an FP64 half-step the flag-checked SpMM forms B before the FP64
+    // solves.
+    int fused;
+    CsrGather gat;
 };
 
 __device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }

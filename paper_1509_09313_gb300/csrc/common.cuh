@@ -124,6 +124,20 @@ nmf_status launch_mm_tc_presplit(const void *hi, const void *lo, int64_t m, int6
 // CSR SpMM: out (rows x k) = S F.
 nmf_status launch_spmm(const int64_t *rowptr, const int32_t *colidx, const float *vals,
                        int64_t rows, const float *F, int k, float *out, cudaStream_t s);
+// The same product, skipped on the device when *mode_flag == 0 (an FP32
+// half-step whose solves gather their right-hand sides themselves).
+nmf_status launch_spmm_unless_fp32(const int64_t *rowptr, const int32_t *colidx,
+                                   const float *vals, int64_t rows, const float *F, int k,
+                                   float *out, const int *mode_flag, cudaStream_t s);
+
+// Right-hand sides formed inside the batched BPP as b_j = (S F)_j (rows of the
+// CSR matrix S times F, k columns), for the sparse ANLS half-steps.
+struct CsrGather {
+    const int64_t *rowptr;
+    const int32_t *colidx;
+    const float *vals;
+    const float *F;
+};
 
 // Objective pieces. Dense: per-block FP64 partial sums of squared residuals,
 // reduced in a fixed order into *f_dev. `partials` holds objective_partials_len().
@@ -176,7 +190,7 @@ nmf_status bpp_get_shape(int k, int *warps, int *chunk, int *group);
 nmf_status launch_bpp_solve(int k, int64_t nrhs, const double *G, const float *B, float *X,
                             const uint64_t *passive_in, uint64_t *passive_out, int32_t *rounds_out,
                             int8_t *status_out, int max_rounds, void *work, BppStats *stats_dev,
-                            cudaStream_t s);
+                            cudaStream_t s, const CsrGather *gather = nullptr);
 
 // Learned passive-set proposal (mlp.cu).
 struct MlpNet;

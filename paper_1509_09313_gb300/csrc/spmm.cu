@@ -23,8 +23,10 @@ template <int KW>
 __global__ void __launch_bounds__(SPMM_THREADS)
     spmm_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                 const float *__restrict__ vals, int64_t rows, const float *__restrict__ F, int k,
-                float *__restrict__ out)
+                float *__restrict__ out, const int *__restrict__ mode_flag)
 {
+    if (mode_flag && *mode_flag == 0)
+        return;   // FP32 half-step: its solves form the product rows themselves
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * SPMM_THREADS + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * SPMM_THREADS) >> 5;
@@ -133,8 +135,10 @@ __global__ void sort_rows_kernel(const int64_t *__restrict__ t_rowptr, int64_t n
 
 }  // namespace
 
-nmf_status launch_spmm(const int64_t *rowptr, const int32_t *colidx, const float *vals,
-                       int64_t rows, const float *F, int k, float *out, cudaStream_t s)
+namespace {
+nmf_status spmm_launch(const int64_t *rowptr, const int32_t *colidx, const float *vals,
+                       int64_t rows, const float *F, int k, float *out, const int *mode_flag,
+                       cudaStream_t s)
 {
     if (rows == 0)
         return NMF_OK;
@@ -142,16 +146,31 @@ nmf_status launch_spmm(const int64_t *rowptr, const int32_t *colidx, const float
     const int64_t cap = 16LL * sm_count();
     if (blocks > cap)
         blocks = cap;
+    const unsigned g = (unsigned)blocks;
     if (k <= 32)
-        spmm_kernel<1><<<(unsigned)blocks, SPMM_THREADS, 0, s>>>(rowptr, colidx, vals, rows, F, k, out);
+        spmm_kernel<1><<<g, SPMM_THREADS, 0, s>>>(rowptr, colidx, vals, rows, F, k, out, mode_flag);
     else if (k <= 64)
-        spmm_kernel<2><<<(unsigned)blocks, SPMM_THREADS, 0, s>>>(rowptr, colidx, vals, rows, F, k, out);
+        spmm_kernel<2><<<g, SPMM_THREADS, 0, s>>>(rowptr, colidx, vals, rows, F, k, out, mode_flag);
     else if (k <= 96)
-        spmm_kernel<3><<<(unsigned)blocks, SPMM_THREADS, 0, s>>>(rowptr, colidx, vals, rows, F, k, out);
+        spmm_kernel<3><<<g, SPMM_THREADS, 0, s>>>(rowptr, colidx, vals, rows, F, k, out, mode_flag);
     else
-        spmm_kernel<4><<<(unsigned)blocks, SPMM_THREADS, 0, s>>>(rowptr, colidx, vals, rows, F, k, out);
+        spmm_kernel<4><<<g, SPMM_THREADS, 0, s>>>(rowptr, colidx, vals, rows, F, k, out, mode_flag);
     NMF_LAUNCHED("spmm_kernel");
     return NMF_OK;
+}
+}  // namespace
+
+nmf_status launch_spmm(const int64_t *rowptr, const int32_t *colidx, const float *vals,
+                       int64_t rows, const float *F, int k, float *out, cudaStream_t s)
+{
+    return spmm_launch(rowptr, colidx, vals, rows, F, k, out, nullptr, s);
+}
+
+nmf_status launch_spmm_unless_fp32(const int64_t *rowptr, const int32_t *colidx,
+                                   const float *vals, int64_t rows, const float *F, int k,
+                                   float *out, const int *mode_flag, cudaStream_t s)
+{
+    return spmm_launch(rowptr, colidx, vals, rows, F, k, out, mode_flag, s);
 }
 
 nmf_status launch_csr_transpose(const int64_t *rowptr, const int32_t *colidx, const float *vals,

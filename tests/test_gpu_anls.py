@@ -172,6 +172,44 @@ def test_split_copies_give_the_same_products(nmf):
     assert np.abs(f1 - f2).max() <= 1e-7 * f2.max()
 
 
+@pytest.mark.parametrize("k,start,ill", [(20, "warm", False), (50, "warm", False),
+                                         (50, "cold", False), (12, "warm", True)])
+def test_sparse_fused_products_bitwise(nmf, k, start, ill):
+    # Sparse BPP half-steps gather each right-hand side inside the FP32 solves,
+    # in the SpMM kernel's order, and write it to V / Y as they go: bitwise the
+    # same factors, objective history, passive sets and round counts as the
+    # separate SpMM pass. `ill`: H0's columns share a dominant common part, so
+    # the first half-steps run in FP64 and take their right-hand sides from the
+    # SpMM that runs only then.
+    m, n, T = 20000, 10000, 4
+    csr = synth.csr_uniform(m, n, 200000, seed=7)
+    W0, Ht0 = synth.init_factors(m, n, k, seed=7)
+    if ill:
+        Ht0 = (Ht0 + 1000.0 * Ht0[:, :1]).astype(np.float32)
+    outs = []
+    for fused in (False, True):
+        h = nmf.nmf_init(tuple(dev(x) for x in csr), dev(W0), dev(Ht0), shape=(m, n),
+                         start=start, fused_products=fused)
+        h.nmf_iterate(T)
+        assert h.nmf_sync() == nmf.NMF_OK
+        W, Ht = h.nmf_get_factors()
+        pW, pH = h.nmf_get_passive()
+        st = h.nmf_get_stats()
+        outs.append((W.cpu(), Ht.cpu(), np.array(h.nmf_objective_history()), pW.cpu(), pH.cpu(),
+                     st))
+        h.nmf_destroy()
+    (W0_, H0_, f0, pW0, pH0, s0), (W1, H1, f1, pW1, pH1, s1) = outs
+    print(f"k={k} {start} ill={ill}: f {f1} fp64 half-steps {s1['bpp_fp64_halfsteps']} "
+          f"launches {s0['kernel_launches']} -> {s1['kernel_launches']}")
+    assert torch.equal(W1, W0_) and torch.equal(H1, H0_)
+    assert np.array_equal(f1, f0)
+    assert torch.equal(pW1, pW0) and torch.equal(pH1, pH0)
+    for key in ("bpp_rhs", "bpp_rounds", "bpp_fp64_solves", "bpp_fp64_halfsteps"):
+        assert s1[key] == s0[key], key
+    if ill:
+        assert s1["bpp_fp64_halfsteps"] > 0
+
+
 def test_checkpoint_resume(nmf):
     m, n, k = 600, 400, 8
     A = synth.dense_planted(m, n, k, 0.01, seed=5)
