@@ -187,165 +187,166 @@ __global__ void __launch_bounds__(GT_THREADS)
         return (t + 1) % SPT != 0 ? t + 1 : t + 1 - SPT + (int64_t)gridDim.x * SPT;
     };
     for (int64_t sp = blockIdx.x; sp < nspans; sp += gridDim.x) {
-      int memb = 0;
-      if (pretest) {
-          __syncthreads();   // the previous span's counts are no longer read
-          if (tid < SPT)
-              tcount[tid] = 0;
-          __syncthreads();
-          const int64_t j = sp * GT_THREADS + tid;
-          if (j < P.nrhs && nU > 0 && P.pin) {
-              memb = 1;
-              for (int w = 0; w < P.nwords; ++w)
-                  if ((P.pin[j * P.nwords + w] & umask[w]) != umask[w])
-                      memb = 0;
-          }
-          if (memb)
-              atomicAdd(&tcount[tid / TR], 1);
-          __syncthreads();
-      }
-      for (int ts = 0; ts < SPT; ++ts) {
-        const int64_t tile = sp * SPT + ts;
-        if (tile >= ntiles)
-            break;
-        const int64_t j0 = tile * TR;
-        const int nr = (int)min((int64_t)TR, P.nrhs - j0);
-        // A tile with fewer members than half its width costs more as tile
-        // products than as per-warp solves: its members are marked and left.
-        const int min_members = (nr + 1) / 2;
-        if (pretest && tcount[ts] < min_members) {
-            if (memb && tid / TR == ts)
-                reinterpret_cast<uint32_t *>(P.X)[(sp * GT_THREADS + tid) * k] = GROUP_PENDING;
-            if (tid == 0)
-                pending += nr;
-            continue;
-        }
-        if (pf_tile != tile)
-            prefetch(tile);
-#pragma unroll
-        for (int m = 0; m < PF_MAX; ++m) {
-            const int e = tid + GT_THREADS * m;
-            const int r = e / k4, i = e - r * k4;
-            if (e < TR * k4)
-                Bt[i * TRS + r] = pf[m];
-        }
-        prefetch(next_tile(tile));
-        __syncthreads();
-        // Which right-hand sides start from F = U: Q threads per right-hand
-        // side, each over the indices i = q (mod Q).
-        const int Q = GT_THREADS / TR, rq = tid / Q, q = tid - rq * Q;
-        const bool rlive = rq < nr && nU > 0;
-        int ok = 1;
-        float gmax = 0.0f;
-        if (rlive)
-            for (int i = q; i < k; i += Q) {
-                const float g = Bt[i * TRS + rq];
-                ok &= isfinite(g) ? 1 : 0;
-                gmax = fmaxf(gmax, fabsf(g) / dsq[i]);
-            }
-        ok = q_and(ok, Q);
-        gmax = q_max(gmax, Q);
-        if (rlive && ok) {
-            if (P.pin) {
+        int memb = 0;
+        if (pretest) {
+            __syncthreads();   // the previous span's counts are no longer read
+            if (tid < SPT)
+                tcount[tid] = 0;
+            __syncthreads();
+            const int64_t j = sp * GT_THREADS + tid;
+            if (j < P.nrhs && nU > 0 && P.pin) {
+                memb = 1;
                 for (int w = 0; w < P.nwords; ++w)
-                    if ((P.pin[(j0 + rq) * P.nwords + w] & umask[w]) != umask[w])
-                        ok = 0;
-            } else if (P.max_rounds >= 1) {
-                const float ytol = FEAS_TOL32 * gmax;
-                for (int i = q; i < k; i += Q)
-                    if (use[i] && !(-Bt[i * TRS + rq] < -ytol * dsq[i]))
-                        ok = 0;
-            } else {
-                ok = 0;
+                    if ((P.pin[j * P.nwords + w] & umask[w]) != umask[w])
+                        memb = 0;
             }
+            if (memb)
+                atomicAdd(&tcount[tid / TR], 1);
+            __syncthreads();
         }
-        ok = q_and(ok, Q) && rlive;
-        const int c = q == 0 ? ok : 0;
-        if (q == 0) {
-            cand[rq] = (unsigned char)c;
-            solved[rq] = 0;
-        }
-        if (__syncthreads_count(c) >= min_members) {
-            // x0 = M g + 0 on F (0 elsewhere), as the per-warp kernel's
-            // complement form with an empty list forms it.
-            tile_product(Ms, k4, Bt, Xt, TR, TRS);
-            __syncthreads();
-            for (int e = tid; e < k4 * TR; e += GT_THREADS) {
-                const int i = e / TR, r = e - i * TR;
-                const float v = Xt[i * TRS + r];
-                Xt[i * TRS + r] = i < k && use[i] ? v + 0.0f : 0.0f;
+        for (int ts = 0; ts < SPT; ++ts) {
+            const int64_t tile = sp * SPT + ts;
+            if (tile >= ntiles)
+                break;
+            const int64_t j0 = tile * TR;
+            const int nr = (int)min((int64_t)TR, P.nrhs - j0);
+            // A tile with fewer members than half its width costs more as tile
+            // products than as per-warp solves: its members are marked and left.
+            const int min_members = (nr + 1) / 2;
+            if (pretest && tcount[ts] < min_members) {
+                if (memb && tid / TR == ts)
+                    reinterpret_cast<uint32_t *>(P.X)[(sp * GT_THREADS + tid) * k] = GROUP_PENDING;
+                if (tid == 0)
+                    pending += nr;
+                continue;
             }
-            __syncthreads();
-            tile_product(Gs, k4, Xt, Wt, TR, TRS);   // w = G x0
-            __syncthreads();
-            for (int e = tid; e < k4 * TR; e += GT_THREADS) {
-                const int i = e / TR, r = e - i * TR;
-                Wt[i * TRS + r] = i < k && use[i] ? Bt[i * TRS + r] - Wt[i * TRS + r] : 0.0f;
+            if (pf_tile != tile)
+                prefetch(tile);
+#pragma unroll
+            for (int m = 0; m < PF_MAX; ++m) {
+                const int e = tid + GT_THREADS * m;
+                const int r = e / k4, i = e - r * k4;
+                if (e < TR * k4)
+                    Bt[i * TRS + r] = pf[m];
             }
+            prefetch(next_tile(tile));
             __syncthreads();
-            tile_product(Ms, k4, Wt, Bt, TR, TRS);   // up = M r (g no longer needed)
-            __syncthreads();
-            for (int e = tid; e < k4 * TR; e += GT_THREADS) {
-                const int i = e / TR, r = e - i * TR;
-                if (i < k && use[i])
-                    Xt[i * TRS + r] = Xt[i * TRS + r] + (Bt[i * TRS + r] + 0.0f);
-            }
-            __syncthreads();
-            {
-                const bool live = rq < nr && cand[rq];
-                const int64_t j = j0 + rq;
-                float xm = 0.0f;
-                if (live)
+            // Which right-hand sides start from F = U: Q threads per right-hand
+            // side, each over the indices i = q (mod Q).
+            const int Q = GT_THREADS / TR, rq = tid / Q, q = tid - rq * Q;
+            const bool rlive = rq < nr && nU > 0;
+            int ok = 1;
+            float gmax = 0.0f;
+            if (rlive)
+                for (int i = q; i < k; i += Q) {
+                    const float g = Bt[i * TRS + rq];
+                    ok &= isfinite(g) ? 1 : 0;
+                    gmax = fmaxf(gmax, fabsf(g) / dsq[i]);
+                }
+            ok = q_and(ok, Q);
+            gmax = q_max(gmax, Q);
+            if (rlive && ok) {
+                if (P.pin) {
+                    for (int w = 0; w < P.nwords; ++w)
+                        if ((P.pin[(j0 + rq) * P.nwords + w] & umask[w]) != umask[w])
+                            ok = 0;
+                } else if (P.max_rounds >= 1) {
+                    const float ytol = FEAS_TOL32 * gmax;
                     for (int i = q; i < k; i += Q)
-                        if (use[i])
-                            xm = fmaxf(xm, fabsf(Xt[i * TRS + rq]) * dsq[i]);
-                const float xtol = FEAS_TOL32 * q_max(xm, Q);
-                int feasible = 1;
-                if (live)
-                    for (int i = q; i < k; i += Q)
-                        if (use[i] && Xt[i * TRS + rq] * dsq[i] < -xtol)
-                            feasible = 0;
-                feasible = q_and(feasible, Q);
-                int fin = 1;
-                if (live && feasible)
-                    for (int i = q; i < k; i += Q) {
-                        const float v = Xt[i * TRS + rq];
-                        const float x = v > 0.0f ? v : 0.0f;
-                        fin &= isfinite(x) ? 1 : 0;
-                        Xt[i * TRS + rq] = x;
-                    }
-                const bool nf = !q_and(fin, Q);
-                if (live && feasible && q == 0) {
-                    const int rounds = P.pin ? 0 : 1;
-                    const int status = nf ? NMF_ERR_NONFINITE : NMF_OK;
-                    solved[rq] = 1;
-                    if (P.pout)
-                        for (int w = 0; w < P.nwords; ++w)
-                            P.pout[j * P.nwords + w] = umask[w];
-                    if (P.rounds_out)
-                        P.rounds_out[j] = rounds;
-                    if (P.status_out)
-                        P.status_out[j] = (int8_t)status;
-                    st_rhs += 1;
-                    st_rounds += rounds;
-                    st_max = st_max > (unsigned long long)rounds ? st_max : (unsigned long long)rounds;
-                    st_nf += nf;
+                        if (use[i] && !(-Bt[i * TRS + rq] < -ytol * dsq[i]))
+                            ok = 0;
+                } else {
+                    ok = 0;
                 }
             }
-            __syncthreads();
-            for (int e = tid; e < nr * k; e += GT_THREADS) {
-                const int r = e / k, i = e - r * k;
-                if (solved[r])
-                    P.X[(j0 + r) * k + i] = Xt[i * TRS + r];
+            ok = q_and(ok, Q) && rlive;
+            const int c = q == 0 ? ok : 0;
+            if (q == 0) {
+                cand[rq] = (unsigned char)c;
+                solved[rq] = 0;
             }
+            if (__syncthreads_count(c) >= min_members) {
+                // x0 = M g + 0 on F (0 elsewhere), as the per-warp kernel's
+                // complement form with an empty list forms it.
+                tile_product(Ms, k4, Bt, Xt, TR, TRS);
+                __syncthreads();
+                for (int e = tid; e < k4 * TR; e += GT_THREADS) {
+                    const int i = e / TR, r = e - i * TR;
+                    const float v = Xt[i * TRS + r];
+                    Xt[i * TRS + r] = i < k && use[i] ? v + 0.0f : 0.0f;
+                }
+                __syncthreads();
+                tile_product(Gs, k4, Xt, Wt, TR, TRS);   // w = G x0
+                __syncthreads();
+                for (int e = tid; e < k4 * TR; e += GT_THREADS) {
+                    const int i = e / TR, r = e - i * TR;
+                    Wt[i * TRS + r] = i < k && use[i] ? Bt[i * TRS + r] - Wt[i * TRS + r] : 0.0f;
+                }
+                __syncthreads();
+                tile_product(Ms, k4, Wt, Bt, TR, TRS);   // up = M r (g no longer needed)
+                __syncthreads();
+                for (int e = tid; e < k4 * TR; e += GT_THREADS) {
+                    const int i = e / TR, r = e - i * TR;
+                    if (i < k && use[i])
+                        Xt[i * TRS + r] = Xt[i * TRS + r] + (Bt[i * TRS + r] + 0.0f);
+                }
+                __syncthreads();
+                {
+                    const bool live = rq < nr && cand[rq];
+                    const int64_t j = j0 + rq;
+                    float xm = 0.0f;
+                    if (live)
+                        for (int i = q; i < k; i += Q)
+                            if (use[i])
+                                xm = fmaxf(xm, fabsf(Xt[i * TRS + rq]) * dsq[i]);
+                    const float xtol = FEAS_TOL32 * q_max(xm, Q);
+                    int feasible = 1;
+                    if (live)
+                        for (int i = q; i < k; i += Q)
+                            if (use[i] && Xt[i * TRS + rq] * dsq[i] < -xtol)
+                                feasible = 0;
+                    feasible = q_and(feasible, Q);
+                    int fin = 1;
+                    if (live && feasible)
+                        for (int i = q; i < k; i += Q) {
+                            const float v = Xt[i * TRS + rq];
+                            const float x = v > 0.0f ? v : 0.0f;
+                            fin &= isfinite(x) ? 1 : 0;
+                            Xt[i * TRS + rq] = x;
+                        }
+                    const bool nf = !q_and(fin, Q);
+                    if (live && feasible && q == 0) {
+                        const int rounds = P.pin ? 0 : 1;
+                        const int status = nf ? NMF_ERR_NONFINITE : NMF_OK;
+                        solved[rq] = 1;
+                        if (P.pout)
+                            for (int w = 0; w < P.nwords; ++w)
+                                P.pout[j * P.nwords + w] = umask[w];
+                        if (P.rounds_out)
+                            P.rounds_out[j] = rounds;
+                        if (P.status_out)
+                            P.status_out[j] = (int8_t)status;
+                        st_rhs += 1;
+                        st_rounds += rounds;
+                        if ((unsigned long long)rounds > st_max)
+                            st_max = (unsigned long long)rounds;
+                        st_nf += nf;
+                    }
+                }
+                __syncthreads();
+                for (int e = tid; e < nr * k; e += GT_THREADS) {
+                    const int r = e / k, i = e - r * k;
+                    if (solved[r])
+                        P.X[(j0 + r) * k + i] = Xt[i * TRS + r];
+                }
+            }
+            if (tid < nr && !solved[tid]) {
+                if (cand[tid])   // the per-warp kernel looks for the mark on members only
+                    reinterpret_cast<uint32_t *>(P.X)[(j0 + tid) * k] = GROUP_PENDING;
+                pending += 1;
+            }
+            __syncthreads();   // the tile buffers are reused
         }
-        if (tid < nr && !solved[tid]) {
-            if (cand[tid])   // the per-warp kernel looks for the mark on members only
-                reinterpret_cast<uint32_t *>(P.X)[(j0 + tid) * k] = GROUP_PENDING;
-            pending += 1;
-        }
-        __syncthreads();   // the tile buffers are reused
-      }
     }
     if (pending)
         atomicAdd(&P.counters[CNT_PENDING], pending);
