@@ -95,3 +95,30 @@ def test_nls_rejects_overlapping_x_and_b(lib, fn):
     for x_off in (0, 4 * k * nrhs - 4, -(4 * k * nrhs - 4)):
         d = NlsDesc(k, nrhs, 0x10000, 0x200000, 0x200000 + x_off, None, None, None, None, 10)
         assert f(ctypes.byref(d), None) == 1, x_off
+
+
+def test_struct_layouts_match_header(tmp_path):
+    # The binding's ctypes structures mirror the header's: same size and the
+    # same offset for every field (compiled against the header with gcc).
+    import subprocess
+
+    import paper_1509_09313_gb300 as lib
+    names = ["nmf_config", "nmf_matrix", "nmf_nls_desc", "nmf_stats"]
+    lines = ['#include <stdio.h>', '#include "nmf_gb300.h"', "int main(void) {"]
+    for s in names:
+        lines.append(f'    printf("{s} %zu\\n", sizeof({s}));')
+        for f in getattr(lib, s)._fields_:
+            lines.append(f'    printf("{s}.{f[0]} %zu\\n", offsetof({s}, {f[0]}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    c_side = dict(line.split() for line in out.splitlines())
+    for s in names:
+        st = getattr(lib, s)
+        assert int(c_side[s]) == ctypes.sizeof(st), s
+        for f in st._fields_:
+            assert int(c_side[f"{s}.{f[0]}"]) == getattr(st, f[0]).offset, (s, f[0])
