@@ -83,6 +83,18 @@ NCU_TRAFFIC = {
 }
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over all ranks: a timed region counts at its slowest
+    rank's time. One rank returns x unchanged."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def env_int(name, default):
     try:
         return int(os.environ.get(name, default))
@@ -287,10 +299,7 @@ def run_stress(args, rank, world, local_rank):
     clocks = sampler.stop()
     launches = nmf.nmf_kernel_launches() - l0
     ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     value = world * nrhs * args.steps / (ms / 1000.0)
 
     # Algorithmic work of the last call: per right-hand side and exchange
@@ -329,10 +338,7 @@ def run_stress(args, rank, world, local_rank):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         barrier()
-        if world > 1:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(dt, world, dev)
         e2e = {"value": world * nrhs * args.steps / dt, "unit": "RHS/s",
                "h2d_bytes_per_step": 4 * nrhs * k, "d2h_bytes_per_step": 4 * nrhs * k,
                "note": "upload B, nmf_nls_bpp, download X, every step"}
@@ -476,10 +482,7 @@ def run_ours(args, rank, world, local_rank):
     if args.pgrad:
         pg = h.nmf_pgrad_history()
         pg_ratio = pg[-1] / pg[0] if pg and pg[0] > 0 else None
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     value = world * args.steps / (ms / 1000.0)
 
     # Roofline of the dominant kernel (the two m*n*k products), from the
@@ -597,10 +600,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         barrier()
-        if world > 1:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(dt, world, dev)
         h2.nmf_destroy()
         h2d = (sum(x.numel() * x.element_size() for x in A_host) if sparse else 4 * m * n) + \
             4 * (m + n) * k
