@@ -150,8 +150,8 @@ _c_mlp_gradient = _sig("nmf_mlp_gradient", [_P, _P, _P, _I64, _P, _P, _P])
 _c_mlp_train = _sig("nmf_mlp_train", [_P, _P, _P, _I64, _I64, ctypes.c_float, _P, _P])
 _c_set_proposal = _sig("nmf_set_proposal", [_P, _P, _I32, _I32, _I64, ctypes.c_float])
 
-EXPORTED = ["nmf_status_str", "nmf_kernel_launches", "nmf_gram", "nmf_mm_dense", "nmf_mm_csr", "nmf_csr_transpose",
-            "nmf_nls_bpp", "nmf_nls_bpp_noalloc", "nmf_nls_bpp_tune", "nmf_nls_bpp_set_shape",
+EXPORTED = ["nmf_status_str", "nmf_kernel_launches", "nmf_gram", "nmf_mm_dense", "nmf_mm_csr",
+            "nmf_csr_transpose", "nmf_nls_bpp", "nmf_nls_bpp_noalloc", "nmf_nls_bpp_tune", "nmf_nls_bpp_set_shape",
             "nmf_nls_bpp_get_shape", "nmf_objective_dense", "nmf_init", "nmf_iterate", "nmf_sync",
             "nmf_objective", "nmf_objective_history", "nmf_get_factors", "nmf_set_factors",
             "nmf_get_passive", "nmf_get_stats", "nmf_set_timing", "nmf_set_graph", "nmf_destroy",

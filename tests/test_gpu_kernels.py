@@ -312,7 +312,8 @@ def test_bpp_singular_gram(nmf):
     scale = np.abs(Bd).max(axis=1)
     assert (X[good] >= 0).all()
     assert (Y[good] >= -1e-9 * scale[good, None]).all()
-    assert (np.abs((X * Y)[good]).sum(axis=1) <= 1e-9 * (scale[good] * np.abs(X[good]).max(axis=1) + 1e-30)).all()
+    comp = np.abs((X * Y)[good]).sum(axis=1)
+    assert (comp <= 1e-9 * (scale[good] * np.abs(X[good]).max(axis=1) + 1e-30)).all()
 
 
 class shape_of:
