@@ -13,12 +13,18 @@ from __future__ import annotations
 
 import itertools
 import os
+from fractions import Fraction
 
 import numpy as np
 
 import synth
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "nls_hand.txt")
+
+
+def _numbers(text):
+    """Whitespace-separated numbers; exact fractions such as 107/173 allowed."""
+    return np.array([float(Fraction(t)) for t in text.split()], dtype=np.float64)
 
 
 def load_golden():
@@ -30,12 +36,8 @@ def load_golden():
                 continue
             name, k, G, g, x, y, rounds = [t.strip() for t in line.split("|")]
             k = int(k)
-            cases.append(dict(name=name, k=k,
-                              G=np.array(G.split(), dtype=np.float64).reshape(k, k),
-                              g=np.array(g.split(), dtype=np.float64),
-                              x=np.array(x.split(), dtype=np.float64),
-                              y=np.array(y.split(), dtype=np.float64),
-                              rounds=int(rounds)))
+            cases.append(dict(name=name, k=k, G=_numbers(G).reshape(k, k), g=_numbers(g),
+                              x=_numbers(x), y=_numbers(y), rounds=int(rounds)))
     return cases
 
 

@@ -1,7 +1,9 @@
 """Pins of the FP64 reference of the learned passive-set proposal (oracle/mlp.py):
 BF16 rounding against an independent implementation, features on hand-worked
-cases, gradients against central finite differences and closed forms, the first
-Adam step in closed form, and training that learns a simple rule."""
+cases, a hand-worked forward pass with nonzero weights and biases (with planted
+mistakes that it must catch), gradients against central finite differences and
+closed forms, the first Adam step in closed form, and training that learns a
+simple rule."""
 import numpy as np
 import pytest
 import torch
@@ -100,3 +102,60 @@ def test_training_learns_a_simple_rule():
         p, m, v = mlp.adam_step(p, g, m, v, t, 1e-2)
     assert loss < 0.25 * loss0
     assert (mlp.propose(p.astype(np.float32), F, k, h) == y).mean() > 0.95
+
+
+# A hand-worked forward pass, k = 1, hidden 2 (3 features). Every weight but
+# W1[0][0] is a BF16 value; W1[0][0] = 1 + 3*2^-9 lies between the BF16 neighbours
+# 1 and 1 + 2^-7, nearer the upper, so it is used as 1.0078125. Biases stay FP32.
+#   z1 = W1 f + b1 = (1.0078125 + 1 - 0.25 + 0.125, -1 + 1 - 1 - 0.5) = (1.8828125, -1.5)
+#   a1 = relu(z1) = (1.8828125, 0)
+#   z2 = W2 a1 + b2 = (1.8828125 + 0.25, 0.94140625 - 1.5) = (2.1328125, -0.55859375)
+#   a2 = (2.1328125, 0)
+#   logit = 2 * 2.1328125 + 4 * 0 - 1 = 3.265625
+HAND_F = np.array([[1.0, 2.0, -1.0]])
+HAND_PARAMS = np.array([1.0 + 3 * 2**-9, 0.5, 0.25, -1.0, 0.5, 1.0,   # W1 (2 x 3)
+                        0.125, -0.5,                                   # b1
+                        1.0, -2.0, 0.5, 1.0,                           # W2 (2 x 2)
+                        0.25, -1.5,                                    # b2
+                        2.0, 4.0,                                      # W3 (1 x 2)
+                        -1.0], dtype=np.float32)                       # b3
+HAND_Z1 = [1.8828125, -1.5]
+HAND_Z2 = [2.1328125, -0.55859375]
+HAND_LOGIT = 3.265625
+
+
+def pin_mlp_forward_hand(mod):
+    z1, a1, z2, a2, logits = mod.forward(HAND_PARAMS, HAND_F, 1, 2)
+    np.testing.assert_array_equal(z1[0], HAND_Z1)
+    np.testing.assert_array_equal(a1[0], [HAND_Z1[0], 0.0])
+    np.testing.assert_array_equal(z2[0], HAND_Z2)
+    np.testing.assert_array_equal(a2[0], [HAND_Z2[0], 0.0])
+    assert logits[0, 0] == HAND_LOGIT
+    assert bool(mod.propose(HAND_PARAMS, HAND_F, 1, 2)[0, 0])
+
+
+def test_forward_hand_worked():
+    pin_mlp_forward_hand(mlp)
+
+
+MLP_MUTANTS = {
+    "relu1_dropped": ("a1 = np.maximum(z1, 0.0)", "a1 = z1"),
+    "relu2_dropped": ("a2 = np.maximum(z2, 0.0)", "a2 = z2"),
+    "w1_not_rounded": ("z1 = F @ q(W1).T", "z1 = F @ np.asarray(W1, dtype=np.float64).T"),
+    "b3_dropped": ("logits = a2 @ q(W3).T + np.asarray(b3, dtype=np.float64)",
+                   "logits = a2 @ q(W3).T"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MLP_MUTANTS))
+def test_forward_mutant_is_caught(name):
+    # The mistake is planted in a copy of oracle/mlp.py's source, loaded as a
+    # separate module; the real module is untouched.
+    import types
+    old, new = MLP_MUTANTS[name]
+    src = open(mlp.__file__).read()
+    assert src.count(old) == 1, name
+    mod = types.ModuleType(f"mlp_mutant_{name}")
+    exec(compile(src.replace(old, new), f"<mutant {name}>", "exec"), mod.__dict__)
+    with pytest.raises(AssertionError):
+        pin_mlp_forward_hand(mod)

@@ -28,6 +28,10 @@ MUTANTS = {
     "pgrad_projection_sign": ("const double pj = x[j] > 0.0 ? gj : (gj < 0.0 ? gj : 0.0);",
                               "const double pj = x[j] > 0.0 ? gj : (gj > 0.0 ? gj : 0.0);"),
     "hals_no_projection": ("x[i] = (num > 0.0 ? num : 0.0) / gii;", "x[i] = num / gii;"),
+    # BPP's backup rule: alpha must be refilled whenever the infeasible count
+    # reaches a new low, and the single exchange takes the largest index.
+    "bpp_alpha_not_reset": ("beta = nv;\n            alpha = 3;", "beta = nv;"),
+    "bpp_backup_smallest_index": ("vmax = i;", "if (vmax < 0)\n                    vmax = i;"),
 }
 
 
