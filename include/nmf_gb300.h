@@ -174,6 +174,9 @@ nmf_status nmf_nls_bpp_get_shape(int32_t k, int32_t *warps, int32_t *chunk, int3
  *     nrhs is not limited.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     The address is kept for the life of the process: destroying the
+ *     device's primary context after that call (cudaDeviceReset) is not
+ *     supported, since later calls would use the old address.
  *   - All calls share the one array and it keeps the last call's contents:
  *     calls that overlap on the GPU (for example on two streams at once)
  *     race and corrupt each other's results. Keep them ordered.
@@ -279,6 +282,9 @@ typedef struct nmf_stats {
     int64_t kernel_launches;   /* CUDA kernels this handle has launched */
     double ms_proposal;        /* features, proposal and training (timing on) */
     int64_t graph_launches;    /* nmf_iterate calls run as one CUDA graph */
+    int64_t mm_splits_max;     /* largest number of CTAs sharing one output tile
+                                  along the contraction in a tensor-core product
+                                  (tall-skinny A splits the long contraction) */
 } nmf_stats;
 
 /* Create a handle. W0 (m x k) and Ht0 (n x k) are the device starting point

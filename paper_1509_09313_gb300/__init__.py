@@ -89,7 +89,7 @@ class nmf_stats(ctypes.Structure):
                 ("ms_gram", ctypes.c_double), ("ms_mm", ctypes.c_double),
                 ("ms_nls", ctypes.c_double), ("ms_objective", ctypes.c_double),
                 ("kernel_launches", _I64), ("ms_proposal", ctypes.c_double),
-                ("graph_launches", _I64)]
+                ("graph_launches", _I64), ("mm_splits_max", _I64)]
 
 
 def _sig(name, args, res=ctypes.c_int):
@@ -195,13 +195,38 @@ def _dev(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
     return t
 
 
+def _shape(t: torch.Tensor, shape: tuple, name: str) -> torch.Tensor:
+    """Exact shape check before any pointer reaches the library (a wrongly
+    sized buffer would otherwise be read or written out of bounds)."""
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
+
+
+def _out(out, rows: int, k: int, ref: torch.Tensor, name: str = "out") -> torch.Tensor:
+    """A caller's output buffer: contiguous float32 (rows x k) on ref's device;
+    allocated when None."""
+    if out is None:
+        return torch.empty((rows, k), dtype=torch.float32, device=ref.device)
+    _dev(out, torch.float32, name)
+    if out.device != ref.device:
+        raise ValueError(f"{name} must be on {ref.device}")
+    return _shape(out, (rows, k), name)
+
+
+def _matrix(t: torch.Tensor, name: str) -> torch.Tensor:
+    if t.dim() != 2:
+        raise ValueError(f"{name} must be a 2-D matrix")
+    return t
+
+
 def _prec(precision) -> int:
     return PRECISIONS[precision] if isinstance(precision, str) else int(precision)
 
 
 def nmf_gram(X: torch.Tensor, stream=None) -> torch.Tensor:
     """G = X^T X (k x k, float64) for X (rows x k, float32)."""
-    _dev(X, torch.float32, "X")
+    _matrix(_dev(X, torch.float32, "X"), "X")
     rows, k = X.shape
     G = torch.empty((k, k), dtype=torch.float64, device=X.device)
     _check(_c_gram(_ptr(X), rows, k, _ptr(G), _stream(stream)), "nmf_gram")
@@ -211,7 +236,7 @@ def nmf_gram(X: torch.Tensor, stream=None) -> torch.Tensor:
 def _local_update(fn, name, G, R, X, stream):
     _dev(G, torch.float64, "G")
     _dev(R, torch.float32, "R")
-    _dev(X, torch.float32, "X")
+    _matrix(_dev(X, torch.float32, "X"), "X")
     rows, k = X.shape
     if tuple(G.shape) != (k, k) or tuple(R.shape) != (rows, k):
         raise ValueError("G must be k x k and R rows x k")
@@ -236,7 +261,7 @@ def nmf_pgrad_sq(G: torch.Tensor, R: torch.Tensor, X: torch.Tensor, stream=None)
     (entries with x = 0 count only where the gradient is negative)."""
     _dev(G, torch.float64, "G")
     _dev(R, torch.float32, "R")
-    _dev(X, torch.float32, "X")
+    _matrix(_dev(X, torch.float32, "X"), "X")
     rows, k = X.shape
     if tuple(G.shape) != (k, k) or tuple(R.shape) != (rows, k):
         raise ValueError("G must be k x k and R rows x k")
@@ -252,12 +277,14 @@ def nmf_mm_dense(A: torch.Tensor, F: torch.Tensor, trans: bool, precision="fp32"
     F = W (m x k) -> n x k. A may have a row stride > n (2-D view)."""
     if A.dtype != torch.float32 or not A.is_cuda or A.dim() != 2 or A.stride(1) != 1:
         raise TypeError("A must be a row-major float32 CUDA matrix")
-    _dev(F, torch.float32, "F")
+    _matrix(_dev(F, torch.float32, "F"), "F")
     m, n = A.shape
     k = F.shape[1]
     rows = n if trans else m
-    if out is None:
-        out = torch.empty((rows, k), dtype=torch.float32, device=A.device)
+    _shape(F, (m if trans else n, k), "F")
+    if F.device != A.device:
+        raise ValueError("A and F must be on the same device")
+    out = _out(out, rows, k, A)
     _check(_c_mm_dense(_ptr(A), m, n, A.stride(0), _ptr(F), k, int(trans), _prec(precision),
                        _ptr(out), _stream(stream)), "nmf_mm_dense")
     return out
@@ -269,11 +296,13 @@ def nmf_mm_csr(rowptr, colidx, vals, cols: int, F: torch.Tensor, out=None,
     _dev(rowptr, torch.int64, "rowptr")
     _dev(colidx, torch.int32, "colidx")
     _dev(vals, torch.float32, "vals")
-    _dev(F, torch.float32, "F")
+    _matrix(_dev(F, torch.float32, "F"), "F")
     rows = rowptr.numel() - 1
     k = F.shape[1]
-    if out is None:
-        out = torch.empty((rows, k), dtype=torch.float32, device=F.device)
+    _shape(F, (cols, k), "F")
+    if colidx.numel() != vals.numel():
+        raise ValueError("colidx and vals must have the same length")
+    out = _out(out, rows, k, F)
     _check(_c_mm_csr(_ptr(rowptr), _ptr(colidx), _ptr(vals), rows, cols, _ptr(F), k, _ptr(out),
                      _stream(stream)), "nmf_mm_csr")
     return out
@@ -284,6 +313,8 @@ def nmf_csr_transpose(rowptr, colidx, vals, m: int, n: int, stream=None):
     _dev(colidx, torch.int32, "colidx")
     _dev(vals, torch.float32, "vals")
     nnz = colidx.numel()
+    if rowptr.numel() != m + 1 or vals.numel() != nnz:
+        raise ValueError("rowptr must have m + 1 entries and vals as many as colidx")
     dev = rowptr.device
     t_rowptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
     t_colidx = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)[:nnz]
@@ -319,11 +350,13 @@ def nmf_nls_bpp_tune(G: torch.Tensor, B: torch.Tensor, passive_in: torch.Tensor 
     every later solve of that k). Returns (warps per CTA, RHS per grab,
     group-tile pass on, X)."""
     _dev(G, torch.float64, "G")
-    _dev(B, torch.float32, "B")
+    _matrix(_dev(B, torch.float32, "B"), "B")
     nrhs, k = B.shape
+    _shape(G, (k, k), "G")
     X = torch.empty_like(B)
     if passive_in is not None:
         _dev(passive_in, torch.int64, "passive_in")
+        _shape(passive_in, (nrhs, (k + 63) // 64), "passive_in")
     d = nmf_nls_desc(k, nrhs, _ptr(G), _ptr(B), _ptr(X), _ptr(passive_in), None, None, None,
                      max_rounds)
     w, c, g = _I32(0), _I32(0), _I32(0)
@@ -347,9 +380,12 @@ def nmf_nls_bpp_get_shape(k: int) -> tuple[int, int, int]:
 
 def _nls_bpp(fn, name, G, B, passive_in, max_rounds, outputs, stream):
     _dev(G, torch.float64, "G")
-    _dev(B, torch.float32, "B")
+    _matrix(_dev(B, torch.float32, "B"), "B")
     nrhs, k = B.shape
     nwords = (k + 63) // 64
+    _shape(G, (k, k), "G")
+    if passive_in is not None:
+        _shape(passive_in, (nrhs, nwords), "passive_in")
     dev = B.device
     X = torch.empty_like(B)
     passive = rounds = status = None
@@ -371,10 +407,12 @@ def nmf_objective_dense(A: torch.Tensor, W: torch.Tensor, Ht: torch.Tensor, prec
                         stream=None) -> float:
     if A.dtype != torch.float32 or not A.is_cuda or A.dim() != 2 or A.stride(1) != 1:
         raise TypeError("A must be a row-major float32 CUDA matrix")
-    _dev(W, torch.float32, "W")
+    _matrix(_dev(W, torch.float32, "W"), "W")
     _dev(Ht, torch.float32, "Ht")
     f = ctypes.c_double(0.0)
     m, n = A.shape
+    _shape(W, (m, W.shape[1]), "W")
+    _shape(Ht, (n, W.shape[1]), "Ht")
     _check(_c_objective_dense(_ptr(A), m, n, A.stride(0), _ptr(W), _ptr(Ht), W.shape[1],
                               _prec(precision), ctypes.byref(f), _stream(stream)),
            "nmf_objective_dense")
@@ -393,10 +431,11 @@ class nmf_init:
                  start="cold", max_bpp_rounds: int = 100, objective_every: bool = True,
                  shape=None, stream=None, solver="bpp", split_copies: bool = True,
                  fused_products: bool = True):
-        _dev(W0, torch.float32, "W0")
-        _dev(Ht0, torch.float32, "Ht0")
+        _matrix(_dev(W0, torch.float32, "W0"), "W0")
+        _matrix(_dev(Ht0, torch.float32, "Ht0"), "Ht0")
         m, k = W0.shape
         n = Ht0.shape[0]
+        _shape(Ht0, (n, k), "Ht0")
         mat = nmf_matrix()
         if isinstance(A, torch.Tensor):
             if A.dtype != torch.float32 or not A.is_cuda or A.stride(1) != 1:
@@ -477,10 +516,11 @@ class nmf_init:
         return W, Ht
 
     def nmf_set_factors(self, W=None, Ht=None):
+        m, n, k = self.shape
         if W is not None:
-            _dev(W, torch.float32, "W")
+            _shape(_dev(W, torch.float32, "W"), (m, k), "W")
         if Ht is not None:
-            _dev(Ht, torch.float32, "Ht")
+            _shape(_dev(Ht, torch.float32, "Ht"), (n, k), "Ht")
         _check(_c_set_factors(self._h, _ptr(W), _ptr(Ht)), "nmf_set_factors")
         self._stream_obj.synchronize()
 
@@ -551,12 +591,12 @@ def nmf_mlp_features(G: torch.Tensor, B: torch.Tensor, Xprev=None, out=None,
                      stream=None) -> torch.Tensor:
     """nrhs x 3k features of right-hand sides B (nrhs x k) with Gram G (k x k FP64)."""
     _dev(G, torch.float64, "G")
-    _dev(B, torch.float32, "B")
-    if Xprev is not None:
-        _dev(Xprev, torch.float32, "Xprev")
+    _matrix(_dev(B, torch.float32, "B"), "B")
     nrhs, k = B.shape
-    if out is None:
-        out = torch.empty((nrhs, 3 * k), dtype=torch.float32, device=B.device)
+    _shape(G, (k, k), "G")
+    if Xprev is not None:
+        _shape(_dev(Xprev, torch.float32, "Xprev"), (nrhs, k), "Xprev")
+    out = _out(out, nrhs, 3 * k, B)
     _check(_c_mlp_features(_ptr(G), _ptr(B), _ptr(Xprev), nrhs, k, _ptr(out), _stream(stream)),
            "nmf_mlp_features")
     return out
@@ -582,15 +622,23 @@ class nmf_mlp_create:
         _check(_c_mlp_get_params(self._h, _ptr(out), _stream(stream)), "nmf_mlp_get_params")
         return out
 
+    def _features(self, F: torch.Tensor) -> torch.Tensor:
+        _matrix(_dev(F, torch.float32, "F"), "F")
+        return _shape(F, (F.shape[0], 3 * self.k), "F")
+
+    def _labels(self, passive: torch.Tensor, nrhs: int) -> torch.Tensor:
+        _dev(passive, torch.int64, "passive")
+        return _shape(passive, (nrhs, (self.k + 63) // 64), "passive")
+
     def nmf_mlp_forward(self, F: torch.Tensor, stream=None) -> torch.Tensor:
-        _dev(F, torch.float32, "F")
+        self._features(F)
         out = torch.empty((F.shape[0], self.k), dtype=torch.float32, device=F.device)
         _check(_c_mlp_forward(self._h, _ptr(F), F.shape[0], _ptr(out), _stream(stream)),
                "nmf_mlp_forward")
         return out
 
     def nmf_mlp_propose(self, F: torch.Tensor, stream=None) -> torch.Tensor:
-        _dev(F, torch.float32, "F")
+        self._features(F)
         nw = (self.k + 63) // 64
         out = torch.empty((F.shape[0], nw), dtype=torch.int64, device=F.device)
         _check(_c_mlp_propose(self._h, _ptr(F), F.shape[0], _ptr(out), _stream(stream)),
@@ -598,8 +646,7 @@ class nmf_mlp_create:
         return out
 
     def nmf_mlp_gradient(self, F: torch.Tensor, passive: torch.Tensor, stream=None):
-        _dev(F, torch.float32, "F")
-        _dev(passive, torch.int64, "passive")
+        self._labels(passive, self._features(F).shape[0])
         g = torch.empty(nmf_mlp_param_count(self.k, self.hidden), dtype=torch.float32,
                         device=F.device)
         loss = torch.empty(1, dtype=torch.float64, device=F.device)
@@ -609,8 +656,7 @@ class nmf_mlp_create:
 
     def nmf_mlp_train(self, F: torch.Tensor, passive: torch.Tensor, batch: int = 8192,
                       lr: float = 1e-3, stream=None) -> torch.Tensor:
-        _dev(F, torch.float32, "F")
-        _dev(passive, torch.int64, "passive")
+        self._labels(passive, self._features(F).shape[0])
         loss = torch.empty(1, dtype=torch.float64, device=F.device)
         _check(_c_mlp_train(self._h, _ptr(F), _ptr(passive), F.shape[0], batch, lr, _ptr(loss),
                             _stream(stream)), "nmf_mlp_train")

@@ -5,6 +5,7 @@
 
 #include <math.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -280,6 +281,7 @@ struct nmf_handle {
     bool timing = false;
     bool use_graph = false;                     // nmf_iterate captures a CUDA graph
     int64_t graph_launches = 0;                 // graphs launched by nmf_iterate
+    int64_t mm_splits_max = 0;                  // largest contraction split of a product
     cudaGraphExec_t graph_exec = nullptr;       // last instantiated iteration graph
     int32_t graph_iters = 0;                    // its iteration count
     int64_t launches = 0;                       // kernels launched by nmf_iterate / objective
@@ -365,6 +367,7 @@ nmf_status mm(nmf_handle *h, int trans, const float *F, float *out)
         return launch_spmm(h->t_rowptr, h->t_colidx, h->t_vals, c.n, F, c.k, out, h->stream);
     }
     if (c.precision == NMF_PREC_BF16X3) {
+        h->mm_splits_max = std::max<int64_t>(h->mm_splits_max, mm_tc_splits(c.m, c.n, trans));
         void *hi = trans ? h->at_hi : h->ar_hi, *lo = trans ? h->at_lo : h->ar_lo;
         if (hi)
             return launch_mm_tc_presplit(hi, lo, c.m, c.n, F, c.k, trans, out, nullptr, nullptr,
@@ -1014,6 +1017,7 @@ extern "C" nmf_status nmf_get_stats(nmf_handle *h, nmf_stats *out)
     out->kernel_launches = h->launches;
     out->ms_proposal = h->ms[4];
     out->graph_launches = h->graph_launches;
+    out->mm_splits_max = h->mm_splits_max;
     return NMF_OK;
 }
 

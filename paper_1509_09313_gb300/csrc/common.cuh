@@ -103,6 +103,9 @@ nmf_status launch_mm_tc(const float *A, int64_t m, int64_t n, int64_t lda, const
                         int k, int trans, float *out, void *work, size_t work_bytes,
                         cudaStream_t s);
 size_t mm_tc_work_bytes(int64_t m, int64_t n, int k, int trans);
+// Contraction splits (CTAs along the contraction per output tile) the plain
+// tensor-core product of this shape uses; 1 for the pass with the objective.
+int mm_tc_splits(int64_t m, int64_t n, int trans);
 // Same, and with W, Ht, f_dev non-null (trans = 0, k <= 64) the objective
 // f(W, H) = ||A - W H||^2 fused into the pass, written to *f_dev.
 nmf_status launch_mm_tc_obj(const float *A, int64_t m, int64_t n, int64_t lda, const float *F,

@@ -1141,6 +1141,11 @@ TcWork tc_work(int64_t m, int64_t n, int k, int trans, bool obj)
 
 }  // namespace
 
+int mm_tc_splits(int64_t m, int64_t n, int trans)
+{
+    return choose_splits(trans ? n : m, trans ? m : n);
+}
+
 size_t mm_tc_work_bytes(int64_t m, int64_t n, int k, int trans)
 {
     const size_t a = tc_work(m, n, k, trans, false).total;

@@ -159,3 +159,17 @@ def test_anls_with_learned_proposal_reaches_the_same_factors(nmf):
     print(f"rounds in iterations 5-8: learned {learned}, cold {cold_last4}")
     assert learned < 0.5 * cold_last4
     assert st["ms_proposal"] >= 0.0
+
+
+def test_forward_hand_worked(nmf):
+    # The hand-worked pass of tests/test_oracle_mlp.py (every intermediate
+    # value exact in FP32, so the GPU must reproduce the logit exactly): one
+    # weight is not a BF16 value and must be used rounded, and each ReLU
+    # zeroes one unit.
+    from tests.test_oracle_mlp import HAND_F, HAND_LOGIT, HAND_PARAMS
+    net = nmf.nmf_mlp_create(1, 2, dev(HAND_PARAMS))
+    z = net.nmf_mlp_forward(dev(HAND_F.astype(np.float32))).cpu().numpy()
+    assert z[0, 0] == np.float32(HAND_LOGIT)
+    P = nmf.passive_to_bool(net.nmf_mlp_propose(dev(HAND_F.astype(np.float32))), 1).cpu()
+    assert bool(P[0, 0])
+    net.nmf_mlp_destroy()
