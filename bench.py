@@ -63,8 +63,6 @@ def metric_name(solver: str) -> str:
     return METRIC if solver == "bpp" else f"ANLS-{solver.upper()} iterations/s"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
 
 # DRAM traffic per launch (read + write bytes) of the dominant kernel from one
 # ncu capture, keyed by (kernel, workload, precision); None until captured or
@@ -74,7 +72,7 @@ FP32_LANES_PER_SM = 128
 # pre-split A^T: 1.5464 GB + 18.8 MB in 6 splits), reads scaled by the element
 # ratio 16, writes by the rows (A H^T 96000 x 50 out; A^T W 3 splits of
 # 64000 x 50 there), averaged: 24.84 GB per launch against 24.61 GB of
-# algorithmic bytes (profiles/mm_tc_kernel_dense-medium.md).
+# algorithmic bytes.
 MLP_HIDDEN = 256     # width of the proposal network (3k -> 256 -> 256 -> k)
 
 NCU_TRAFFIC = {
@@ -159,6 +157,32 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
                 "samples": len(rows)}
+
+
+def fp32_peak_probe(nmf, gpu_index: int) -> dict:
+    """The FP32 FMA rate this GPU sustains, measured in-process by the
+    library's probe (eight independent chains per thread on every SM, scalar
+    FFMA and packed FFMA2; CUDA events), with the SM clock sampled while it
+    ran. No GPU setting is touched."""
+    sampler = ClockSampler(gpu_index)
+    sampler.start()
+    ffma = nmf.nmf_probe_fp32_fma(packed=False, launches=120) / 1e12
+    ffma2 = nmf.nmf_probe_fp32_fma(packed=True, launches=120) / 1e12
+    clocks = sampler.stop()
+    return {"tflops": max(ffma, ffma2), "ffma_tflops": ffma, "ffma2_tflops": ffma2,
+            "sm_mhz": clocks["sm_mhz"] if clocks else None}
+
+
+def alu_peak(probe: dict, clocks) -> tuple[float, str]:
+    """The probe's FP32 rate at the timed region's median SM clock."""
+    scale, how = 1.0, "probe clock not sampled"
+    if clocks and clocks.get("sm_mhz") and probe.get("sm_mhz"):
+        scale = clocks["sm_mhz"] / probe["sm_mhz"]
+        how = f"x {clocks['sm_mhz']:.0f} / {probe['sm_mhz']:.0f} MHz (timed / probe median)"
+    peak = probe["tflops"] * scale
+    src = (f"measured: FP32 FMA probe {probe['tflops']:.1f} TFLOP/s (FFMA {probe['ffma_tflops']:.1f}, "
+           f"FFMA2 {probe['ffma2_tflops']:.1f}) {how}")
+    return peak, src
 
 
 def oracle_sample(m, n, k, sigma, steps, warm: bool, solver="bpp"):
@@ -278,6 +302,7 @@ def run_stress(args, rank, world, local_rank):
     r = None
     for _ in range(args.warmup):
         r = nmf.nmf_nls_bpp(G, B, max_rounds=args.max_rounds)
+    probe = fp32_peak_probe(nmf, local_rank)
     torch.cuda.synchronize()
     barrier()
     sampler = ClockSampler(local_rank)
@@ -312,13 +337,12 @@ def run_stress(args, rank, world, local_rank):
     nbytes = 4.0 * nrhs * k * 2 + (8 + 4 + 1) * nrhs
     step_s = ms / 1000.0 / args.steps
     pk, pk_kind = peaks()
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fp32_peak, peak_src = alu_peak(probe, clocks)
     achieved = flops / step_s / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "kernel": "bpp_group_kernel",
             "timed": "the whole nmf_nls_bpp call (all its kernels)",
-            "peak_source": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                           f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max clock)",
+            "peak_source": peak_src,
             "achieved_gbs": nbytes / step_s / 1e9, "hbm_frac": nbytes / step_s / 1e9 / pk["hbm_gbs"],
             "traffic": None}
 
@@ -450,6 +474,9 @@ def run_ours(args, rank, world, local_rank):
     if learned:
         h.nmf_set_proposal(net, "use")
     warm_status = h.nmf_sync()
+    # The FP32 SIMT forms (plain FP32 products, sparse BPP) are quoted against
+    # the measured FP32 FMA rate.
+    probe = fp32_peak_probe(nmf, local_rank) if (sparse or args.precision == "fp32") else None
     st0 = h.nmf_get_stats()
     h.nmf_set_timing(True)
 
@@ -515,12 +542,11 @@ def run_ours(args, rank, world, local_rank):
                     "note": "no separate product pass: each right-hand side is gathered "
                             "inside the FP32 BPP solves"}
     elif args.precision == "fp32":
-        fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        fp32_peak, peak_src = alu_peak(probe, clocks)
         achieved = flops_mm / (mm_ms / 1000.0) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "kernel": "mm_simt_kernel",
-                "peak_source": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                               f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max clock)",
+                "peak_source": peak_src,
                 "achieved_gbs": bytes_mm / (mm_ms / 1000.0) / 1e9}
     else:
         achieved = bytes_mm / (mm_ms / 1000.0) / 1e9
@@ -547,13 +573,12 @@ def run_ours(args, rank, world, local_rank):
         flops_bpp = fsum * (1.0 + rounds_per)
         bytes_bpp = (m + n) * (8.0 * k + 16.0)
         t_bpp = 2 * nls_ms / 1000.0                   # both half-steps of one iteration
-        fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        fp32_peak, peak_src = alu_peak(probe, clocks)
         roof_products = roof
         roof = {"bound": "alu", "achieved": flops_bpp / t_bpp / 1e12, "peak": fp32_peak,
                 "unit": "TFLOP/s", "frac": flops_bpp / t_bpp / 1e12 / fp32_peak,
                 "kernel": "bpp_solve32_kernel",
-                "peak_source": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                               f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max clock)",
+                "peak_source": peak_src,
                 "flops_per_iteration": flops_bpp,
                 "achieved_gbs": bytes_bpp / t_bpp / 1e9,
                 "hbm_frac": bytes_bpp / t_bpp / 1e9 / pk["hbm_gbs"],

@@ -54,6 +54,18 @@ const char *nmf_status_str(nmf_status s);
  * entry point and handle; host-side counter, no synchronisation). */
 int64_t nmf_kernel_launches(void);
 
+/* FP32 FMA throughput of the current device (a measurement utility of this
+ * library, no counterpart in the paper): the FP32 SIMT kernels' arithmetic
+ * is quoted against this measured rate rather than a nominal one. Runs one
+ * untimed and `launches` timed launches (1..100000; each ~3e11 flops) of a
+ * kernel in which every thread advances eight independent FMA chains, scalar
+ * FFMA (packed = 0) or packed FP32x2 FFMA2 (packed = 1), on all SMs; times
+ * them with CUDA events on `stream` and writes the rate (flop/s, one FMA =
+ * 2 flops) to *flops_per_s (host). Synchronises `stream`. Changes no GPU
+ * setting. */
+nmf_status nmf_probe_fp32_fma(int32_t packed, int32_t launches, double *flops_per_s,
+                              void *stream);
+
 /* Arithmetic used for the two m*n*k products (A H^T and W^T A) and for the
  * objective:
  *   NMF_PREC_FP32   plain FP32 FMAs on the SIMT pipes;
@@ -303,7 +315,12 @@ nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nmf_matrix *A
 nmf_status nmf_iterate(nmf_handle *h, int32_t iters);
 
 /* Wait for the handle's stream; return the worst BPP status since the last
- * nmf_sync (NMF_OK, NMF_ERR_NOT_CONVERGED or NMF_ERR_SINGULAR_GRAM). */
+ * nmf_sync (NMF_OK, NMF_ERR_NOT_CONVERGED or NMF_ERR_SINGULAR_GRAM).
+ * Dense BF16x3 handles compute f of an iteration inside the next iteration's
+ * A H^T pass; the last iteration's f stays pending until the handle iterates
+ * again or the objective is read (nmf_objective, nmf_objective_history, which
+ * then run one A H^T pass for it). Neither nmf_sync nor nmf_get_stats
+ * computes it. */
 nmf_status nmf_sync(nmf_handle *h);
 
 /* f(W, H) of Eq. 1 for the current factors. Synchronises; *f_out is host. */

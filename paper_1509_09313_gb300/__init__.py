@@ -119,6 +119,7 @@ _c_nls_bpp_tune = _sig("nmf_nls_bpp_tune", [ctypes.POINTER(nmf_nls_desc), _P,
                                             ctypes.POINTER(_I32)])
 _c_nls_bpp_set_shape = _sig("nmf_nls_bpp_set_shape", [_I32, _I32, _I32, _I32])
 _c_kernel_launches = _sig("nmf_kernel_launches", [], _I64)
+_c_probe_fp32_fma = _sig("nmf_probe_fp32_fma", [_I32, _I32, ctypes.POINTER(ctypes.c_double), _P])
 _c_nls_bpp_get_shape = _sig("nmf_nls_bpp_get_shape", [_I32, ctypes.POINTER(_I32),
                                                       ctypes.POINTER(_I32), ctypes.POINTER(_I32)])
 _c_objective_dense = _sig("nmf_objective_dense",
@@ -150,7 +151,7 @@ _c_mlp_gradient = _sig("nmf_mlp_gradient", [_P, _P, _P, _I64, _P, _P, _P])
 _c_mlp_train = _sig("nmf_mlp_train", [_P, _P, _P, _I64, _I64, ctypes.c_float, _P, _P])
 _c_set_proposal = _sig("nmf_set_proposal", [_P, _P, _I32, _I32, _I64, ctypes.c_float])
 
-EXPORTED = ["nmf_status_str", "nmf_kernel_launches", "nmf_gram", "nmf_mm_dense", "nmf_mm_csr",
+EXPORTED = ["nmf_status_str", "nmf_kernel_launches", "nmf_probe_fp32_fma", "nmf_gram", "nmf_mm_dense", "nmf_mm_csr",
             "nmf_csr_transpose", "nmf_nls_bpp", "nmf_nls_bpp_noalloc", "nmf_nls_bpp_tune", "nmf_nls_bpp_set_shape",
             "nmf_nls_bpp_get_shape", "nmf_objective_dense", "nmf_init", "nmf_iterate", "nmf_sync",
             "nmf_objective", "nmf_objective_history", "nmf_get_factors", "nmf_set_factors",
@@ -168,6 +169,15 @@ def nmf_status_str(status: int) -> str:
 def nmf_kernel_launches() -> int:
     """CUDA kernels this process has launched through the library so far."""
     return int(_c_kernel_launches())
+
+
+def nmf_probe_fp32_fma(packed: bool = True, launches: int = 200, stream=None) -> float:
+    """Measured FP32 FMA throughput of the current GPU in flop/s (scalar FFMA
+    or packed FFMA2 chains on every SM; synchronises the stream)."""
+    out = ctypes.c_double(0.0)
+    _check(_c_probe_fp32_fma(int(bool(packed)), int(launches), ctypes.byref(out),
+                             _stream(stream)), "nmf_probe_fp32_fma")
+    return out.value
 
 
 def _check(status: int, what: str):

@@ -795,7 +795,8 @@ extern "C" nmf_status nmf_sync(nmf_handle *h)
 {
     if (!h)
         return NMF_ERR_INVALID_ARG;
-    NMF_TRY(flush_objective(h));
+    // A pending fused objective stays pending: the next iteration's A H^T
+    // pass computes it, or reading the objective flushes it.
     BppStats st;
     NMF_CUDA(cudaMemcpyAsync(&st, h->stats_dev, sizeof(BppStats), cudaMemcpyDeviceToHost,
                              h->stream));
@@ -995,7 +996,6 @@ extern "C" nmf_status nmf_get_stats(nmf_handle *h, nmf_stats *out)
 {
     if (!h || !out)
         return NMF_ERR_INVALID_ARG;
-    NMF_TRY(flush_objective(h));
     BppStats st;
     NMF_CUDA(cudaMemcpyAsync(&st, h->stats_dev, sizeof(BppStats), cudaMemcpyDeviceToHost,
                              h->stream));

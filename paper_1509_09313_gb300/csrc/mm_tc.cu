@@ -55,7 +55,9 @@
 // issuing thread (warp 14) runs these MMAs as soon as the stage lands. The
 // split warps, each owning 32 rows of the tile (their TMEM lane quarter),
 // subtract it from the FP32 A values they are about to split and add the
-// squared residuals (FP32 within a half row, FP64 across). The A H^T pass of
+// squared residuals into Kahan-compensated FP32 sums, one per thread, which
+// are added in FP64 across the CTA's threads at the end (one FP64 partial per
+// CTA, summed in a fixed order). The A H^T pass of
 // an ANLS iteration thereby yields f(W, H) of the previous iterate without
 // reading A again. A relative bias b of W H shifts f by about S b with
 // S = 2 mean(r) mean(WH) / mean(r^2) (|S| <= 4 on the dense workloads), far
