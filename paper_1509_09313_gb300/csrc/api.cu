@@ -99,6 +99,12 @@ extern "C" nmf_status nmf_mm_dense(const float *A, int64_t m, int64_t n, int64_t
         NMF_CUDA(w.alloc(wb));
         return launch_mm_tc(A, m, n, lda, F, k, trans, out, w.p, wb, s);
     }
+    if (mm_f32_supported(A, lda)) {
+        const size_t wb = mm_f32_work_bytes(m, n, k, trans);
+        TempBuf w(s);
+        NMF_CUDA(w.alloc(wb));
+        return launch_mm_f32(A, m, n, lda, F, k, trans, out, nullptr, nullptr, w.p, wb, s);
+    }
     return launch_mm_simt(A, m, n, lda, F, k, trans, out, s);
 }
 
@@ -262,8 +268,9 @@ struct nmf_handle {
     double *f_now = nullptr;
     double *pgw2 = nullptr, *pgh2 = nullptr;    // rings: squared projected gradient in W, in H
     double *pg_part = nullptr;
-    void *tc_work = nullptr;
+    void *tc_work = nullptr;                    // product workspace (tensor-core or FP32 path)
     size_t tc_work_bytes = 0;
+    bool f32 = false;                           // dense FP32: the packed-FMA product kernel
     void *at_hi = nullptr, *at_lo = nullptr;   // A^T pre-split, tile-major (dense BF16x3)
     void *ar_hi = nullptr, *ar_lo = nullptr;   // A pre-split, tile-major (dense BF16x3)
     int64_t *t_rowptr = nullptr;                // CSR of A^T (sparse input)
@@ -375,16 +382,23 @@ nmf_status mm(nmf_handle *h, int trans, const float *F, float *out)
         return launch_mm_tc(h->A.dense, c.m, c.n, h->A.lda, F, c.k, trans, out, h->tc_work,
                             h->tc_work_bytes, h->stream);
     }
+    if (h->f32)
+        return launch_mm_f32(h->A.dense, c.m, c.n, h->A.lda, F, c.k, trans, out, nullptr, nullptr,
+                             h->tc_work, h->tc_work_bytes, h->stream);
     return launch_mm_simt(h->A.dense, c.m, c.n, h->A.lda, F, c.k, trans, out, h->stream);
 }
 
 // f(W, H) into *f_dev. Sparse input: after an H half-step (after_h) Y holds
 // A^T W and GW = W^T W for the current W; otherwise both are formed here (Y
 // and GW are scratch between iterations).
-// A H^T into V with f(W, H) of the current factors fused (dense BF16x3).
+// A H^T into V with f(W, H) of the current factors fused (dense BF16x3, or
+// dense FP32 through the packed-FMA kernel).
 nmf_status mm_obj(nmf_handle *h, double *f_dev)
 {
     const nmf_config &c = h->cfg;
+    if (h->f32)
+        return launch_mm_f32(h->A.dense, c.m, c.n, h->A.lda, h->Ht, c.k, 0, h->V, h->W, f_dev,
+                             h->tc_work, h->tc_work_bytes, h->stream);
     if (h->ar_hi)
         return launch_mm_tc_presplit(h->ar_hi, h->ar_lo, c.m, c.n, h->Ht, c.k, 0, h->V, h->W,
                                      f_dev, h->tc_work, h->tc_work_bytes, h->stream);
@@ -652,7 +666,15 @@ extern "C" nmf_status nmf_init(nmf_handle **out, const nmf_config *cfg, const nm
     chk(dalloc(&h->pgw2, (size_t)F_HIST_CAP));
     chk(dalloc(&h->pgh2, (size_t)F_HIST_CAP));
     chk(dalloc(&h->pg_part, (size_t)pgrad_partials_len()));
-    h->fused_obj = c.input_kind == NMF_INPUT_DENSE && c.precision == NMF_PREC_BF16X3 && c.k <= 64;
+    h->f32 = c.input_kind == NMF_INPUT_DENSE && c.precision == NMF_PREC_FP32 &&
+             mm_f32_supported(A->dense, A->lda);
+    h->fused_obj = c.input_kind == NMF_INPUT_DENSE && c.k <= 64 &&
+                   (c.precision == NMF_PREC_BF16X3 || h->f32);
+    if (e == cudaSuccess && h->f32) {
+        h->tc_work_bytes = std::max(mm_f32_work_bytes(c.m, c.n, c.k, 0),
+                                    mm_f32_work_bytes(c.m, c.n, c.k, 1));
+        chk(cudaMalloc(&h->tc_work, h->tc_work_bytes));
+    }
     if (e == cudaSuccess && c.input_kind == NMF_INPUT_DENSE && c.precision == NMF_PREC_BF16X3) {
         h->tc_work_bytes = mm_tc_work_bytes(c.m, c.n, c.k, 0);
         const size_t b1 = mm_tc_work_bytes(c.m, c.n, c.k, 1);

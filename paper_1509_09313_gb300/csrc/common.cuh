@@ -98,6 +98,18 @@ nmf_status launch_gram(const float *X, int64_t rows, int k, double *G, double *p
 nmf_status launch_mm_simt(const float *A, int64_t m, int64_t n, int64_t lda, const float *F,
                           int k, int trans, float *out, cudaStream_t s);
 
+// Dense products in plain FP32 with packed FP32x2 FMAs (mm_f32.cu): A 16-byte
+// aligned with lda a multiple of 4 (mm_f32_supported). trans = 0 with W and
+// f_dev non-null (k <= 64) also writes f(W, H) = ||A - W H||^2 to *f_dev.
+// `work` holds mm_f32_work_bytes(m, n, k, trans) bytes.
+bool mm_f32_supported(const float *A, int64_t lda);
+size_t mm_f32_work_bytes(int64_t m, int64_t n, int k, int trans);
+nmf_status launch_mm_f32(const float *A, int64_t m, int64_t n, int64_t lda, const float *F, int k,
+                         int trans, float *out, const float *W, double *f_dev, void *work,
+                         size_t work_bytes, cudaStream_t s);
+// *f_dev = sum of partials[0..parts) in a fixed order (FP64).
+nmf_status launch_sum_partials(const double *partials, int parts, double *f_dev, cudaStream_t s);
+
 // Dense products on tcgen05 tensor cores with BF16 head/tail operand splits.
 nmf_status launch_mm_tc(const float *A, int64_t m, int64_t n, int64_t lda, const float *F,
                         int k, int trans, float *out, void *work, size_t work_bytes,

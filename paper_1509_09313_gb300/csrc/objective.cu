@@ -173,6 +173,14 @@ int obj_parts() { return 2 * sm_count(); }
 
 int64_t objective_partials_len() { return obj_parts(); }
 
+nmf_status launch_sum_partials(const double *partials, int parts, double *f_dev, cudaStream_t s)
+{
+    sum_partials_kernel<<<1, 256, 0, s>>>(partials, parts, 1.0, nullptr, nullptr, nullptr, 0,
+                                          f_dev);
+    NMF_LAUNCHED("sum_partials_kernel");
+    return NMF_OK;
+}
+
 nmf_status launch_objective_dense(const float *A, int64_t m, int64_t n, int64_t lda,
                                   const float *W, const float *Ht, int k, int precision,
                                   double *partials, double *f_dev, cudaStream_t s)
