@@ -49,10 +49,20 @@ SPARSE_DRAWS = {"sparse-large": 20000000, "sparse-medium": 2000000}
 # whole batch (its metric is right-hand sides per second, not iterations).
 STRESS = "bpp-stress"
 STRESS_ROWS, STRESS_K, STRESS_NRHS = 200000, 100, 1000000
-STRESS_DESC = ("batched NLS: 1000000 right-hand sides, k=100; G = W^T W of W 200000x100 "
-               "U[0,1) with 30% zeros; b drawn as W^T a for a U[0,1)^200000 (CLT form)")
+# name: (mean of a, description). With a uniform in [0, 1) every solution is
+# positive (the all-passive group); a = u - 0.45 gives solutions of mixed
+# signs (about 71 of 100 indices passive, 3-4 exchange rounds per
+# right-hand side).
+STRESS_WORKLOADS = {
+    STRESS: (0.5, "batched NLS: 1000000 right-hand sides, k=100; G = W^T W of W 200000x100 "
+                  "U[0,1) with 30% zeros; b drawn as W^T a for a U[0,1)^200000 (CLT form)"),
+    "bpp-stress-mixed": (0.05, "batched NLS: 1000000 right-hand sides, k=100; the same G; b "
+                               "drawn as W^T a for a = u - 0.45, u U[0,1)^200000 (CLT form): "
+                               "solutions of mixed signs"),
+}
 STRESS_METRIC = "BPP right-hand sides/s"
 STRESS_CPU_SAMPLE = 300000
+STRESS_CHECK = 10000      # right-hand sides of the oracle check (cpu_baseline leg)
 SEED = 1509
 METRIC = "ANLS-BPP iterations/s"
 
@@ -238,31 +248,61 @@ def oracle_sample_sparse(m, n, k, draws, steps, warm: bool, csr, solver="bpp"):
     return 1.0 / (dt * scale), sample, orc.num_threads(), dt
 
 
-def stress_oracle_sample(G, B, n):
+def stress_oracle_sample(G, B, n, keep=0):
     """The FP64 oracle (as it stands) on the first n right-hand sides of the
     stress batch. Returns (right-hand sides per second, sample text, threads,
-    seconds)."""
+    seconds, the oracle's (X, passive, rounds) of the first `keep`)."""
     import oracle
     Gh = G.cpu().numpy()
     Bs = B[:n].double().cpu().numpy()
     oracle.bpp(Gh, Bs[:100])                    # warm-up
     t0 = time.perf_counter()
-    oracle.bpp(Gh, Bs)
+    Xo, Po, Ro, _, _ = oracle.bpp(Gh, Bs)
     dt = time.perf_counter() - t0
     return (n / dt, f"oracle BPP on the first {n} right-hand sides of the same batch",
-            oracle.num_threads(), dt)
+            oracle.num_threads(), dt, (Xo[:keep], Po[:keep], Ro[:keep]))
+
+
+def stress_oracle_check(nmf, G, B, r, kept, k, margin):
+    """The GPU's solutions of the first right-hand sides against the oracle's
+    (kept from the timed oracle sample): relative error against the FP32
+    bound 20 cond(G) 6e-8, and passive sets and round counts on the
+    right-hand sides whose KKT margin is clear (every passive x_i at least
+    margin max|x|, every active y_i at least margin max|b|)."""
+    import numpy as np
+    Xo, Po, Ro = kept
+    n = Xo.shape[0]
+    Gh = G.cpu().numpy()
+    Bs = B[:n].double().cpu().numpy()
+    X = r["X"][:n].double().cpu().numpy()
+    P = nmf.passive_to_bool(r["passive"][:n], k).cpu().numpy()
+    R = r["rounds"][:n].cpu().numpy()
+    Pb = Po.astype(bool)
+    cond = float(np.linalg.cond(Gh))
+    err = float(np.linalg.norm(X - Xo) / np.linalg.norm(Xo))
+    Y = Xo @ Gh - Bs
+    xm = np.where(Pb, Xo, np.inf).min(axis=1) / np.maximum(np.abs(Xo).max(axis=1), 1e-300)
+    ym = np.where(~Pb, Y, np.inf).min(axis=1) / np.maximum(np.abs(Bs).max(axis=1), 1e-300)
+    ok = np.minimum(xm, ym) >= margin
+    return {"rhs": int(n), "rel_err": err, "bound": 20 * cond * 6e-8, "cond": cond,
+            "margin": margin, "margin_clear": float(ok.mean()),
+            "passive_equal_margin_clear": float((P[ok] == Pb[ok]).all(axis=1).mean())
+            if ok.any() else None,
+            "rounds_equal_margin_clear": float((R[ok] == Ro[ok]).mean()) if ok.any() else None,
+            "passive_equal_all": float((P == Pb).all(axis=1).mean())}
 
 
 def run_stress_reference(args, world):
     import torch
 
     from synth import torch_gen
+    mean_a, desc = STRESS_WORKLOADS[args.workload]
     G, B = torch_gen.stress_batch_device(torch.device("cpu"), STRESS_ROWS, STRESS_K,
-                                         max(STRESS_CPU_SAMPLE // 10, 1000))
+                                         max(STRESS_CPU_SAMPLE // 10, 1000), mean_a=mean_a)
     steps = max(1, args.steps)
     total_n, total_s = 0, 0.0
     for _ in range(steps):
-        v, sample, cores, dt = stress_oracle_sample(G, B, B.shape[0])
+        v, sample, cores, dt, _ = stress_oracle_sample(G, B, B.shape[0])
         total_n += B.shape[0]
         total_s += dt
     value = total_n / total_s
@@ -270,7 +310,7 @@ def run_stress_reference(args, world):
             "n_gpus": world, "steps": steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * STRESS_NRHS / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": STRESS_DESC},
+            "config": {"workload": desc},
             "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": cores, "kind": "oracle",
                              "sample": sample + f", {steps} times"},
             "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0,
@@ -290,8 +330,9 @@ def run_stress(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     k, nrhs = STRESS_K, STRESS_NRHS
+    mean_a, desc = STRESS_WORKLOADS[args.workload]
     t_gen = time.perf_counter()
-    G, B = torch_gen.stress_batch_device(dev, STRESS_ROWS, k, nrhs)
+    G, B = torch_gen.stress_batch_device(dev, STRESS_ROWS, k, nrhs, mean_a=mean_a)
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
 
@@ -336,11 +377,16 @@ def run_stress(args, rank, world, local_rank):
     flops = float((rounds * (2 * f * f + 2 * f * (k - f))).sum().item())
     nbytes = 4.0 * nrhs * k * 2 + (8 + 4 + 1) * nrhs
     step_s = ms / 1000.0 / args.steps
+    # Rounds per right-hand side, and the share the group-tile pass can take:
+    # right-hand sides whose first candidate (every index passive) was final.
+    rh = torch.bincount(r["rounds"].long().clamp(min=0)).cpu().tolist()
+    group_share = float(((r["rounds"] == 1) & (f == k)).double().mean().item())
     pk, pk_kind = peaks()
     fp32_peak, peak_src = alu_peak(probe, clocks)
     achieved = flops / step_s / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak, "kernel": "bpp_group_kernel",
+            "frac": achieved / fp32_peak,
+            "kernel": "bpp_group_kernel" if group_share >= 0.5 else "bpp_solve32_kernel",
             "timed": "the whole nmf_nls_bpp call (all its kernels)",
             "peak_source": peak_src,
             "achieved_gbs": nbytes / step_s / 1e9, "hbm_frac": nbytes / step_s / 1e9 / pk["hbm_gbs"],
@@ -367,25 +413,32 @@ def run_stress(args, rank, world, local_rank):
                "h2d_bytes_per_step": 4 * nrhs * k, "d2h_bytes_per_step": 4 * nrhs * k,
                "note": "upload B, nmf_nls_bpp, download X, every step"}
 
-    cpu = None
+    cpu, check = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, sample, cores, _ = stress_oracle_sample(G, B, STRESS_CPU_SAMPLE)
+        sample_n = STRESS_CPU_SAMPLE if mean_a >= 0.5 else STRESS_CPU_SAMPLE // 2
+        v, sample, cores, _, kept = stress_oracle_sample(G, B, sample_n, keep=STRESS_CHECK)
         cpu = {"value": v, "unit": "RHS/s", "cores": cores, "kind": "oracle", "sample": sample}
+        # Mixed partitions have ~30 active indices of 100, so few right-hand
+        # sides clear 1e-3; 3e-4 is still ~40 cond(G) 6e-8 (cond ~117).
+        check = stress_oracle_check(nmf, G, B, r, kept, k, 1e-3 if mean_a >= 0.5 else 3e-4)
 
     if rank == 0:
         line = {"metric": STRESS_METRIC, "value": value, "unit": "RHS/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
-                "config": {"workload": STRESS_DESC, "seed": SEED,
+                "config": {"workload": desc, "seed": SEED, "mean_a": mean_a,
                            "launch_shape": list(nmf.nmf_nls_bpp_get_shape(k)),
                            "l2": f"inputs larger than L2 (B = {4 * nrhs * k / 1e9:.1f} GB)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches,
                 "bpp": {"rounds_per_rhs": float(rounds.mean().item()),
+                        "rounds_histogram": rh,
                         "passive_per_rhs": float(f.mean().item()),
+                        "group_share": group_share, "per_warp_share": 1.0 - group_share,
                         "status": nmf.nmf_status_str(r["worst"])},
+                "oracle_check": check,
                 "setup_s": {"generate": t_gen}}
         print(json.dumps(line), flush=True)
 
@@ -393,7 +446,7 @@ def run_stress(args, rank, world, local_rank):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    if args.workload == STRESS:
+    if args.workload in STRESS_WORKLOADS:
         import oracle
         oracle.build()
         run_stress_reference(args, world)
@@ -698,7 +751,7 @@ def main():
     ap.add_argument("--start", choices=["cold", "warm", "learned"], default="warm",
                     help="BPP starting partitions: empty, the previous iteration's, or the "
                          "proposal network's (trained during the warm-up iterations)")
-    ap.add_argument("--workload", choices=sorted(list(WORKLOADS) + [STRESS]),
+    ap.add_argument("--workload", choices=sorted(list(WORKLOADS) + list(STRESS_WORKLOADS)),
                     default="dense-large")
     ap.add_argument("--pgrad", action="store_true",
                     help="record the projected-gradient stopping measure in every iteration")
@@ -727,7 +780,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    if args.workload == STRESS:
+    if args.workload in STRESS_WORKLOADS:
         run_stress(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)

@@ -20,8 +20,10 @@
 //    rows are 16 apart and its columns 16 apart, which spreads the warps'
 //    reads over all banks.
 //  - A^T W pairs consecutive output rows: {A[q][p], A[q][p+1]} (q-major tile)
-//    times {F[q][c], F[q][c]} (F is copied with every value twice); the
-//    thread's 8 rows and 4 columns are contiguous.
+//    times {F[q][c], F[q][c]} (the value paired with itself in registers:
+//    a copy with every value twice in shared memory would double the bytes
+//    each thread loads, and a warp's shared-memory bandwidth goes by those
+//    bytes); the thread's 8 rows and 4 columns are contiguous.
 // The partial sums of each stage (A H^T: two chains of 2 NCG steps; A^T W:
 // 32 steps) are added into the running totals with Kahan compensation, and
 // the output is the compensated total rounded once (with contraction splits:
@@ -58,7 +60,7 @@ constexpr int F32_BQ1 = 32;                // contraction steps per stage, trans
 // trans = 1 takes 64. Row strides are padded by 4 floats.
 template <int TRANS, int NCG, int RPT>
 struct F32Tile {
-    // Three stages; A^T W at most 144 registers, so that two CTAs share an
+    // Three stages; A^T W at most 128 registers, so that two CTAs share an
     // SM; A H^T (with the objective's W tile): one CTA.
     static constexpr int STAGES = 3;
     static constexpr int THREADS = 16 * NCG;
@@ -66,13 +68,13 @@ struct F32Tile {
     static constexpr int KP = 4 * NCG;
     static constexpr int BQ = TRANS == 0 ? 4 * NCG : F32_BQ1;
     static constexpr int LDA = TRANS == 0 ? BQ + 4 : BP + 4;   // A p-major / q-major
-    static constexpr int LDF = TRANS == 0 ? BQ + 4 : 2 * KP + 4;   // F^T c-major / F doubled q-major
+    static constexpr int LDF = TRANS == 0 ? BQ + 4 : KP + 4;   // F^T c-major / F q-major
     static constexpr int A = TRANS == 0 ? BP * LDA : BQ * LDA;
     static constexpr int F = TRANS == 0 ? KP * LDF : BQ * LDF;
     static constexpr int STAGE = A + F;                   // floats
     static constexpr int W = KP * BP;                     // objective: W^T of the CTA's rows
     static constexpr int ACH = TRANS == 0 ? BP * BQ / 4 : BQ * BP / 4;         // 16-byte chunks
-    static constexpr int FCH = TRANS == 0 ? KP * BQ / 4 : BQ * 2 * KP / 4;
+    static constexpr int FCH = KP * BQ / 4;
     static constexpr size_t bytes(bool obj)
     {
         return sizeof(float) * ((size_t)STAGES * STAGE + (obj ? W : 0)) + 64 * sizeof(double);
@@ -149,10 +151,10 @@ __device__ __forceinline__ void mm_f32_body(const float *__restrict__ A, int64_t
                 const float *src = Fc + (bytes ? (int64_t)(c0 + cr) * ldf + q : 0);
                 cp_async16(smem_addr(Fs + cr * T::LDF + 4 * qc), src, bytes);
             } else {
-                // F with every value twice: rows = q (ldf = 2 x padded columns).
-                const int qr = e / (KP / 2), cc = e % (KP / 2);
+                // F: rows = q (ldf = padded columns).
+                const int qr = e / (KP / 4), cc = e % (KP / 4);
                 const int64_t q = q0 + qr;
-                const float *src = Fc + (q < qe ? q * ldf + 2 * c0 + 4 * cc : 0);
+                const float *src = Fc + (q < qe ? q * ldf + c0 + 4 * cc : 0);
                 cp_async16(smem_addr(Fs + qr * T::LDF + 4 * cc), src, q < qe ? 16 : 0);
             }
         }
@@ -287,7 +289,7 @@ __device__ __forceinline__ void mm_f32_body(const float *__restrict__ A, int64_t
 #pragma unroll
                 for (int b = 0; b < 4; ++b)
                     pp[ap][b] = make_float2(0.0f, 0.0f);
-#pragma unroll 4
+#pragma unroll 1
             for (int q = 0; q < BQ; ++q) {
                 float2 av[RPT / 2];
 #pragma unroll
@@ -297,11 +299,9 @@ __device__ __forceinline__ void mm_f32_body(const float *__restrict__ A, int64_t
                     av[2 * v] = make_float2(a4.x, a4.y);
                     av[2 * v + 1] = make_float2(a4.z, a4.w);
                 }
-                const float4 f0 = *reinterpret_cast<const float4 *>(Fs + q * T::LDF + 4 * cg);
-                const float4 f1 =
-                    *reinterpret_cast<const float4 *>(Fs + q * T::LDF + KP + 4 * cg);
-                const float2 fd[4] = {make_float2(f0.x, f0.y), make_float2(f0.z, f0.w),
-                                      make_float2(f1.x, f1.y), make_float2(f1.z, f1.w)};
+                const float4 f4 = *reinterpret_cast<const float4 *>(Fs + q * T::LDF + 4 * cg);
+                const float2 fd[4] = {make_float2(f4.x, f4.x), make_float2(f4.y, f4.y),
+                                      make_float2(f4.z, f4.z), make_float2(f4.w, f4.w)};
 #pragma unroll
                 for (int b = 0; b < 4; ++b)
 #pragma unroll
@@ -390,8 +390,9 @@ __device__ __forceinline__ void mm_f32_body(const float *__restrict__ A, int64_t
     }
 }
 
-// A H^T (one CTA per SM) and A^T W (two CTAs per SM: at most 144 registers
-// for up to 224 threads, 128 for 256).
+// A H^T (one CTA per SM) and A^T W (two CTAs per SM: at most 128 registers,
+// since each of the SM's four quarters holds 16384 registers and up to four
+// of the two CTAs' warps).
 template <bool OBJ, int NCG, int RPT>
 __global__ void __launch_bounds__(16 * NCG, 1)
     mm_f32_kernel(const float *__restrict__ A, int64_t P, int64_t Q, int64_t lda,
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(16 * NCG, 1)
 }
 
 template <int NCG, int RPT>
-__global__ void __maxnreg__(NCG == 16 ? 128 : 144)
+__global__ void __maxnreg__(128)
     mm_f32_t_kernel(const float *__restrict__ A, int64_t P, int64_t Q, int64_t lda,
                     const float *__restrict__ Fc, int64_t ldf, int k, int64_t q_per_split,
                     float *__restrict__ out)
@@ -449,23 +450,17 @@ __global__ void f32_transpose_kernel(const float *__restrict__ F, int64_t Q, int
     }
 }
 
-// F with every value twice (trans = 1), in rows of 2 kpt floats: in chunk h
-// of kp columns, column c = h kp + 4 g + j goes to floats 2 h kp + (j / 2) kp
-// + 4 g + 2 (j % 2) and the one after (0 for c >= k). Column group g's two
-// 16-byte halves are then the g-th of two runs of 16-byte chunks, which the
-// warps read without bank conflicts.
-__global__ void f32_double_kernel(const float *__restrict__ F, int64_t Q, int k, int kp,
-                                  int kpt, float *__restrict__ Fd)
+// F padded to kpt columns (trans = 1): Fp[q][c] = F[q][c] for c < k, 0 up to
+// kpt.
+__global__ void f32_pad_kernel(const float *__restrict__ F, int64_t Q, int k, int kpt,
+                               float *__restrict__ Fp)
 {
     const int64_t total = Q * kpt;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = e / kpt;
         const int c = (int)(e - q * kpt);
-        const float v = c < k ? F[q * k + c] : 0.0f;
-        const int h = c / kp, g = (c % kp) / 4, j = c % 4;
-        const int64_t at = q * 2 * kpt + 2 * h * kp + (j / 2) * kp + 4 * g + 2 * (j % 2);
-        *reinterpret_cast<float2 *>(Fd + at) = make_float2(v, v);
+        Fp[e] = c < k ? F[q * k + c] : 0.0f;
     }
 }
 
@@ -490,21 +485,37 @@ F32Plan f32_plan(int64_t m, int64_t n, int k, int trans, bool obj)
     w.nch = (int)cdiv(k, w.kp);
     w.kpt = w.kp * w.nch;
     w.bp = 16 * (trans ? RPT1 : RPT0);
-    w.ldf = trans ? 2 * w.kpt : cdiv(w.Q > 0 ? w.Q : 1, 4) * 4;
-    // A^T W splits its contraction when the output tiles leave SMs idle
-    // (each split keeps at least 8 stages). A H^T never does, so that its
-    // products are the same with and without the fused objective.
+    w.ldf = trans ? w.kpt : cdiv(w.Q > 0 ? w.Q : 1, 4) * 4;
+    // A^T W splits its contraction (up to 16 ways, each split keeping at
+    // least 8 stages) so that its CTAs fill whole waves of two per SM: the
+    // fewest splits within 2% of the best wave efficiency. A H^T never
+    // splits, so that its products are the same with and without the fused
+    // objective.
     const int64_t tiles = cdiv(w.P > 0 ? w.P : 1, w.bp) * w.nch;
     const int64_t bq = trans ? F32_BQ1 : 4 * w.ncg;
     w.splits = 1;
-    while (trans && w.splits < 16 && tiles * w.splits < 2 * (int64_t)sm_count() &&
-           w.Q / (2 * w.splits) >= 8 * bq)
-        w.splits *= 2;
+    if (trans) {
+        const int64_t slots = 2 * (int64_t)sm_count();
+        auto eff = [&](int64_t sp) {
+            const int64_t ctas = tiles * sp;
+            return (double)ctas / (double)(cdiv(ctas, slots) * slots);
+        };
+        auto allowed = [&](int64_t sp) { return sp == 1 || w.Q / sp >= 8 * bq; };
+        double best = 0.0;
+        for (int64_t sp = 1; sp <= 16; ++sp)
+            if (allowed(sp))
+                best = std::max(best, eff(sp));
+        for (int64_t sp = 1; sp <= 16; ++sp)
+            if (allowed(sp) && eff(sp) >= best - 0.02) {
+                w.splits = (int)sp;
+                break;
+            }
+    }
     (void)obj;
     w.q_per_split = cdiv(cdiv(w.Q > 0 ? w.Q : 1, w.splits), bq) * bq;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     w.f_off = 0;
-    const size_t fbytes = trans ? sizeof(float) * (size_t)(w.Q > 0 ? w.Q : 1) * 2 * w.kpt
+    const size_t fbytes = trans ? sizeof(float) * (size_t)(w.Q > 0 ? w.Q : 1) * w.kpt
                                 : sizeof(float) * (size_t)w.kpt * w.ldf;
     w.part_off = al(fbytes);
     w.split_off = w.part_off + al(sizeof(double) * (size_t)cdiv(w.P > 0 ? w.P : 1, w.bp));
@@ -529,6 +540,14 @@ nmf_status launch_tile(const float *A, const F32Plan &w, int64_t lda, const floa
         NMF_LAUNCHED("mm_f32_kernel");
     } else {
         NMF_TRY(ensure_smem(mm_f32_t_kernel<NCG, RPT>, opt_in, smem));
+        static SmemOptIn carve;   // all of the SM's on-chip memory as shared memory
+        int dev = 0;
+        NMF_CUDA(cudaGetDevice(&dev));
+        if (dev >= 0 && dev < SmemOptIn::MAX_DEVICES && !carve.bytes[dev]) {
+            NMF_CUDA(cudaFuncSetAttribute(mm_f32_t_kernel<NCG, RPT>,
+                                          cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+            carve.bytes[dev] = 1;
+        }
         mm_f32_t_kernel<NCG, RPT><<<grid, T::THREADS, smem, s>>>(
             A, w.P, w.Q, lda, Fc, w.ldf, k, w.q_per_split, out);
         NMF_LAUNCHED("mm_f32_t_kernel");
@@ -583,8 +602,8 @@ nmf_status launch_mm_f32(const float *A, int64_t m, int64_t n, int64_t lda, cons
         const int64_t total = w.Q * (int64_t)w.kpt;
         const unsigned blocks = (unsigned)std::min<int64_t>(cdiv(total > 0 ? total : 1, 256),
                                                             (int64_t)sm_count() * 8);
-        f32_double_kernel<<<blocks, 256, 0, s>>>(F, w.Q, k, w.kp, w.kpt, Fc);
-        NMF_LAUNCHED("f32_double_kernel");
+        f32_pad_kernel<<<blocks, 256, 0, s>>>(F, w.Q, k, w.kpt, Fc);
+        NMF_LAUNCHED("f32_pad_kernel");
     }
     if (trans)
         NMF_TRY((launch_ncg<1, false>(A, w, lda, Fc, k, dst, nullptr, nullptr, s)));

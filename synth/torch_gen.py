@@ -80,17 +80,21 @@ def normal_device(seed: int, tensor_pair, rows: int, cols: int, device: torch.de
 
 
 def stress_batch_device(device: torch.device, rows: int = 200000, k: int = 100,
-                        nrhs: int = 1000000, seed: int = DEFAULT_SEED):
+                        nrhs: int = 1000000, seed: int = DEFAULT_SEED, mean_a: float = 0.5):
     """The batched-NLS stress inputs: G = W^T W of W = ``synth.stress_factor``
     (rows x k) and nrhs right-hand sides drawn from the distribution of W^T a
     for a uniform in [0, 1)^rows (central limit theorem: mean W^T 1 / 2,
     covariance G / 12), b = W^T 1 / 2 + L z / sqrt(12) with G = L L^T and z
     standard normal. Forming W^T a itself would cost 2 rows k nrhs flops.
+    mean_a shifts a (a = u + mean_a - 1/2, u uniform in [0, 1)): b = mean_a
+    W^T 1 + L z / sqrt(12). mean_a = 1/2 (the default) makes every solution
+    positive; a small mean_a gives solutions of mixed signs, so the passive
+    sets vary from one right-hand side to the next.
     Returns (G float64 k x k, B float32 nrhs x k), both on `device`. The
     factor L is taken on the host (input generation only)."""
     W = torch.from_numpy(stress_factor(rows, k, seed=seed)).to(device).double()
     G = W.T @ W
-    mean = 0.5 * W.sum(dim=0)
+    mean = mean_a * W.sum(dim=0)
     L = torch.linalg.cholesky(G.cpu()).to(device)
     B = torch.empty((nrhs, k), dtype=torch.float32, device=device)
     pair = (TID_STRESS_A, TID_NOISE_U2)

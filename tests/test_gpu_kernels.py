@@ -3,7 +3,7 @@
 Tolerances (derived from the arithmetic; the oracle is FP64):
   * Gram: FP32 products summed in FP32 over 32-row tiles, tiles in FP64:
     |err| <= 2e-6 * (|X|^T |X|) elementwise.
-  * Products (plain FP32): 16-term FP32 tile sums merged with Kahan
+  * Products (plain FP32): FP32 stage sums merged with Kahan
     compensation, so the result is near FP32 rounding:
     |err| <= 2e-6 * (|A| |F|) elementwise, and RMS relative error <= 2e-7.
   * BPP: FP32 factorisations of systems whose data (G and b rounded to FP32)
@@ -50,8 +50,12 @@ def test_gram(nmf, k, rows):
 
 
 # ----------------------------------------------------------------------------- products
+# Rows of A that are a multiple of 4 floats take the packed-FMA kernels (ragged
+# tiles, contraction splits of A^T W on the tall shapes); the others the
+# scalar-load kernel.
 @pytest.mark.parametrize("shape", [(1, 1), (37, 23), (129, 257), (300, 1000), (1000, 300),
-                                   (2050, 17)])
+                                   (2050, 17), (37, 24), (129, 260), (2050, 20), (8192, 40),
+                                   (40, 8192)])
 @pytest.mark.parametrize("k", [1, 5, 10, 16, 17, 50, 64, 100, 128])
 @pytest.mark.parametrize("trans", [0, 1])
 def test_mm_dense_fp32(nmf, shape, k, trans):
@@ -98,12 +102,14 @@ def test_mm_dense_bf16x3_needs_aligned_rows(nmf):
         nmf.nmf_mm_dense(A, F, False, precision="bf16x3")
 
 
+@pytest.mark.parametrize("pad", [2, 3])
 @pytest.mark.parametrize("trans", [0, 1])
-def test_mm_dense_strided_and_signed(nmf, trans):
-    # Leading dimension > n and not a multiple of 4 (scalar-load path), signed data.
+def test_mm_dense_strided_and_signed(nmf, trans, pad):
+    # Leading dimension n + pad > n, signed data: 519 floats (not a multiple
+    # of 4: scalar-load kernel) or 520 (packed-FMA kernels).
     m, n, k = 333, 517, 50
-    rng = np.random.default_rng(5)
-    Afull = rng.uniform(-1, 1, (m, n + 3)).astype(np.float32)
+    rng = np.random.default_rng(5 + pad)
+    Afull = rng.uniform(-1, 1, (m, n + pad)).astype(np.float32)
     F = rng.uniform(-1, 1, (n if trans == 0 else m, k)).astype(np.float32)
     Ad = dev(Afull)[:, :n]
     out = nmf.nmf_mm_dense(Ad, dev(F), bool(trans)).cpu().numpy().astype(np.float64)

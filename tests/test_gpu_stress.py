@@ -10,7 +10,12 @@ b = W^T 1 / 2 + L z / sqrt(12) with G = L L^T and z standard normal
 
 The launch is timed (printed); every status must be OK; a sample of 10^4
 right-hand sides is compared with the FP64 oracle: values within the FP32
-bound and passive sets equal wherever the KKT margin is clear."""
+bound and passive sets equal wherever the KKT margin is clear.
+
+The mixed variant shifts a to u - 0.45 (b = 0.05 W^T 1 + L z / sqrt(12)):
+the solutions have mixed signs, so no right-hand side is solved by its first
+candidate (every index passive) and the per-warp k = 100 solves, with their
+exchange rounds (Sec. 4.2, Eq. 4), do all the work."""
 import time
 
 import numpy as np
@@ -34,6 +39,68 @@ def nmf():
     return lib
 
 
+def _check_sample(nmf, G, B, r, min_clear, margin=1e-3):
+    """FP64 oracle on every 100th right-hand side: values within the FP32
+    bound, passive sets equal and round counts (98%) equal on right-hand sides
+    with a clear KKT margin (every passive x_i at least margin max|x|, every
+    active y_i at least margin max|b|). Returns the oracle's passive sets and
+    rounds."""
+    dev = B.device
+    idx = torch.arange(0, NRHS, 100, device=dev)
+    Gh = G.cpu().numpy()
+    Bs = B[idx].double().cpu().numpy()
+    Xo, Po, Ro, So, wo = oracle.bpp(Gh, Bs)
+    X = r["X"][idx].double().cpu().numpy()
+    P = nmf.passive_to_bool(r["passive"][idx], K).cpu().numpy()
+    cond = np.linalg.cond(Gh)
+    err = np.linalg.norm(X - Xo) / np.linalg.norm(Xo)
+    Y = Xo @ Gh - Bs
+    xm = np.where(Po, Xo, np.inf).min(axis=1) / np.maximum(np.abs(Xo).max(axis=1), 1e-300)
+    ym = np.where(~Po.astype(bool), Y, np.inf).min(axis=1) / np.maximum(np.abs(Bs).max(axis=1), 1e-300)
+    ok = np.minimum(xm, ym) >= margin
+    print(f"cond(G) {cond:.3e}, sample rel err {err:.2e}, margin-clear {ok.mean():.2f}")
+    assert err <= 20 * cond * 6e-8
+    assert ok.mean() > min_clear
+    assert np.array_equal(P[ok], Po.astype(bool)[ok])
+    R = r["rounds"][idx].cpu().numpy()
+    assert (R[ok] == Ro[ok]).mean() >= 0.98
+    assert (X[~P] == 0).all()
+    return Po.astype(bool), Ro
+
+
+def test_stress_mixed_signs_million_rhs(nmf):
+    dev = torch.device("cuda")
+    G, B = torch_gen.stress_batch_device(dev, ROWS, K, NRHS, mean_a=0.05)
+    torch.cuda.synchronize()
+    nmf.nmf_nls_bpp(G, B)                      # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r = nmf.nmf_nls_bpp(G, B)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    rounds = r["rounds"].double()
+    f = nmf.passive_to_bool(r["passive"], K).double().sum(dim=1)
+    first = ((r["rounds"] == 1) & (f == K)).double().mean().item()
+    print(f"BPP stress, mixed signs: {NRHS} RHS, k={K}: {ms:.2f} ms "
+          f"({NRHS / ms * 1e3:.3e} RHS/s), rounds mean {rounds.mean().item():.3f} max "
+          f"{int(rounds.max().item())}, |F| mean {f.mean().item():.1f}, solved by the first "
+          f"candidate {first:.4f}")
+    assert r["worst"] == nmf.NMF_OK
+    assert (r["status"] == 0).all()
+    # Mixed partitions: the per-warp solves did the work.
+    assert 55 <= f.mean().item() <= 85
+    assert rounds.mean().item() >= 2.5
+    assert first < 0.01
+    # With 100 indices per right-hand side, about 30 of them active, only ~5%
+    # of the right-hand sides have every index 1e-3 clear of the KKT
+    # boundary. cond(G) is ~117, so an FP32 solve moves x by ~7e-6 of its
+    # scale: a margin of 3e-4 is still 40x that, and ~40% clear it.
+    Po, Ro = _check_sample(nmf, G, B, r, min_clear=0.3, margin=3e-4)
+    assert 55 <= Po.sum(axis=1).mean() <= 85 and Ro.mean() >= 2.5
+
+
 def test_stress_one_launch_million_rhs(nmf):
     dev = torch.device("cuda")
     G, B = torch_gen.stress_batch_device(dev, ROWS, K, NRHS)
@@ -53,25 +120,7 @@ def test_stress_one_launch_million_rhs(nmf):
           f"host {1e3 * (time.perf_counter() - t0):.1f} ms")
     assert r["worst"] == nmf.NMF_OK
     assert (r["status"] == 0).all()
-    # FP64 oracle on every 100th right-hand side.
-    idx = torch.arange(0, NRHS, 100, device=dev)
-    Gh = G.cpu().numpy()
-    Bs = B[idx].double().cpu().numpy()
-    Xo, Po, Ro, So, wo = oracle.bpp(Gh, Bs)
-    X = r["X"][idx].double().cpu().numpy()
-    P = nmf.passive_to_bool(r["passive"][idx], K).cpu().numpy()
-    cond = np.linalg.cond(Gh)
-    err = np.linalg.norm(X - Xo) / np.linalg.norm(Xo)
-    print(f"cond(G) {cond:.3e}, sample rel err {err:.2e}")
-    assert err <= 20 * cond * 6e-8
-    Y = Xo @ Gh - Bs
-    xm = np.where(Po, Xo, np.inf).min(axis=1) / np.maximum(np.abs(Xo).max(axis=1), 1e-300)
-    ym = np.where(~Po.astype(bool), Y, np.inf).min(axis=1) / np.maximum(np.abs(Bs).max(axis=1), 1e-300)
-    ok = np.minimum(xm, ym) >= 1e-3
-    assert ok.mean() > 0.3
-    assert np.array_equal(P[ok], Po.astype(bool)[ok])
-    R = r["rounds"][idx].cpu().numpy()
-    assert (R[ok] == Ro[ok]).mean() >= 0.98
+    _check_sample(nmf, G, B, r, min_clear=0.3)
     # Autotuned launch shape for k = 100: same bits, timed again.
     warps, chunk, group, Xt = nmf.nmf_nls_bpp_tune(G, B)
     assert torch.equal(Xt, r["X"])
