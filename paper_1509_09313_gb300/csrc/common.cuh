@@ -220,6 +220,13 @@ nmf_status mlp_features(const double *G, const float *B, const float *Xp, int64_
                         float *F, cudaStream_t s);
 nmf_status mlp_logits(MlpNet *net, const float *F, int64_t n, float *logits, cudaStream_t s);
 nmf_status mlp_propose(MlpNet *net, const float *F, int64_t n, uint64_t *passive, cudaStream_t s);
+// Inference pass on the tensor cores (mlp_tc.cu): logits (rows x k) and / or
+// proposed passive sets (rows x ceil(k / 64) words), either nullable, from
+// the BF16-valued working weights. Supported for k and hidden width up to 256.
+bool mlp_tc_supported(int k, int h);
+nmf_status launch_mlp_tc_forward(int k, int h, const float *W1, const float *b1, const float *W2,
+                                 const float *b2, const float *W3, const float *b3, const float *F,
+                                 int64_t n, float *logits, uint64_t *bits, cudaStream_t s);
 nmf_status mlp_gradient(MlpNet *net, const float *F, const uint64_t *lab, int64_t n,
                         float *grad_out, double *loss_dev, cudaStream_t s);
 nmf_status mlp_train(MlpNet *net, const float *F, const uint64_t *lab, int64_t n, int64_t batch,

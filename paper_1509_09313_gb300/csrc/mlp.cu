@@ -12,7 +12,8 @@
 // binary cross-entropy against the solve's final passive set, Adam (0.9,
 // 0.999, 1e-8) on FP32 master weights.
 //
-// Kernels (all SIMT FP32):
+// Kernels (SIMT FP32; the inference pass runs on the tensor cores instead,
+// mlp_tc.cu, when k and h are at most 256):
 //   mlp_features_kernel  one warp per right-hand side, G in shared memory;
 //                        G x_p by shared-memory broadcast (as in the BPP solve).
 //   mlp_gemm_kernel      C = op(A) op(B) tiled 64 x 64 x 16, 4 x 4 per thread,
@@ -527,10 +528,26 @@ nmf_status mlp_features(const double *G, const float *B, const float *Xp, int64_
     return launch_features(G, B, Xp, nrhs, k, F, s);
 }
 
+namespace {
+
+// Inference on the tensor cores (mlp_tc.cu) when the widths allow it.
+nmf_status forward_tc(const MlpNet &net, const float *F, int64_t n, float *logits,
+                      uint64_t *bits, cudaStream_t s)
+{
+    const float *w = net.work;
+    return launch_mlp_tc_forward(net.k, net.h, w + net.off[0], w + net.off[1], w + net.off[2],
+                                 w + net.off[3], w + net.off[4], w + net.off[5], F, n, logits,
+                                 bits, s);
+}
+
+}  // namespace
+
 nmf_status mlp_propose(MlpNet *net, const float *F, int64_t n, uint64_t *passive, cudaStream_t s)
 {
     if (n == 0)
         return NMF_OK;
+    if (mlp_tc_supported(net->k, net->h))
+        return forward_tc(*net, F, n, nullptr, passive, s);
     Scratch mem(s);
     NMF_CUDA(mem.alloc(acts_bytes(*net, n, false)));
     const Acts a = carve(*net, n, false, mem.p);
@@ -546,6 +563,8 @@ nmf_status mlp_logits(MlpNet *net, const float *F, int64_t n, float *logits, cud
 {
     if (n == 0)
         return NMF_OK;
+    if (mlp_tc_supported(net->k, net->h))
+        return forward_tc(*net, F, n, logits, nullptr, s);
     Scratch mem(s);
     NMF_CUDA(mem.alloc(acts_bytes(*net, n, false)));
     const Acts a = carve(*net, n, false, mem.p);
