@@ -439,11 +439,12 @@ nmf_status solve_half(nmf_handle *h, int64_t rows, const double *G, const float 
     }
     const bool use = h->mlp && h->prop_mode == NMF_PROPOSAL_USE;
     const bool train = h->mlp && h->prop_mode == NMF_PROPOSAL_TRAIN;
-    if (use || train) {
+    if (use) {
+        PhaseTimer t(h, 4);
+        NMF_TRY(mlp_features_propose(h->mlp, G, R, X, rows, h->feat, passive, h->stream));
+    } else if (train) {
         PhaseTimer t(h, 4);
         NMF_TRY(mlp_features(G, R, X, rows, c.k, h->feat, h->stream));
-        if (use)
-            NMF_TRY(mlp_propose(h->mlp, h->feat, rows, passive, h->stream));
     }
     {
         PhaseTimer t(h, 2);

@@ -223,10 +223,22 @@ nmf_status mlp_propose(MlpNet *net, const float *F, int64_t n, uint64_t *passive
 // Inference pass on the tensor cores (mlp_tc.cu): logits (rows x k) and / or
 // proposed passive sets (rows x ceil(k / 64) words), either nullable, from
 // the BF16-valued working weights. Supported for k and hidden width up to 256.
+// The input is the features F (rows x 3k FP32), or, with F null, formed from
+// G, B and Xp as mlp_features does.
 bool mlp_tc_supported(int k, int h);
 nmf_status launch_mlp_tc_forward(int k, int h, const float *W1, const float *b1, const float *W2,
                                  const float *b2, const float *W3, const float *b3, const float *F,
-                                 int64_t n, float *logits, uint64_t *bits, cudaStream_t s);
+                                 const double *G, const float *B, const float *Xp, int64_t n,
+                                 float *logits, uint64_t *bits, cudaStream_t s);
+// Features of a batch straight into the first layer's BF16 hi / lo operand
+// (blocks of kpf >= k columns; rows of ldd >= 3 kpf columns, a multiple of 8).
+nmf_status launch_mlp_features_split(const double *G, const float *B, const float *Xp,
+                                     int64_t nrhs, int k, int kpf, int ldd, __nv_bfloat16 *hi,
+                                     __nv_bfloat16 *lo, cudaStream_t s);
+// Features and proposal of one half-step (F: rows x 3k FP32 scratch, used
+// only when the tensor-core pass does not apply).
+nmf_status mlp_features_propose(MlpNet *net, const double *G, const float *B, const float *Xp,
+                                int64_t n, float *F, uint64_t *passive, cudaStream_t s);
 nmf_status mlp_gradient(MlpNet *net, const float *F, const uint64_t *lab, int64_t n,
                         float *grad_out, double *loss_dev, cudaStream_t s);
 nmf_status mlp_train(MlpNet *net, const float *F, const uint64_t *lab, int64_t n, int64_t batch,

@@ -30,6 +30,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "tc_ptx.cuh"
 
 namespace nmf {
 namespace {
@@ -40,11 +41,16 @@ constexpr int MLP_MAX_SPLITS = 32;
 constexpr float ADAM_B1 = 0.9f, ADAM_B2 = 0.999f, ADAM_EPS = 1e-8f;
 
 // -------------------------------------------------------------- features
-template <int KW>
+// SPLIT: instead of Fout, the BF16 hi / lo pair the tensor-core layers read
+// (hi = bf16(v), lo = bf16(v - hi)): row j of hi and lo (ldd columns) holds
+// the three blocks of the features at columns [0, kpf), [kpf, 2 kpf),
+// [2 kpf, 3 kpf), zero-padded.
+template <int KW, bool SPLIT>
 __global__ void __launch_bounds__(256)
     mlp_features_kernel(const double *__restrict__ G, const float *__restrict__ B,
                         const float *__restrict__ Xp, int64_t nrhs, int k,
-                        float *__restrict__ Fout)
+                        float *__restrict__ Fout, int kpf, int ldd,
+                        __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo)
 {
     extern __shared__ float sh[];
     float *Gs = sh;                              // k x k
@@ -104,14 +110,43 @@ __global__ void __launch_bounds__(256)
             }
         }
         __syncwarp();
-        float *f = Fout + j * (3 * k);
+        if (!SPLIT) {
+            float *f = Fout + j * (3 * k);
 #pragma unroll
-        for (int s = 0; s < KW; ++s) {
-            const int i = lane + 32 * s;
-            if (i < k) {
-                f[i] = y[s] / d[s] * sc;
-                f[k + i] = logd[s];
-                f[2 * k + i] = x[s] * d[s] * sc;
+            for (int s = 0; s < KW; ++s) {
+                const int i = lane + 32 * s;
+                if (i < k) {
+                    f[i] = y[s] / d[s] * sc;
+                    f[k + i] = logd[s];
+                    f[2 * k + i] = x[s] * d[s] * sc;
+                }
+            }
+        } else {
+            __nv_bfloat16 *hr = hi + j * ldd, *lr = lo + j * ldd;
+            auto put = [&](int c, float v) {
+                const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                hr[c] = h;
+                lr[c] = __float2bfloat16_rn(fmaf(__bfloat162float(h), -1.0f, v));
+            };
+#pragma unroll
+            for (int s = 0; s < KW; ++s) {
+                const int i = lane + 32 * s;
+                if (i < k) {
+                    put(i, y[s] / d[s] * sc);
+                    put(kpf + i, logd[s]);
+                    put(2 * kpf + i, x[s] * d[s] * sc);
+                }
+            }
+            // Zero columns: [k, kpf) of each block, and [3 kpf, ldd).
+            const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+            for (int c = k + lane; c < kpf; c += 32)
+                for (int b = 0; b < 3; ++b) {
+                    hr[b * kpf + c] = z;
+                    lr[b * kpf + c] = z;
+                }
+            for (int c = 3 * kpf + lane; c < ldd; c += 32) {
+                hr[c] = z;
+                lr[c] = z;
             }
         }
     }
@@ -388,17 +423,17 @@ nmf_status launch_features(const double *G, const float *B, const float *Xp, int
         if (smem > 48 * 1024)
             NMF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
-        kern<<<blocks, 256, smem, s>>>(G, B, Xp, nrhs, k, F);
+        kern<<<blocks, 256, smem, s>>>(G, B, Xp, nrhs, k, F, 0, 0, nullptr, nullptr);
         NMF_LAUNCHED("mlp_features_kernel");
         return NMF_OK;
     };
     if (kw == 1)
-        return go(mlp_features_kernel<1>);
+        return go(mlp_features_kernel<1, false>);
     if (kw == 2)
-        return go(mlp_features_kernel<2>);
+        return go(mlp_features_kernel<2, false>);
     if (kw == 3)
-        return go(mlp_features_kernel<3>);
-    return go(mlp_features_kernel<4>);
+        return go(mlp_features_kernel<3, false>);
+    return go(mlp_features_kernel<4, false>);
 }
 
 // Activation buffers of one batch: z1, z2 (n x h), logits (n x k), and the
@@ -528,6 +563,34 @@ nmf_status mlp_features(const double *G, const float *B, const float *Xp, int64_
     return launch_features(G, B, Xp, nrhs, k, F, s);
 }
 
+nmf_status launch_mlp_features_split(const double *G, const float *B, const float *Xp,
+                                     int64_t nrhs, int k, int kpf, int ldd, __nv_bfloat16 *hi,
+                                     __nv_bfloat16 *lo, cudaStream_t s)
+{
+    if (nrhs == 0)
+        return NMF_OK;
+    if (kpf < k || 3 * kpf > ldd || (ldd % 8))
+        return NMF_ERR_INVALID_ARG;
+    const int kw = (k + 31) / 32;
+    const size_t smem = sizeof(float) * ((size_t)k * k + 8 * 32 * kw);
+    const unsigned blocks = (unsigned)std::min<int64_t>(cdiv(nrhs, 8), 4 * sm_count());
+    auto go = [&](auto kern) -> nmf_status {
+        if (smem > 48 * 1024)
+            NMF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+        kern<<<blocks, 256, smem, s>>>(G, B, Xp, nrhs, k, nullptr, kpf, ldd, hi, lo);
+        NMF_LAUNCHED("mlp_features_kernel");
+        return NMF_OK;
+    };
+    if (kw == 1)
+        return go(mlp_features_kernel<1, true>);
+    if (kw == 2)
+        return go(mlp_features_kernel<2, true>);
+    if (kw == 3)
+        return go(mlp_features_kernel<3, true>);
+    return go(mlp_features_kernel<4, true>);
+}
+
 namespace {
 
 // Inference on the tensor cores (mlp_tc.cu) when the widths allow it.
@@ -536,8 +599,8 @@ nmf_status forward_tc(const MlpNet &net, const float *F, int64_t n, float *logit
 {
     const float *w = net.work;
     return launch_mlp_tc_forward(net.k, net.h, w + net.off[0], w + net.off[1], w + net.off[2],
-                                 w + net.off[3], w + net.off[4], w + net.off[5], F, n, logits,
-                                 bits, s);
+                                 w + net.off[3], w + net.off[4], w + net.off[5], F, nullptr,
+                                 nullptr, nullptr, n, logits, bits, s);
 }
 
 }  // namespace
@@ -557,6 +620,21 @@ nmf_status mlp_propose(MlpNet *net, const float *F, int64_t n, uint64_t *passive
                                                                         passive);
     NMF_LAUNCHED("mlp_propose_kernel");
     return NMF_OK;
+}
+
+nmf_status mlp_features_propose(MlpNet *net, const double *G, const float *B, const float *Xp,
+                                int64_t n, float *F, uint64_t *passive, cudaStream_t s)
+{
+    if (n == 0)
+        return NMF_OK;
+    if (mlp_tc_supported(net->k, net->h)) {
+        const float *w = net->work;
+        return launch_mlp_tc_forward(net->k, net->h, w + net->off[0], w + net->off[1],
+                                     w + net->off[2], w + net->off[3], w + net->off[4],
+                                     w + net->off[5], nullptr, G, B, Xp, n, nullptr, passive, s);
+    }
+    NMF_TRY(launch_features(G, B, Xp, n, net->k, F, s));
+    return mlp_propose(net, F, n, passive, s);
 }
 
 nmf_status mlp_logits(MlpNet *net, const float *F, int64_t n, float *logits, cudaStream_t s)

@@ -283,11 +283,14 @@ __global__ void __launch_bounds__(ML_THREADS, 1)
     }
 }
 
-// src (rows x cols FP32, row stride cols) -> BF16 hi / lo (rows x ldd, zero
-// past cols), 8 columns per thread. lo may be null (hi only: for values that
-// are BF16 already).
+// src (rows x cols FP32, row stride cols) -> BF16 hi / lo (rows x ldd), 8
+// columns per thread, in blocks: source column b bs + i (i < bs) goes to
+// column b bd + i, every other column is zero (bs = bd = ldd: the plain
+// zero-padded copy). lo may be null (hi only: for values that are BF16
+// already).
 __global__ void mlp_tc_split_kernel(const float *__restrict__ src, int64_t rows, int cols, int ldd,
-                                    __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo)
+                                    int bs, int bd, __nv_bfloat16 *__restrict__ hi,
+                                    __nv_bfloat16 *__restrict__ lo)
 {
     const int chunks = ldd / 8;
     const int64_t total = rows * chunks;
@@ -297,8 +300,10 @@ __global__ void mlp_tc_split_kernel(const float *__restrict__ src, int64_t rows,
         const int c0 = (int)(e - r * chunks) * 8;
         float v[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            v[i] = c0 + i < cols ? src[r * cols + c0 + i] : 0.0f;
+        for (int i = 0; i < 8; ++i) {
+            const int d = c0 + i, b = d / bd, w = d - b * bd, sc = b * bs + w;
+            v[i] = (w < bs && sc < cols) ? src[r * cols + sc] : 0.0f;
+        }
         uint4 h, l;
         split8(v, h, l);
         *reinterpret_cast<uint4 *>(hi + r * ldd + c0) = h;
@@ -318,13 +323,17 @@ bool mlp_tc_supported(int k, int h)
 
 nmf_status launch_mlp_tc_forward(int k, int h, const float *W1, const float *b1, const float *W2,
                                  const float *b2, const float *W3, const float *b3, const float *F,
-                                 int64_t n, float *logits, uint64_t *bits, cudaStream_t s)
+                                 const double *G, const float *B, const float *Xp, int64_t n,
+                                 float *logits, uint64_t *bits, cudaStream_t s)
 {
     if (!mlp_tc_supported(k, h) || n < 0 || n > INT32_MAX)
         return NMF_ERR_INVALID_ARG;
     if (n == 0)
         return NMF_OK;
-    const int k1 = 3 * k, kp1 = pad(k1, ML_BK);     // features, padded K of layer 1
+    // Layer 1 reads the three blocks of the features (gradient, Gram
+    // diagonal, previous iterate; k each) at columns [0, kpf), [kpf, 2 kpf),
+    // [2 kpf, 3 kpf) of its operand, and W1's columns are placed to match.
+    const int k1 = 3 * k, kpf = pad(k, 16), kp1 = pad(3 * kpf, ML_BK);
     const int nph = pad(h, 32), kph = pad(nph, ML_BK);   // hidden width, padded K of layers 2, 3
     const int npk = pad(k, 32);
     const int nwords = (k + 63) / 64;
@@ -356,21 +365,24 @@ nmf_status launch_mlp_tc_forward(int k, int h, const float *W1, const float *b1,
     __nv_bfloat16 *w1 = take(w1b), *w2 = take(w2b), *w3 = take(w3b);
 
     // Weights (BF16 values) into zero-padded BF16 matrices; features into hi / lo.
-    auto split = [&](const float *src, int64_t rows, int cols, int prow, int ldd,
+    auto split = [&](const float *src, int64_t rows, int cols, int prow, int ldd, int bs, int bd,
                      __nv_bfloat16 *hi, __nv_bfloat16 *lo) -> nmf_status {
         if (prow > rows)   // zero rows past the matrix (padded output columns)
             NMF_CUDA(cudaMemsetAsync(hi + rows * ldd, 0,
                                      sizeof(__nv_bfloat16) * (size_t)(prow - rows) * ldd, s));
         const int64_t work = rows * (ldd / 8);
         const unsigned blocks = (unsigned)std::min<int64_t>(cdiv(work, 256), 8 * (int64_t)sm_count());
-        mlp_tc_split_kernel<<<blocks, 256, 0, s>>>(src, rows, cols, ldd, hi, lo);
+        mlp_tc_split_kernel<<<blocks, 256, 0, s>>>(src, rows, cols, ldd, bs, bd, hi, lo);
         NMF_LAUNCHED("mlp_tc_split_kernel");
         return NMF_OK;
     };
-    NMF_TRY(split(W1, h, k1, nph, kp1, w1, nullptr));
-    NMF_TRY(split(W2, h, h, nph, kph, w2, nullptr));
-    NMF_TRY(split(W3, k, h, npk, kph, w3, nullptr));
-    NMF_TRY(split(F, n, k1, (int)n, kp1, fhi, flo));
+    NMF_TRY(split(W1, h, k1, nph, kp1, k, kpf, w1, nullptr));
+    NMF_TRY(split(W2, h, h, nph, kph, kph, kph, w2, nullptr));
+    NMF_TRY(split(W3, k, h, npk, kph, kph, kph, w3, nullptr));
+    if (F)
+        NMF_TRY(split(F, n, k1, (int)n, kp1, k, kpf, fhi, flo));
+    else
+        NMF_TRY(launch_mlp_features_split(G, B, Xp, n, k, kpf, kp1, fhi, flo, s));
 
     auto layer = [&](const __nv_bfloat16 *ahi, const __nv_bfloat16 *alo, int kp,
                      const __nv_bfloat16 *w, int nout, int np, const float *bias, int relu,
