@@ -148,10 +148,11 @@ nmf_status nmf_nls_bpp(const nmf_nls_desc *d, void *stream);
 
 /* Launch-shape autotuner for the batched solve (an interface of this library,
  * no counterpart in the paper): times the solve kernels' candidate shapes
- * (warps per CTA x right-hand sides per grab of the work counter, with and
- * without the group-tile pass for the all-passive group) on this batch and
- * keeps the fastest for d->k; every later solve of that k in the process
- * (nmf_nls_bpp, handles) uses it. All shapes give bit-identical results. X
+ * (warps per CTA x right-hand sides per grab of the work counter, with the
+ * group-tile pass mode of the current shape, and without the pass when that
+ * mode is 1) on this batch and keeps the fastest for d->k; every later solve
+ * of that k in the process (nmf_nls_bpp, handles) uses it. All candidates
+ * give bit-identical results. X
  * receives the solution; passive_out, rounds_out and status_out are not
  * written. Synchronises `stream`; *warps, *chunk and *group (host, nullable)
  * get the chosen shape. */
@@ -159,14 +160,16 @@ nmf_status nmf_nls_bpp_tune(const nmf_nls_desc *d, void *stream, int32_t *warps,
                             int32_t *group);
 
 /* Sets the launch shape of every later solve of this k in the process, as the
- * tuner would (an interface of this library; results do not depend on it):
- * warps per CTA 1..16 (the FP64 solves use at most 8), right-hand sides per
- * grab of the work counter 1..1024, and group = 1 to run the group-tile pass
- * first in FP32 half-steps (right-hand sides whose first candidate partition
- * is all usable indices are solved together by tile products with the
- * preparation's inverse; the rest go to the per-warp solves), 0 not to.
- * Default {8, 8, 1}. Host-side only; NMF_ERR_INVALID_ARG outside these
- * ranges. */
+ * tuner would (an interface of this library): warps per CTA 1..16 (the FP64
+ * solves use at most 8), right-hand sides per grab of the work counter
+ * 1..1024, and the group-tile pass of FP32 half-steps (right-hand sides whose
+ * first candidate partition is all usable indices are solved together by
+ * tile products with the preparation's inverse; the rest go to the per-warp
+ * solves): group = 0 off, 1 on the SIMT pipes, 2 on the tensor cores (k <=
+ * 112). Warps, chunk and groups 0 and 1 do not change the results; group 2
+ * gives them to FP32 solve accuracy, not the same bits. Default {8, 8, 2}
+ * for k <= 112, {8, 8, 1} above. Host-side only; NMF_ERR_INVALID_ARG outside
+ * these ranges. */
 nmf_status nmf_nls_bpp_set_shape(int32_t k, int32_t warps, int32_t chunk, int32_t group);
 
 /* Reads the launch shape solves of this k use (host pointers, nullable). */

@@ -742,7 +742,10 @@ nmf_status launch_modes(const SolveParams &P, cudaStream_t s)
     // Mode 0 (FP32): the group-tile pass for the all-passive group first,
     // then the per-warp solves of what it left.
     if (P.group && !P.fused) {
-        NMF_TRY(launch_group32(P, s));
+        if (P.group == 2)
+            NMF_TRY(launch_group_tc(P, s));
+        else
+            NMF_TRY(launch_group32(P, s));
     }
     NMF_TRY(launch_solve32(P, s));
     if (P.fused) {
@@ -775,11 +778,14 @@ namespace {
 
 // Launch shape of the solve kernels per k (warps per CTA, right-hand sides per
 // grab of the work counter, whether the group-tile pass runs first):
-// {8, 8, on} until bpp_tune has measured the batch or the caller set one.
-// Every shape computes the same results: a right-hand side's arithmetic does
-// not depend on where it runs.
+// {8, 8, group pass on} until bpp_tune has measured the batch or the caller
+// set one; the group pass runs on the tensor cores (2) where k allows, else
+// on the SIMT pipes (1). Shapes with group 0 or 1 compute the same results
+// (a right-hand side's arithmetic does not depend on where it runs); group 2
+// solves the all-passive group with tensor-core products, to FP32 accuracy
+// but not the same bits.
 struct BppShape {
-    int warps = BPP_WARPS, chunk = 8, group = 1;
+    int warps = BPP_WARPS, chunk = 8, group = -1;   // -1: the default for k
 };
 std::mutex g_shape_mu;
 BppShape g_shape[NMF_MAX_K + 1];
@@ -787,7 +793,10 @@ BppShape g_shape[NMF_MAX_K + 1];
 BppShape shape_for(int k)
 {
     std::lock_guard<std::mutex> lock(g_shape_mu);
-    return g_shape[k];
+    BppShape sh = g_shape[k];
+    if (sh.group < 0)
+        sh.group = group_tc_supported(k) ? 2 : 1;
+    return sh;
 }
 
 SolveParams solve_params(int k, int64_t nrhs, const double *G, const float *B, float *X,
@@ -878,8 +887,12 @@ nmf_status bpp_tune(int k, int64_t nrhs, const double *G, const float *B, float 
                     const uint64_t *passive_in, int max_rounds, void *work, BppStats *stats_dev,
                     cudaStream_t s, int *warps_out, int *chunk_out, int *group_out)
 {
-    static const BppShape cand[] = {{16, 4, 1}, {16, 8, 1}, {8, 1, 1},  {8, 4, 1},
-                                    {8, 8, 1},  {8, 32, 1}, {4, 16, 1}, {8, 8, 0}};
+    // The candidates keep the group mode of the current shape (and try the
+    // pass off only beside the SIMT pass, whose results it shares), so every
+    // candidate gives the same bits.
+    const int gm = shape_for(k).group;
+    const BppShape cand[] = {{16, 4, gm}, {16, 8, gm}, {8, 1, gm},  {8, 4, gm},
+                             {8, 8, gm},  {8, 32, gm}, {4, 16, gm}, {8, 8, gm == 1 ? 0 : gm}};
     NMF_TRY(launch_bpp_prep(k, G, work, stats_dev, s));
     SolveParams P = solve_params(k, nrhs, G, B, X, passive_in, nullptr, nullptr, nullptr,
                                  max_rounds, work, stats_dev);
@@ -935,7 +948,7 @@ nmf_status bpp_tune(int k, int64_t nrhs, const double *G, const float *B, float 
 nmf_status bpp_set_shape(int k, int warps, int chunk, int group)
 {
     if (k < 1 || k > NMF_MAX_K || warps < 1 || warps > 16 || chunk < 1 || chunk > 1024 ||
-        (group != 0 && group != 1))
+        group < 0 || group > 2 || (group == 2 && !group_tc_supported(k)))
         return NMF_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_shape_mu);
     g_shape[k].warps = warps;

@@ -82,8 +82,12 @@ __device__ __forceinline__ T warp_max(T v)
 nmf_status launch_solve32(const SolveParams &P, cudaStream_t s);
 
 // Group-tile pass for the all-passive group (mode 0; returns at once
-// otherwise). X must not overlap B.
+// otherwise). X must not overlap B. launch_group32: SIMT (group = 1), the
+// same bits as the per-warp kernel; launch_group_tc: tensor cores (group =
+// 2, k <= 112).
 nmf_status launch_group32(const SolveParams &P, cudaStream_t s);
+bool group_tc_supported(int k);
+nmf_status launch_group_tc(const SolveParams &P, cudaStream_t s);
 
 }  // namespace bpp
 }  // namespace nmf

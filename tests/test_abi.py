@@ -67,15 +67,20 @@ def test_launch_shape_set_and_get(lib):
     lib.nmf_nls_bpp_get_shape.argtypes = [I] + [ctypes.POINTER(I)] * 3
     w, c, g = I(0), I(0), I(0)
     assert lib.nmf_nls_bpp_get_shape(50, ctypes.byref(w), ctypes.byref(c), ctypes.byref(g)) == 0
-    assert (w.value, c.value, g.value) == (8, 8, 1)        # the default
+    # The default: group pass on the tensor cores up to k = 112, SIMT above.
+    assert (w.value, c.value, g.value) == (8, 8, 2)
+    assert lib.nmf_nls_bpp_get_shape(120, ctypes.byref(w), ctypes.byref(c), ctypes.byref(g)) == 0
+    assert (w.value, c.value, g.value) == (8, 8, 1)
     assert lib.nmf_nls_bpp_set_shape(50, 16, 4, 0) == 0
     lib.nmf_nls_bpp_get_shape(50, ctypes.byref(w), ctypes.byref(c), ctypes.byref(g))
     assert (w.value, c.value, g.value) == (16, 4, 0)
+    assert lib.nmf_nls_bpp_set_shape(50, 8, 8, 1) == 0
     for bad in [(0, 8, 8, 1), (129, 8, 8, 1), (50, 0, 8, 1), (50, 17, 8, 1),
-                (50, 8, 0, 1), (50, 8, 1025, 1), (50, 8, 8, 2), (50, 8, 8, -1)]:
+                (50, 8, 0, 1), (50, 8, 1025, 1), (50, 8, 8, 3), (50, 8, 8, -1),
+                (113, 8, 8, 2)]:
         assert lib.nmf_nls_bpp_set_shape(*bad) == 1, bad
     assert lib.nmf_nls_bpp_get_shape(0, None, None, None) == 1
-    assert lib.nmf_nls_bpp_set_shape(50, 8, 8, 1) == 0
+    assert lib.nmf_nls_bpp_set_shape(50, 8, 8, 2) == 0
 
 
 class NlsDesc(ctypes.Structure):

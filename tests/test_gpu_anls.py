@@ -216,18 +216,27 @@ def test_sparse_fused_products_bitwise(nmf, k, start, ill):
     W0, Ht0 = synth.init_factors(m, n, k, seed=7)
     if ill:
         Ht0 = (Ht0 + 1000.0 * Ht0[:, :1]).astype(np.float32)
+    # The separate-SpMM path runs the group-tile pass first; its SIMT form
+    # (launch shape group = 1) gives the per-warp kernel's bits, so the two
+    # paths are compared with it (the tensor-core form is checked against the
+    # oracle in test_gpu_kernels.py).
+    old_shape = nmf.nmf_nls_bpp_get_shape(k)
+    nmf.nmf_nls_bpp_set_shape(k, old_shape[0], old_shape[1], 1)
     outs = []
-    for fused in (False, True):
-        h = nmf.nmf_init(tuple(dev(x) for x in csr), dev(W0), dev(Ht0), shape=(m, n),
-                         start=start, fused_products=fused)
-        h.nmf_iterate(T)
-        assert h.nmf_sync() == nmf.NMF_OK
-        W, Ht = h.nmf_get_factors()
-        pW, pH = h.nmf_get_passive()
-        st = h.nmf_get_stats()
-        outs.append((W.cpu(), Ht.cpu(), np.array(h.nmf_objective_history()), pW.cpu(), pH.cpu(),
-                     st))
-        h.nmf_destroy()
+    try:
+        for fused in (False, True):
+            h = nmf.nmf_init(tuple(dev(x) for x in csr), dev(W0), dev(Ht0), shape=(m, n),
+                             start=start, fused_products=fused)
+            h.nmf_iterate(T)
+            assert h.nmf_sync() == nmf.NMF_OK
+            W, Ht = h.nmf_get_factors()
+            pW, pH = h.nmf_get_passive()
+            st = h.nmf_get_stats()
+            outs.append((W.cpu(), Ht.cpu(), np.array(h.nmf_objective_history()), pW.cpu(),
+                         pH.cpu(), st))
+            h.nmf_destroy()
+    finally:
+        nmf.nmf_nls_bpp_set_shape(k, *old_shape)
     (W0_, H0_, f0, pW0, pH0, s0), (W1, H1, f1, pW1, pH1, s1) = outs
     print(f"k={k} {start} ill={ill}: f {f1} fp64 half-steps {s1['bpp_fp64_halfsteps']} "
           f"launches {s0['kernel_launches']} -> {s1['kernel_launches']}")

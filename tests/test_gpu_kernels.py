@@ -374,9 +374,10 @@ def group_cases(k):
 
 @pytest.mark.parametrize("k", [1, 5, 10, 33, 50, 64, 65, 100, 128])
 def test_bpp_group_pass_bitwise_equal(nmf, k):
-    # The group-tile pass forms each entry with the same operations in the same
-    # order as the per-warp kernel: the same X bits, passive sets, rounds and
-    # statuses with the pass on or off, on every path.
+    # The SIMT group-tile pass (launch shape group = 1) forms each entry with
+    # the same operations in the same order as the per-warp kernel: the same X
+    # bits, passive sets, rounds and statuses with the pass on or off, on every
+    # path.
     for name, G, B32, warm, cap in group_cases(k):
         pin = None if warm is None else nmf.bool_to_passive(torch.from_numpy(warm)).numpy()
         outs = []
@@ -390,6 +391,46 @@ def test_bpp_group_pass_bitwise_equal(nmf, k):
         assert np.array_equal(S1, S0) and w1 == w0, name
         if name == "positive":   # every solve in the group: one full exchange, all passive
             assert (R1 == 1).all() and (S1 == 0).all() and P1.all()
+
+
+@pytest.mark.parametrize("k", [1, 5, 10, 33, 50, 64, 65, 100, 112])
+def test_bpp_group_pass_tensor_cores(nmf, k):
+    # The tensor-core group pass (launch shape group = 2) forms the all-passive
+    # group's products from BF16 splits (G three-way): not the bits of the
+    # per-warp kernel, but FP32 solve accuracy. On every branch of the pass:
+    # values within the FP32 bound of the FP64 oracle, passive sets and round
+    # counts equal on right-hand sides with a clear KKT margin, and statuses
+    # equal to the per-warp kernel's (pass off) on those.
+    for name, G, B32, warm, cap in group_cases(k):
+        pin = None if warm is None else nmf.bool_to_passive(torch.from_numpy(warm)).numpy()
+        with shape_of(nmf, k, 8, 8, 0):
+            X0, P0, R0, S0, w0 = run_bpp(nmf, G, B32, passive_in=pin, max_rounds=cap)
+        with shape_of(nmf, k, 8, 8, 2):
+            X2, P2, R2, S2, w2 = run_bpp(nmf, G, B32, passive_in=pin, max_rounds=cap)
+        Bd = B32.astype(np.float64)
+        Xo, Po, Ro, So, wo = oracle.bpp(G, Bd, None if warm is None else warm.astype(np.uint8),
+                                        max_rounds=cap)
+        fin = np.isfinite(Bd).all(axis=1) & (So == 0)
+        ok = margin_ok(G, Bd[fin], Xo[fin], Po[fin].astype(bool))
+        cond = np.linalg.cond(G[np.ix_(np.diag(G) > 0, np.diag(G) > 0)])
+        err = np.linalg.norm(X2[fin] - Xo[fin]) / max(np.linalg.norm(Xo[fin]), 1e-300)
+        print(f"k={k} {name}: rel err {err:.2e} (bound {20 * cond * 6e-8:.1e}), "
+              f"margin-clear {ok.mean() if ok.size else 0:.2f}, rounds {R2.mean():.2f}")
+        assert err <= 20 * cond * 6e-8, name
+        if name == "fp64" and cond > 1e5:
+            # An FP64 half-step (its solves start from FP32-predicted
+            # partitions, so their round counts are not the oracle's): the pass
+            # stays off and the results are those of the pass-off run.
+            assert np.array_equal(X2, X0) and np.array_equal(R2, R0) and np.array_equal(S2, S0)
+            continue
+        assert np.array_equal(P2[fin][ok], Po[fin][ok].astype(bool)), name
+        if ok.any():
+            assert (R2[fin][ok] == Ro[fin][ok]).mean() >= 0.98, name
+        assert np.array_equal(S2[fin][ok], S0[fin][ok]), name
+        assert np.array_equal(S2[~fin] != 0, S0[~fin] != 0), name
+        assert (X2[fin] >= 0).all() and (X2[fin][~P2[fin]] == 0).all(), name
+        if name == "positive":   # every solve in the group: one full exchange, all passive
+            assert (R2 == 1).all() and (S2 == 0).all() and P2.all()
 
 
 def test_bpp_group_pass_matches_oracle(nmf):
