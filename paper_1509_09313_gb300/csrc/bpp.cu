@@ -63,7 +63,7 @@ constexpr int BPP_THREADS = BPP_WARPS * 32;
 
 // Workspace layout (bytes, 256-aligned pieces).
 struct WorkLayout {
-    size_t g32, m32, m64, usable, flags, counters, defer, total;
+    size_t g32, m32, m64, usable, flags, counters, defer, prep, total;
 };
 
 WorkLayout layout(int k)
@@ -78,6 +78,7 @@ WorkLayout layout(int k)
     w.flags = off; off += al(sizeof(int) * 4);
     w.counters = off; off += al(sizeof(unsigned long long) * CNT_WORDS);
     w.defer = off; off += al(sizeof(int64_t) * DEFER_CAP);
+    w.prep = off; off += al(sizeof(double) * (NMF_MAX_K + 2));   // 1 / L_aa, two norms
     w.total = off;
     return w;
 }
@@ -95,16 +96,38 @@ __device__ __forceinline__ int tri_row(int e)
 }
 
 // ---------------------------------------------------------------------------
-// Prep: FP64 Cholesky of G_UU, its inverse and the scaled cond_1; one CTA.
-// flags[0] = mode (0 FP32, 1 FP64 with M, 2 FP64 without M), flags[1] = |U|.
+// Prep: FP64 Cholesky of G_UU, its inverse and the scaled cond_1.
+// flags[0] = mode (0 FP32, 1 FP64 with M, 2 FP64 without M), flags[1] = |U|,
+// flags[2] = 1 while the inverse and cond_1 are left to the kernels below,
+// flags[3] counts their last kernel's finished CTAs.
+//
+// The factorisation runs on one CTA (a chain of pivots). When every index is
+// usable and k >= PREP_SPLIT_K, the rest spreads over the GPU (GB300's FP64
+// pipe does two operations per clock per SM, so one CTA spent most of the
+// preparation on them): L^{-1} one warp per column (bpp_prep_inv_kernel), M =
+// L^{-T} L^{-1} one CTA per column (bpp_prep_m_kernel), the column sums of
+// cond_1 and the symmetric copy of M one CTA per column
+// (bpp_prep_cond_kernel). All work inside M64: L in its lower triangle,
+// L^{-1} transposed in its strict upper triangle, then M's lower triangle
+// over L, then M's upper triangle over L^{-1}.
 // ---------------------------------------------------------------------------
 constexpr int PREP_THREADS = 256;
+constexpr int PREP_SPLIT_K = 48;
+
+// Sum over the 32 lanes (xor butterfly: every lane gets the same value).
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
 
 __global__ void __launch_bounds__(PREP_THREADS)
     bpp_prep_kernel(const double *__restrict__ G, int k, float *__restrict__ G32,
                     float *__restrict__ M32, double *__restrict__ M64,
                     uint32_t *__restrict__ usable_words, int *__restrict__ flags,
-                    unsigned long long *__restrict__ counters, BppStats *__restrict__ stats)
+                    unsigned long long *__restrict__ counters, BppStats *__restrict__ stats,
+                    double *__restrict__ prep)
 {
     extern __shared__ double sm[];
     // L: u x u, the Cholesky factor in its lower triangle (diagonal included)
@@ -170,12 +193,11 @@ __global__ void __launch_bounds__(PREP_THREADS)
         for (int i = j + 1 + tid; i < u; i += PREP_THREADS)
             L[i * u + j] *= rj;
         __syncthreads();
-        // Trailing lower triangle (a >= b > j), entries numbered row by row.
-        const int t = u - j - 1;
-        for (int e = tid; e < t * (t + 1) / 2; e += PREP_THREADS) {
-            const int ra = tri_row(e), rb = e - ra * (ra + 1) / 2;
-            const int a = j + 1 + ra, b = j + 1 + rb;
-            L[a * u + b] = fma(-L[a * u + j], L[b * u + j], L[a * u + b]);
+        // Trailing lower triangle (a >= b > j): rows by warp, columns by lane.
+        for (int a = j + 1 + (tid >> 5); a < u; a += PREP_THREADS / 32) {
+            const double laj = L[a * u + j];
+            for (int b = j + 1 + (tid & 31); b <= a; b += 32)
+                L[a * u + b] = fma(-laj, L[b * u + j], L[a * u + b]);
         }
         __syncthreads();
     }
@@ -183,10 +205,31 @@ __global__ void __launch_bounds__(PREP_THREADS)
         if (tid == 0) {
             flags[0] = 2;
             flags[1] = u;
+            flags[2] = 0;
             atomicAdd(&stats->fp64_halfsteps, 1ull);
         }
         return;
     }
+    if (u == k && k >= PREP_SPLIT_K) {
+        // L (lower triangle, diagonal included) and 1 / L_aa to the kernels
+        // that finish the preparation.
+        for (int e = tid; e < k * k; e += PREP_THREADS) {
+            const int a = e / k, b = e - a * k;
+            if (b <= a)
+                M64[e] = L[a * u + b];
+        }
+        for (int a = tid; a < k; a += PREP_THREADS)
+            prep[a] = rdiag[a];
+        if (tid == 0) {
+            prep[k] = 0.0;
+            prep[k + 1] = 0.0;
+            flags[2] = 1;
+            flags[3] = 0;
+        }
+        return;
+    }
+    if (tid == 0)
+        flags[2] = 0;
     // Columns of L^{-1} by forward substitution, one column per thread, into
     // the strict upper triangle of L (transposed).
     for (int c = tid; c < u; c += PREP_THREADS) {
@@ -235,6 +278,127 @@ __global__ void __launch_bounds__(PREP_THREADS)
         flags[1] = u;
         if (mode)
             atomicAdd(&stats->fp64_halfsteps, 1ull);
+    }
+}
+
+
+// (L^{-1})_ac, a > c, into M64[c][a]: one CTA per column c, the column's
+// forward substitution in its first warp, right-looking: lane a % 32 keeps
+// the pending sum of row a, s_a = -L_ac / L_cc - sum_{c < b < a} L_ab x_b,
+// adding the terms in increasing b (the order of the single-thread form, so
+// the values are the same); once x_b = s_b / L_bb is final its lane
+// broadcasts it and every later row takes its term. L's rows from c on are
+// staged in shared memory by the whole CTA first.
+constexpr int INV_THREADS = 256;
+
+__global__ void __launch_bounds__(INV_THREADS)
+    bpp_prep_inv_kernel(int k, double *__restrict__ M64, const double *__restrict__ prep,
+                        const int *__restrict__ flags)
+{
+    if (flags[2] != 1)
+        return;
+    extern __shared__ double inv_sm[];
+    double *Ls = inv_sm;               // k x k (lower triangle, rows c and on)
+    const int c = blockIdx.x;
+    for (int e = c * k + (int)threadIdx.x; e < k * k; e += INV_THREADS) {
+        const int a = e / k, b = e - a * k;
+        Ls[e] = b <= a ? M64[e] : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x >= 32)
+        return;
+    const int lane = threadIdx.x;
+    constexpr int T = (NMF_MAX_K + 31) / 32;
+    const double rc = prep[c];
+    double sr[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int a = lane + 32 * t;
+        sr[t] = (a > c && a < k) ? -Ls[a * k + c] * rc : 0.0;
+    }
+    for (int b = c + 1; b < k; ++b) {
+        const int owner = b & 31, slot = b >> 5;
+        double mine = 0.0;
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+            if (t == slot)
+                mine = sr[t];
+        const double xb = __shfl_sync(FULL, mine * prep[b], owner);
+        if (lane == owner)
+            M64[c * k + b] = xb;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int a = lane + 32 * t;
+            if (a > b && a < k)
+                sr[t] = fma(-Ls[a * k + b], xb, sr[t]);
+        }
+    }
+}
+
+// M_ab = sum_{c >= a} (L^{-1})_ca (L^{-1})_cb for a >= b into M64[a][b] (and
+// M32 both ways): one CTA per column b, one warp per entry.
+__global__ void __launch_bounds__(128)
+    bpp_prep_m_kernel(int k, double *__restrict__ M64, float *__restrict__ M32,
+                      const double *__restrict__ prep, const int *__restrict__ flags)
+{
+    if (flags[2] != 1)
+        return;
+    const int b = blockIdx.x, lane = threadIdx.x & 31;
+    for (int a = b + (threadIdx.x >> 5); a < k; a += 4) {
+        double part = 0.0;
+        for (int c = a + lane; c < k; c += 32) {
+            const double xa = c == a ? prep[a] : M64[a * k + c];
+            const double xb = c == b ? prep[b] : M64[b * k + c];
+            part = fma(xa, xb, part);
+        }
+        const double m = warp_sum_d(part);
+        if (lane == 0) {
+            M64[a * k + b] = m;
+            M32[a * k + b] = (float)m;
+            M32[b * k + a] = (float)m;
+        }
+    }
+}
+
+// Column c of the scaled cond_1 (max column sum of |G_ac| / (d_a d_c) and of
+// |M_ac| d_a d_c, d_a = sqrt(G_aa)) from M's lower triangle, and M's upper
+// triangle in column c; the last CTA sets the mode.
+__global__ void __launch_bounds__(32)
+    bpp_prep_cond_kernel(const double *__restrict__ G, int k, double *__restrict__ M64,
+                         double *__restrict__ prep, int *__restrict__ flags,
+                         BppStats *__restrict__ stats)
+{
+    if (flags[2] != 1)
+        return;
+    const int c = blockIdx.x, lane = threadIdx.x;
+    double sg = 0.0, sm = 0.0;
+    for (int a = lane; a < k; a += 32) {
+        const double da = sqrt(G[a * k + a]);
+        sg += fabs(G[a * k + c]) / da;
+        sm += fabs(a >= c ? M64[a * k + c] : M64[c * k + a]) * da;
+    }
+    const double dc = sqrt(G[c * k + c]);
+    sg = warp_sum_d(sg) / dc;
+    sm = warp_sum_d(sm) * dc;
+    for (int a = lane; a < c; a += 32)
+        M64[a * k + c] = M64[c * k + a];
+    if (lane == 0) {
+        unsigned long long *norm = reinterpret_cast<unsigned long long *>(prep + k);
+        // Non-negative doubles order like their bit patterns.
+        atomicMax(&norm[0], (unsigned long long)__double_as_longlong(sg));
+        atomicMax(&norm[1], (unsigned long long)__double_as_longlong(sm));
+        __threadfence();
+        if (atomicAdd(&flags[3], 1) == k - 1) {
+            __threadfence();
+            const double cond = __longlong_as_double((long long)atomicAdd(&norm[0], 0ull)) *
+                                __longlong_as_double((long long)atomicAdd(&norm[1], 0ull));
+            const int mode = cond <= COND_FP32 ? 0 : 1;
+            flags[0] = mode;
+            flags[1] = k;
+            flags[2] = 0;
+            if (mode)
+                atomicAdd(&stats->fp64_halfsteps, 1ull);
+        }
     }
 }
 
@@ -855,11 +1019,26 @@ nmf_status launch_bpp_prep(int k, const double *G, void *work, BppStats *stats_d
     const size_t prep_smem = sizeof(double) * ((size_t)k * k + 3 * k) + sizeof(int) * (size_t)k;
     static SmemOptIn opt_in;
     NMF_TRY(ensure_smem(bpp_prep_kernel, opt_in, prep_smem));
+    double *prep = reinterpret_cast<double *>(static_cast<unsigned char *>(work) + layout(k).prep);
     bpp_prep_kernel<<<1, PREP_THREADS, prep_smem, s>>>(
         G, k, const_cast<float *>(P.G32), const_cast<float *>(P.M32),
         const_cast<double *>(P.M64), const_cast<uint32_t *>(P.usable_words),
-        const_cast<int *>(P.flags), P.counters, stats_dev);
+        const_cast<int *>(P.flags), P.counters, stats_dev, prep);
     NMF_LAUNCHED("bpp_prep_kernel");
+    if (k >= PREP_SPLIT_K) {   // (each returns at once unless the prep left them the work)
+        const size_t inv_smem = sizeof(double) * (size_t)k * k;
+        static SmemOptIn inv_opt_in;
+        NMF_TRY(ensure_smem(bpp_prep_inv_kernel, inv_opt_in, inv_smem));
+        bpp_prep_inv_kernel<<<(unsigned)k, INV_THREADS, inv_smem, s>>>(
+            k, const_cast<double *>(P.M64), prep, P.flags);
+        NMF_LAUNCHED("bpp_prep_inv_kernel");
+        bpp_prep_m_kernel<<<(unsigned)k, 128, 0, s>>>(k, const_cast<double *>(P.M64),
+                                                      const_cast<float *>(P.M32), prep, P.flags);
+        NMF_LAUNCHED("bpp_prep_m_kernel");
+        bpp_prep_cond_kernel<<<(unsigned)k, 32, 0, s>>>(G, k, const_cast<double *>(P.M64), prep,
+                                                       const_cast<int *>(P.flags), stats_dev);
+        NMF_LAUNCHED("bpp_prep_cond_kernel");
+    }
     return NMF_OK;
 }
 

@@ -284,19 +284,37 @@ __global__ void __launch_bounds__(GC_THREADS, 1) bpp_group_tc_kernel(const Solve
         unsigned long long st_rhs = 0, st_rounds = 0, st_max = 0, st_nf = 0, pending = 0;
         uint32_t ph = 0;
         bool dead = false;   // a wait of this warp timed out: only mark from now on
+        // Rows of B and X start on 16 bytes when k is a multiple of 4 (the
+        // bases come from the allocator, 256-byte aligned, checked here).
+        const bool vec4 = (k & 3) == 0 &&
+                          ((reinterpret_cast<uintptr_t>(P.B) | reinterpret_cast<uintptr_t>(P.X)) & 15) == 0;
         for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const int64_t j = t * GC_BM + rl;
             const bool live = j < P.nrhs;
-            // This part's columns of the right-hand side, in registers.
+            // This part's columns of the right-hand side, in registers (16-byte
+            // loads when the rows are 16-byte aligned: scalar loads flood the
+            // load queue).
             float g[MYCH][16];
             {
                 const float *row = P.B + (live ? j : 0) * k;
 #pragma unroll
                 for (int m = 0; m < MYCH; ++m)
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int c = 16 * (part + GC_PARTS * m) + i;
-                        g[m][i] = live && c < k ? row[c] : 0.0f;
+                    for (int q = 0; q < 4; ++q) {
+                        const int c = 16 * (part + GC_PARTS * m) + 4 * q;
+                        if (vec4) {
+                            const float4 v = live && c < k
+                                                 ? *reinterpret_cast<const float4 *>(row + c)
+                                                 : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                            g[m][4 * q] = v.x;
+                            g[m][4 * q + 1] = v.y;
+                            g[m][4 * q + 2] = v.z;
+                            g[m][4 * q + 3] = v.w;
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                g[m][4 * q + i] = live && c + i < k ? row[c + i] : 0.0f;
+                        }
                     }
             }
             // Membership: the first candidate partition is U (the test of the
@@ -505,10 +523,21 @@ __global__ void __launch_bounds__(GC_THREADS, 1) bpp_group_tc_kernel(const Solve
 #pragma unroll
                 for (int m = 0; m < MYCH; ++m)
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int c = 16 * (part + GC_PARTS * m) + i;
-                        if (c < k)
-                            xr[c] = x1[m][i] > 0.0f ? x1[m][i] : 0.0f;
+                    for (int q = 0; q < 4; ++q) {
+                        const int c = 16 * (part + GC_PARTS * m) + 4 * q;
+                        float v[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            v[i] = x1[m][4 * q + i] > 0.0f ? x1[m][4 * q + i] : 0.0f;
+                        if (vec4) {
+                            if (c < k)
+                                *reinterpret_cast<float4 *>(xr + c) = make_float4(v[0], v[1], v[2], v[3]);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                if (c + i < k)
+                                    xr[c + i] = v[i];
+                        }
                     }
                 if (part == 0) {
                     const bool fin = fin_f == 0.0f;
