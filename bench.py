@@ -386,7 +386,8 @@ def run_stress(args, rank, world, local_rank):
     achieved = flops / step_s / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak,
-            "kernel": "bpp_group_kernel" if group_share >= 0.5 else "bpp_solve32_kernel",
+            "kernel": ("bpp_group_tc_kernel" if nmf.nmf_nls_bpp_get_shape(k)[2] == 2
+                       else "bpp_group_kernel") if group_share >= 0.5 else "bpp_solve32_kernel",
             "timed": "the whole nmf_nls_bpp call (all its kernels)",
             "peak_source": peak_src,
             "achieved_gbs": nbytes / step_s / 1e9, "hbm_frac": nbytes / step_s / 1e9 / pk["hbm_gbs"],

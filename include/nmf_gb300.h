@@ -168,8 +168,8 @@ nmf_status nmf_nls_bpp_tune(const nmf_nls_desc *d, void *stream, int32_t *warps,
  * solves): group = 0 off, 1 on the SIMT pipes, 2 on the tensor cores (k <=
  * 112). Warps, chunk and groups 0 and 1 do not change the results; group 2
  * gives them to FP32 solve accuracy, not the same bits. Default {8, 8, 2}
- * for k <= 112, {8, 8, 1} above. Host-side only; NMF_ERR_INVALID_ARG outside
- * these ranges. */
+ * for 65 <= k <= 112, {8, 8, 1} otherwise. Host-side only;
+ * NMF_ERR_INVALID_ARG outside these ranges. */
 nmf_status nmf_nls_bpp_set_shape(int32_t k, int32_t warps, int32_t chunk, int32_t group);
 
 /* Reads the launch shape solves of this k use (host pointers, nullable). */

@@ -943,8 +943,8 @@ namespace {
 // Launch shape of the solve kernels per k (warps per CTA, right-hand sides per
 // grab of the work counter, whether the group-tile pass runs first):
 // {8, 8, group pass on} until bpp_tune has measured the batch or the caller
-// set one; the group pass runs on the tensor cores (2) where k allows, else
-// on the SIMT pipes (1). Shapes with group 0 or 1 compute the same results
+// set one; the group pass runs on the tensor cores (2) for 65 <= k <= 112,
+// else on the SIMT pipes (1). Shapes with group 0 or 1 compute the same results
 // (a right-hand side's arithmetic does not depend on where it runs); group 2
 // solves the all-passive group with tensor-core products, to FP32 accuracy
 // but not the same bits.
@@ -958,8 +958,9 @@ BppShape shape_for(int k)
 {
     std::lock_guard<std::mutex> lock(g_shape_mu);
     BppShape sh = g_shape[k];
-    if (sh.group < 0)
-        sh.group = group_tc_supported(k) ? 2 : 1;
+    if (sh.group < 0)   // measured: the tensor-core pass wins from k = 65 (k = 100: 2.5x), the
+                        // SIMT pass at k = 50 (dense ANLS, 127.1 against 126.4 iter/s)
+        sh.group = k >= 65 && group_tc_supported(k) ? 2 : 1;
     return sh;
 }
 

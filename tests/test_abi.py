@@ -67,10 +67,12 @@ def test_launch_shape_set_and_get(lib):
     lib.nmf_nls_bpp_get_shape.argtypes = [I] + [ctypes.POINTER(I)] * 3
     w, c, g = I(0), I(0), I(0)
     assert lib.nmf_nls_bpp_get_shape(50, ctypes.byref(w), ctypes.byref(c), ctypes.byref(g)) == 0
-    # The default: group pass on the tensor cores up to k = 112, SIMT above.
-    assert (w.value, c.value, g.value) == (8, 8, 2)
-    assert lib.nmf_nls_bpp_get_shape(120, ctypes.byref(w), ctypes.byref(c), ctypes.byref(g)) == 0
+    # The default: group pass on the SIMT pipes, on the tensor cores for
+    # 65 <= k <= 112.
     assert (w.value, c.value, g.value) == (8, 8, 1)
+    for kk, gg in ((64, 1), (65, 2), (100, 2), (112, 2), (113, 1), (128, 1)):
+        assert lib.nmf_nls_bpp_get_shape(kk, ctypes.byref(w), ctypes.byref(c), ctypes.byref(g)) == 0
+        assert (w.value, c.value, g.value) == (8, 8, gg), kk
     assert lib.nmf_nls_bpp_set_shape(50, 16, 4, 0) == 0
     lib.nmf_nls_bpp_get_shape(50, ctypes.byref(w), ctypes.byref(c), ctypes.byref(g))
     assert (w.value, c.value, g.value) == (16, 4, 0)
@@ -81,6 +83,7 @@ def test_launch_shape_set_and_get(lib):
         assert lib.nmf_nls_bpp_set_shape(*bad) == 1, bad
     assert lib.nmf_nls_bpp_get_shape(0, None, None, None) == 1
     assert lib.nmf_nls_bpp_set_shape(50, 8, 8, 2) == 0
+    assert lib.nmf_nls_bpp_set_shape(50, 8, 8, 1) == 0
 
 
 class NlsDesc(ctypes.Structure):
