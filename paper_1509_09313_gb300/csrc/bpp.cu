@@ -174,19 +174,26 @@ __global__ void __launch_bounds__(PREP_THREADS)
         dsq[a] = sqrt(gdiag[a]);
     }
     __syncthreads();
-    // Right-looking Cholesky on the lower triangle.
-    for (int j = 0; j < u; ++j) {
-        if (tid == 0) {
-            const double d = L[j * u + j];
-            if (!(d > PIVOT_TOL64 * gdiag[j])) {
-                s_ok = 0;
-            } else {
-                const double l = sqrt(d);
-                L[j * u + j] = l;
-                rdiag[j] = 1.0 / l;
-            }
+    // Right-looking Cholesky on the lower triangle. Pivot j + 1 is final once
+    // its diagonal entry has taken pivot j's update, which thread 0 makes
+    // itself (row j + 1 of the trailing triangle is its first row): it forms
+    // that pivot's root in the same phase, so each pivot takes two barriers.
+    auto pivot = [&](int j) {
+        const double d = L[j * u + j];
+        if (!(d > PIVOT_TOL64 * gdiag[j])) {
+            s_ok = 0;
+        } else {
+            // One reciprocal square root instead of a root and a division on
+            // the pivots' serial path (GB300's FP64 pipe is narrow).
+            const double r = rsqrt(d);
+            L[j * u + j] = d * r;
+            rdiag[j] = r;
         }
-        __syncthreads();
+    };
+    if (tid == 0 && u > 0)
+        pivot(0);
+    __syncthreads();
+    for (int j = 0; j < u; ++j) {
         if (!s_ok)
             break;
         const double rj = rdiag[j];
@@ -199,6 +206,8 @@ __global__ void __launch_bounds__(PREP_THREADS)
             for (int b = j + 1 + (tid & 31); b <= a; b += 32)
                 L[a * u + b] = fma(-laj, L[b * u + j], L[a * u + b]);
         }
+        if (tid == 0 && j + 1 < u)
+            pivot(j + 1);
         __syncthreads();
     }
     if (!s_ok) {

@@ -88,41 +88,50 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[1
         : "r"(taddr));
 }
 
-__device__ __forceinline__ uint32_t bf2(float a, float b)
-{
-    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<const uint32_t *>(&h);
-}
-
 // v = hi + mid + lo to 2^-24 |v| (each step's remainder is exact in FP32).
 __device__ __forceinline__ void split8_3(const float (&v)[8], uint4 &hi, uint4 &mid, uint4 &lo)
 {
-    float h[8], m[8], l[8];
+    uint32_t hw[4], mw[4], lw[4];
+    const float2 neg1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        h[i] = __bfloat162float(__float2bfloat16_rn(v[i]));
-        const float r1 = fmaf(h[i], -1.0f, v[i]);
-        m[i] = __bfloat162float(__float2bfloat16_rn(r1));
-        l[i] = fmaf(m[i], -1.0f, r1);
+    for (int i = 0; i < 4; ++i) {
+        const float2 v2 = make_float2(v[2 * i], v[2 * i + 1]);
+        const __nv_bfloat162 hb = __floats2bfloat162_rn(v2.x, v2.y);
+        const float2 r1 = __ffma2_rn(__bfloat1622float2(hb), neg1, v2);   // exact
+        const __nv_bfloat162 mb = __floats2bfloat162_rn(r1.x, r1.y);
+        const float2 r2 = __ffma2_rn(__bfloat1622float2(mb), neg1, r1);   // exact
+        const __nv_bfloat162 lb = __floats2bfloat162_rn(r2.x, r2.y);
+        hw[i] = *reinterpret_cast<const uint32_t *>(&hb);
+        mw[i] = *reinterpret_cast<const uint32_t *>(&mb);
+        lw[i] = *reinterpret_cast<const uint32_t *>(&lb);
     }
-    hi = make_uint4(bf2(h[0], h[1]), bf2(h[2], h[3]), bf2(h[4], h[5]), bf2(h[6], h[7]));
-    mid = make_uint4(bf2(m[0], m[1]), bf2(m[2], m[3]), bf2(m[4], m[5]), bf2(m[6], m[7]));
-    lo = make_uint4(bf2(l[0], l[1]), bf2(l[2], l[3]), bf2(l[4], l[5]), bf2(l[6], l[7]));
+    hi = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    mid = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+    lo = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
 
 // v = hi + lo within 2^-17 |v|; s = hi + lo (exact in FP32).
 __device__ __forceinline__ void split8_sum(const float (&v)[8], uint4 &hi, uint4 &lo,
                                            float (&s)[8])
 {
-    float h[8], l[8];
+    uint32_t hw[4], lw[4];
+    const float2 neg1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        h[i] = __bfloat162float(__float2bfloat16_rn(v[i]));
-        l[i] = __bfloat162float(__float2bfloat16_rn(fmaf(h[i], -1.0f, v[i])));
-        s[i] = h[i] + l[i];
+    for (int i = 0; i < 4; ++i) {
+        const float2 v2 = make_float2(v[2 * i], v[2 * i + 1]);
+        const __nv_bfloat162 hb = __floats2bfloat162_rn(v2.x, v2.y);
+        const float2 hf = __bfloat1622float2(hb);
+        const float2 d = __ffma2_rn(hf, neg1, v2);   // v - hi, exact
+        const __nv_bfloat162 lb = __floats2bfloat162_rn(d.x, d.y);
+        const float2 lf = __bfloat1622float2(lb);
+        const float2 sm = __fadd2_rn(hf, lf);
+        s[2 * i] = sm.x;
+        s[2 * i + 1] = sm.y;
+        hw[i] = *reinterpret_cast<const uint32_t *>(&hb);
+        lw[i] = *reinterpret_cast<const uint32_t *>(&lb);
     }
-    hi = make_uint4(bf2(h[0], h[1]), bf2(h[2], h[3]), bf2(h[4], h[5]), bf2(h[6], h[7]));
-    lo = make_uint4(bf2(l[0], l[1]), bf2(l[2], l[3]), bf2(l[4], l[5]), bf2(l[6], l[7]));
+    hi = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    lo = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
 
 template <int NP>
@@ -263,9 +272,18 @@ __global__ void __launch_bounds__(GC_THREADS, 1) bpp_group_tc_kernel(const Solve
             *reinterpret_cast<uint4 *>(arow_hi + off) = h;
             *reinterpret_cast<uint4 *>(arow_lo + off) = l;
         };
-        auto usable = [&](int c) {
-            return c < k && (((c < 64 ? umask[0] : umask[1]) >> (c & 63)) & 1ull);
-        };
+        // This thread's usable columns, bit 16 m + i for column 16 (part + 4 m)
+        // + i (formed once: the per-column tests below are one bit test).
+        uint32_t mymask = 0;
+#pragma unroll
+        for (int m = 0; m < MYCH; ++m)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int c = 16 * (part + GC_PARTS * m) + i;
+                if (c < k && (((c < 64 ? umask[0] : umask[1]) >> (c & 63)) & 1ull))
+                    mymask |= 1u << (16 * m + i);
+            }
+        auto use_mi = [&](int m, int i) { return (mymask >> (16 * m + i)) & 1u; };
         // The parts' partial results of one decision: AND of the flags, max of
         // the values (every part gets the same combined result).
         auto combine = [&](int okp, float vp, int &ok, float &v) {
@@ -351,7 +369,7 @@ __global__ void __launch_bounds__(GC_THREADS, 1) bpp_group_tc_kernel(const Solve
 #pragma unroll
                             for (int i = 0; i < 16; ++i) {
                                 const int c = 16 * (part + GC_PARTS * m) + i;
-                                if (usable(c) && !(-g[m][i] < -ytol * dsq[c]))
+                                if (use_mi(m, i) && !(-g[m][i] < -ytol * dsq[c]))
                                     inp = 0;
                             }
                     } else {
@@ -409,7 +427,8 @@ __global__ void __launch_bounds__(GC_THREADS, 1) bpp_group_tc_kernel(const Solve
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
                             const int c = 16 * c16 + 8 * h8 + i;
-                            v[i] = usable(c) ? __uint_as_float(raw[8 * h8 + i]) + 0.0f : 0.0f;
+                            v[i] = use_mi(m, 8 * h8 + i) ? __uint_as_float(raw[8 * h8 + i]) + 0.0f
+                                                         : 0.0f;
                         }
                         uint4 h, l;
                         split8_sum(v, h, l, sm);
@@ -443,7 +462,7 @@ __global__ void __launch_bounds__(GC_THREADS, 1) bpp_group_tc_kernel(const Solve
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
                             const int c = 16 * c16 + 8 * h8 + i;
-                            v[i] = member && usable(c)
+                            v[i] = member && use_mi(m, 8 * h8 + i)
                                        ? g[m][8 * h8 + i] - __uint_as_float(raw[8 * h8 + i])
                                        : 0.0f;
                         }
@@ -483,11 +502,11 @@ __global__ void __launch_bounds__(GC_THREADS, 1) bpp_group_tc_kernel(const Solve
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         const int c = 16 * c16 + i;
-                        const float x = usable(c)
+                        const float x = use_mi(m, i)
                                             ? __uint_as_float(a0[i]) + (__uint_as_float(a2[i]) + 0.0f)
                                             : 0.0f;
                         x1[m][i] = x;
-                        if (usable(c))
+                        if (use_mi(m, i))
                             xmp = fmaxf(xmp, fabsf(x) * dsq[c]);
                     }
                 }
@@ -509,7 +528,7 @@ __global__ void __launch_bounds__(GC_THREADS, 1) bpp_group_tc_kernel(const Solve
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int c = 16 * (part + GC_PARTS * m) + i;
-                    if (usable(c) && x1[m][i] * dsq[c] < -xtol)
+                    if (use_mi(m, i) && x1[m][i] * dsq[c] < -xtol)
                         feasp = 0;
                     if (c < k && !isfinite(x1[m][i] > 0.0f ? x1[m][i] : 0.0f))
                         finp = 0;
