@@ -226,10 +226,15 @@ nmf_status mlp_propose(MlpNet *net, const float *F, int64_t n, uint64_t *passive
 // The input is the features F (rows x 3k FP32), or, with F null, formed from
 // G, B and Xp as mlp_features does.
 bool mlp_tc_supported(int k, int h);
-nmf_status launch_mlp_tc_forward(int k, int h, const float *W1, const float *b1, const float *W2,
-                                 const float *b2, const float *W3, const float *b3, const float *F,
-                                 const double *G, const float *B, const float *Xp, int64_t n,
-                                 float *logits, uint64_t *bits, cudaStream_t s);
+// The layers' BF16 weight operands (mlp_tc_weights_bytes of device memory),
+// from the BF16-valued working weights; the forward pass reads them.
+size_t mlp_tc_weights_bytes(int k, int h);
+nmf_status launch_mlp_tc_weights(int k, int h, const float *W1, const float *W2, const float *W3,
+                                 void *dst, cudaStream_t s);
+nmf_status launch_mlp_tc_forward(int k, int h, const void *wts, const float *b1, const float *b2,
+                                 const float *b3, const float *F, const double *G, const float *B,
+                                 const float *Xp, int64_t n, float *logits, uint64_t *bits,
+                                 cudaStream_t s);
 // Features of a batch straight into the first layer's BF16 hi / lo operand
 // (blocks of kpf >= k columns; rows of ldd >= 3 kpf columns, a multiple of 8).
 nmf_status launch_mlp_features_split(const double *G, const float *B, const float *Xp,

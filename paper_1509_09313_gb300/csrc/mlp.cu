@@ -45,6 +45,8 @@ constexpr float ADAM_B1 = 0.9f, ADAM_B2 = 0.999f, ADAM_EPS = 1e-8f;
 // (hi = bf16(v), lo = bf16(v - hi)): row j of hi and lo (ldd columns) holds
 // the three blocks of the features at columns [0, kpf), [kpf, 2 kpf),
 // [2 kpf, 3 kpf), zero-padded.
+constexpr int FEAT_R = 4;   // right-hand sides per pass of a warp
+
 template <int KW, bool SPLIT>
 __global__ void __launch_bounds__(256)
     mlp_features_kernel(const double *__restrict__ G, const float *__restrict__ B,
@@ -54,7 +56,7 @@ __global__ void __launch_bounds__(256)
 {
     extern __shared__ float sh[];
     float *Gs = sh;                              // k x k
-    float *stage_all = Gs + k * k;               // 8 warps x 32 KW
+    float *stage_all = Gs + k * k;               // 8 warps x FEAT_R x 32 KW
     __shared__ float s_mean;
     for (int e = threadIdx.x; e < k * k; e += blockDim.x)
         Gs[e] = (float)G[e];
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *stage = stage_all + warp * 32 * KW;
+    float *stage = stage_all + warp * FEAT_R * 32 * KW;
     float d[KW], logd[KW];
 #pragma unroll
     for (int s = 0; s < KW; ++s) {
@@ -79,78 +81,103 @@ __global__ void __launch_bounds__(256)
         d[s] = gii > 0.0f ? sqrtf(gii) : 1.0f;
         logd[s] = gii > 0.0f ? logf(gii / s_mean) : 0.0f;
     }
+    // FEAT_R right-hand sides per pass of a warp: the row of G read for index
+    // c serves all of them (one shared-memory load per FEAT_R FMAs instead of
+    // one per FMA); each right-hand side's sums run in the same order as one
+    // at a time.
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; j < nrhs; j += nw) {
-        float g[KW], x[KW], y[KW];
-        float smax = 0.0f;
+    for (int64_t j0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * FEAT_R; j0 < nrhs;
+         j0 += nw * FEAT_R) {
+        float g[FEAT_R][KW], x[FEAT_R][KW], y[FEAT_R][KW], sc[FEAT_R];
 #pragma unroll
-        for (int s = 0; s < KW; ++s) {
-            const int i = lane + 32 * s;
-            g[s] = i < k ? B[j * k + i] : 0.0f;
-            x[s] = (i < k && Xp) ? Xp[j * k + i] : 0.0f;
-            y[s] = -g[s];
-            smax = fmaxf(smax, fabsf(g[s]) / d[s]);
+        for (int r = 0; r < FEAT_R; ++r) {
+            const int64_t j = j0 + r;
+            const bool live = j < nrhs;
+            float smax = 0.0f;
+#pragma unroll
+            for (int s = 0; s < KW; ++s) {
+                const int i = lane + 32 * s;
+                g[r][s] = live && i < k ? B[j * k + i] : 0.0f;
+                x[r][s] = (live && i < k && Xp) ? Xp[j * k + i] : 0.0f;
+                y[r][s] = -g[r][s];
+                smax = fmaxf(smax, fabsf(g[r][s]) / d[s]);
+            }
+            for (int o = 16; o > 0; o >>= 1)
+                smax = fmaxf(smax, __shfl_xor_sync(FULL, smax, o));
+            sc[r] = smax > 0.0f ? 1.0f / smax : 1.0f;
+            // y = G x - g (G symmetric), x staged in shared memory and read by broadcast.
+#pragma unroll
+            for (int s = 0; s < KW; ++s)
+                stage[(r * KW + s) * 32 + lane] = x[r][s];
         }
-        for (int o = 16; o > 0; o >>= 1)
-            smax = fmaxf(smax, __shfl_xor_sync(FULL, smax, o));
-        const float sc = smax > 0.0f ? 1.0f / smax : 1.0f;
-        // y = G x - g (G symmetric), x staged in shared memory and read by broadcast.
-#pragma unroll
-        for (int s = 0; s < KW; ++s)
-            stage[32 * s + lane] = x[s];
         __syncwarp();
         for (int c = 0; c < k; ++c) {
-            const float xc = stage[c];
             const float *row = Gs + c * k;
+            float rv[KW];
 #pragma unroll
             for (int s = 0; s < KW; ++s) {
                 const int i = lane + 32 * s;
-                if (i < k)
-                    y[s] = fmaf(row[i], xc, y[s]);
+                rv[s] = i < k ? row[i] : 0.0f;
+            }
+            const int cs = c >> 5, cl = c & 31;
+#pragma unroll
+            for (int r = 0; r < FEAT_R; ++r) {
+                const float xc = stage[(r * KW + cs) * 32 + cl];
+#pragma unroll
+                for (int s = 0; s < KW; ++s)
+                    if (lane + 32 * s < k)
+                        y[r][s] = fmaf(rv[s], xc, y[r][s]);
             }
         }
         __syncwarp();
-        if (!SPLIT) {
-            float *f = Fout + j * (3 * k);
 #pragma unroll
-            for (int s = 0; s < KW; ++s) {
-                const int i = lane + 32 * s;
-                if (i < k) {
-                    f[i] = y[s] / d[s] * sc;
-                    f[k + i] = logd[s];
-                    f[2 * k + i] = x[s] * d[s] * sc;
-                }
-            }
-        } else {
-            __nv_bfloat16 *hr = hi + j * ldd, *lr = lo + j * ldd;
-            auto put = [&](int c, float v) {
-                const __nv_bfloat16 h = __float2bfloat16_rn(v);
-                hr[c] = h;
-                lr[c] = __float2bfloat16_rn(fmaf(__bfloat162float(h), -1.0f, v));
-            };
+        for (int r = 0; r < FEAT_R; ++r) {
+            const int64_t j = j0 + r;
+            if (j >= nrhs)
+                break;
+            if (!SPLIT) {
+                float *f = Fout + j * (3 * k);
 #pragma unroll
-            for (int s = 0; s < KW; ++s) {
-                const int i = lane + 32 * s;
-                if (i < k) {
-                    put(i, y[s] / d[s] * sc);
-                    put(kpf + i, logd[s]);
-                    put(2 * kpf + i, x[s] * d[s] * sc);
+                for (int s = 0; s < KW; ++s) {
+                    const int i = lane + 32 * s;
+                    if (i < k) {
+                        f[i] = y[r][s] / d[s] * sc[r];
+                        f[k + i] = logd[s];
+                        f[2 * k + i] = x[r][s] * d[s] * sc[r];
+                    }
                 }
-            }
-            // Zero columns: [k, kpf) of each block, and [3 kpf, ldd).
-            const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
-            for (int c = k + lane; c < kpf; c += 32)
-                for (int b = 0; b < 3; ++b) {
-                    hr[b * kpf + c] = z;
-                    lr[b * kpf + c] = z;
+            } else {
+                __nv_bfloat16 *hr = hi + j * ldd, *lr = lo + j * ldd;
+                auto put = [&](int c, float v) {
+                    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                    hr[c] = h;
+                    lr[c] = __float2bfloat16_rn(fmaf(__bfloat162float(h), -1.0f, v));
+                };
+#pragma unroll
+                for (int s = 0; s < KW; ++s) {
+                    const int i = lane + 32 * s;
+                    if (i < k) {
+                        put(i, y[r][s] / d[s] * sc[r]);
+                        put(kpf + i, logd[s]);
+                        put(2 * kpf + i, x[r][s] * d[s] * sc[r]);
+                    }
                 }
-            for (int c = 3 * kpf + lane; c < ldd; c += 32) {
-                hr[c] = z;
-                lr[c] = z;
+                // Zero columns: [k, kpf) of each block, and [3 kpf, ldd).
+                const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+                for (int c = k + lane; c < kpf; c += 32)
+                    for (int b = 0; b < 3; ++b) {
+                        hr[b * kpf + c] = z;
+                        lr[b * kpf + c] = z;
+                    }
+                for (int c = 3 * kpf + lane; c < ldd; c += 32) {
+                    hr[c] = z;
+                    lr[c] = z;
+                }
             }
         }
     }
 }
+
 
 // -------------------------------------------------------------------- GEMM
 // C[z][i][j] = sum_{l in split z} opA(i, l) opB(l, j) (+ bias[j]); then, with
@@ -402,6 +429,10 @@ struct MlpNet {
     int64_t off[6];          // W1, b1, W2, b2, W3, b3 in the flat arrays
     float *master = nullptr, *work = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
     int64_t t = 0;           // Adam steps taken
+    // The tensor-core layers' BF16 weights, converted from `work` after Adam
+    // step tcw_t (-1: not yet).
+    void *tcw = nullptr;
+    int64_t tcw_t = -1;
 };
 
 int64_t mlp_param_count(int k, int h)
@@ -417,8 +448,8 @@ nmf_status launch_features(const double *G, const float *B, const float *Xp, int
     if (nrhs == 0)
         return NMF_OK;
     const int kw = (k + 31) / 32;
-    const size_t smem = sizeof(float) * ((size_t)k * k + 8 * 32 * kw);
-    const unsigned blocks = (unsigned)std::min<int64_t>(cdiv(nrhs, 8), 4 * sm_count());
+    const size_t smem = sizeof(float) * ((size_t)k * k + 8 * FEAT_R * 32 * kw);
+    const unsigned blocks = (unsigned)std::min<int64_t>(cdiv(nrhs, 8 * FEAT_R), 4 * sm_count());
     auto go = [&](auto kern) -> nmf_status {
         if (smem > 48 * 1024)
             NMF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -572,8 +603,8 @@ nmf_status launch_mlp_features_split(const double *G, const float *B, const floa
     if (kpf < k || 3 * kpf > ldd || (ldd % 8))
         return NMF_ERR_INVALID_ARG;
     const int kw = (k + 31) / 32;
-    const size_t smem = sizeof(float) * ((size_t)k * k + 8 * 32 * kw);
-    const unsigned blocks = (unsigned)std::min<int64_t>(cdiv(nrhs, 8), 4 * sm_count());
+    const size_t smem = sizeof(float) * ((size_t)k * k + 8 * FEAT_R * 32 * kw);
+    const unsigned blocks = (unsigned)std::min<int64_t>(cdiv(nrhs, 8 * FEAT_R), 4 * sm_count());
     auto go = [&](auto kern) -> nmf_status {
         if (smem > 48 * 1024)
             NMF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -593,14 +624,28 @@ nmf_status launch_mlp_features_split(const double *G, const float *B, const floa
 
 namespace {
 
-// Inference on the tensor cores (mlp_tc.cu) when the widths allow it.
-nmf_status forward_tc(const MlpNet &net, const float *F, int64_t n, float *logits,
-                      uint64_t *bits, cudaStream_t s)
+// The tensor-core layers' BF16 weights, current with the working copy.
+nmf_status tc_weights(MlpNet &net, cudaStream_t s)
 {
+    if (!net.tcw)
+        NMF_CUDA(cudaMalloc(&net.tcw, mlp_tc_weights_bytes(net.k, net.h)));
+    if (net.tcw_t != net.t) {
+        const float *w = net.work;
+        NMF_TRY(launch_mlp_tc_weights(net.k, net.h, w + net.off[0], w + net.off[2],
+                                      w + net.off[4], net.tcw, s));
+        net.tcw_t = net.t;
+    }
+    return NMF_OK;
+}
+
+// Inference on the tensor cores (mlp_tc.cu) when the widths allow it.
+nmf_status forward_tc(MlpNet &net, const float *F, int64_t n, float *logits, uint64_t *bits,
+                      cudaStream_t s)
+{
+    NMF_TRY(tc_weights(net, s));
     const float *w = net.work;
-    return launch_mlp_tc_forward(net.k, net.h, w + net.off[0], w + net.off[1], w + net.off[2],
-                                 w + net.off[3], w + net.off[4], w + net.off[5], F, nullptr,
-                                 nullptr, nullptr, n, logits, bits, s);
+    return launch_mlp_tc_forward(net.k, net.h, net.tcw, w + net.off[1], w + net.off[3],
+                                 w + net.off[5], F, nullptr, nullptr, nullptr, n, logits, bits, s);
 }
 
 }  // namespace
@@ -628,9 +673,9 @@ nmf_status mlp_features_propose(MlpNet *net, const double *G, const float *B, co
     if (n == 0)
         return NMF_OK;
     if (mlp_tc_supported(net->k, net->h)) {
+        NMF_TRY(tc_weights(*net, s));
         const float *w = net->work;
-        return launch_mlp_tc_forward(net->k, net->h, w + net->off[0], w + net->off[1],
-                                     w + net->off[2], w + net->off[3], w + net->off[4],
+        return launch_mlp_tc_forward(net->k, net->h, net->tcw, w + net->off[1], w + net->off[3],
                                      w + net->off[5], nullptr, G, B, Xp, n, nullptr, passive, s);
     }
     NMF_TRY(launch_features(G, B, Xp, n, net->k, F, s));
@@ -743,6 +788,7 @@ void mlp_destroy(MlpNet *net)
     cudaFree(net->m);
     cudaFree(net->v);
     cudaFree(net->grad);
+    cudaFree(net->tcw);
     delete net;
 }
 

@@ -321,10 +321,65 @@ bool mlp_tc_supported(int k, int h)
     return k >= 1 && h >= 1 && pad(h, 32) <= ML_MAX_N && pad(k, 32) <= ML_MAX_N;
 }
 
-nmf_status launch_mlp_tc_forward(int k, int h, const float *W1, const float *b1, const float *W2,
-                                 const float *b2, const float *W3, const float *b3, const float *F,
-                                 const double *G, const float *B, const float *Xp, int64_t n,
-                                 float *logits, uint64_t *bits, cudaStream_t s)
+namespace {
+
+// The layers' B operands in one buffer: W1 (nph x kp1, its columns in the
+// features' three blocks), W2 (nph x kph), W3 (npk x kph), BF16, zero-padded.
+struct MlWeights {
+    int kpf, kp1, nph, kph, npk;
+    size_t w1, w2, w3, total;   // byte offsets
+};
+
+MlWeights ml_weights(int k, int h)
+{
+    MlWeights w;
+    w.kpf = pad(k, 16);
+    w.kp1 = pad(3 * w.kpf, ML_BK);
+    w.nph = pad(h, 32);
+    w.kph = pad(w.nph, ML_BK);
+    w.npk = pad(k, 32);
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    w.w1 = 0;
+    w.w2 = w.w1 + al(sizeof(__nv_bfloat16) * (size_t)w.nph * w.kp1);
+    w.w3 = w.w2 + al(sizeof(__nv_bfloat16) * (size_t)w.nph * w.kph);
+    w.total = w.w3 + al(sizeof(__nv_bfloat16) * (size_t)w.npk * w.kph);
+    return w;
+}
+
+nmf_status split_rows(const float *src, int64_t rows, int cols, int prow, int ldd, int bs, int bd,
+                      __nv_bfloat16 *hi, __nv_bfloat16 *lo, cudaStream_t s)
+{
+    if (prow > rows)   // zero rows past the matrix (padded output columns)
+        NMF_CUDA(cudaMemsetAsync(hi + rows * ldd, 0,
+                                 sizeof(__nv_bfloat16) * (size_t)(prow - rows) * ldd, s));
+    const int64_t work = rows * (ldd / 8);
+    const unsigned blocks = (unsigned)std::min<int64_t>(cdiv(work, 256), 8 * (int64_t)sm_count());
+    mlp_tc_split_kernel<<<blocks, 256, 0, s>>>(src, rows, cols, ldd, bs, bd, hi, lo);
+    NMF_LAUNCHED("mlp_tc_split_kernel");
+    return NMF_OK;
+}
+
+}  // namespace
+
+size_t mlp_tc_weights_bytes(int k, int h) { return ml_weights(k, h).total; }
+
+nmf_status launch_mlp_tc_weights(int k, int h, const float *W1, const float *W2, const float *W3,
+                                 void *dst, cudaStream_t s)
+{
+    if (!mlp_tc_supported(k, h))
+        return NMF_ERR_INVALID_ARG;
+    const MlWeights w = ml_weights(k, h);
+    unsigned char *d = static_cast<unsigned char *>(dst);
+    auto at = [&](size_t off) { return reinterpret_cast<__nv_bfloat16 *>(d + off); };
+    NMF_TRY(split_rows(W1, h, 3 * k, w.nph, w.kp1, k, w.kpf, at(w.w1), nullptr, s));
+    NMF_TRY(split_rows(W2, h, h, w.nph, w.kph, w.kph, w.kph, at(w.w2), nullptr, s));
+    return split_rows(W3, k, h, w.npk, w.kph, w.kph, w.kph, at(w.w3), nullptr, s);
+}
+
+nmf_status launch_mlp_tc_forward(int k, int h, const void *wts, const float *b1, const float *b2,
+                                 const float *b3, const float *F, const double *G, const float *B,
+                                 const float *Xp, int64_t n, float *logits, uint64_t *bits,
+                                 cudaStream_t s)
 {
     if (!mlp_tc_supported(k, h) || n < 0 || n > INT32_MAX)
         return NMF_ERR_INVALID_ARG;
@@ -340,10 +395,7 @@ nmf_status launch_mlp_tc_forward(int k, int h, const float *W1, const float *b1,
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     const size_t fbytes = al(sizeof(__nv_bfloat16) * (size_t)n * kp1);
     const size_t hbytes = al(sizeof(__nv_bfloat16) * (size_t)n * kph);
-    const size_t w1b = al(sizeof(__nv_bfloat16) * (size_t)nph * kp1);
-    const size_t w2b = al(sizeof(__nv_bfloat16) * (size_t)nph * kph);
-    const size_t w3b = al(sizeof(__nv_bfloat16) * (size_t)npk * kph);
-    const size_t total = 2 * fbytes + 4 * hbytes + w1b + w2b + w3b;
+    const size_t total = 2 * fbytes + 4 * hbytes;
     struct Mem {
         void *p = nullptr;
         cudaStream_t s;
@@ -362,25 +414,15 @@ nmf_status launch_mlp_tc_forward(int k, int h, const float *W1, const float *b1,
     };
     __nv_bfloat16 *fhi = take(fbytes), *flo = take(fbytes);
     __nv_bfloat16 *xhi = take(hbytes), *xlo = take(hbytes), *yhi = take(hbytes), *ylo = take(hbytes);
-    __nv_bfloat16 *w1 = take(w1b), *w2 = take(w2b), *w3 = take(w3b);
+    const MlWeights wl = ml_weights(k, h);
+    const unsigned char *wb = static_cast<const unsigned char *>(wts);
+    const __nv_bfloat16 *w1 = reinterpret_cast<const __nv_bfloat16 *>(wb + wl.w1);
+    const __nv_bfloat16 *w2 = reinterpret_cast<const __nv_bfloat16 *>(wb + wl.w2);
+    const __nv_bfloat16 *w3 = reinterpret_cast<const __nv_bfloat16 *>(wb + wl.w3);
 
-    // Weights (BF16 values) into zero-padded BF16 matrices; features into hi / lo.
-    auto split = [&](const float *src, int64_t rows, int cols, int prow, int ldd, int bs, int bd,
-                     __nv_bfloat16 *hi, __nv_bfloat16 *lo) -> nmf_status {
-        if (prow > rows)   // zero rows past the matrix (padded output columns)
-            NMF_CUDA(cudaMemsetAsync(hi + rows * ldd, 0,
-                                     sizeof(__nv_bfloat16) * (size_t)(prow - rows) * ldd, s));
-        const int64_t work = rows * (ldd / 8);
-        const unsigned blocks = (unsigned)std::min<int64_t>(cdiv(work, 256), 8 * (int64_t)sm_count());
-        mlp_tc_split_kernel<<<blocks, 256, 0, s>>>(src, rows, cols, ldd, bs, bd, hi, lo);
-        NMF_LAUNCHED("mlp_tc_split_kernel");
-        return NMF_OK;
-    };
-    NMF_TRY(split(W1, h, k1, nph, kp1, k, kpf, w1, nullptr));
-    NMF_TRY(split(W2, h, h, nph, kph, kph, kph, w2, nullptr));
-    NMF_TRY(split(W3, k, h, npk, kph, kph, kph, w3, nullptr));
+    // The features into hi / lo (the weights are converted already).
     if (F)
-        NMF_TRY(split(F, n, k1, (int)n, kp1, k, kpf, fhi, flo));
+        NMF_TRY(split_rows(F, n, k1, (int)n, kp1, k, kpf, fhi, flo, s));
     else
         NMF_TRY(launch_mlp_features_split(G, B, Xp, n, k, kpf, kp1, fhi, flo, s));
 
