@@ -15,8 +15,12 @@
 //    form, the active set in the complement form) loops over that list only:
 //    y = G_{:,F} x_F costs |F| row reads, not k;
 //  * u = M g is formed only when a complement solve first needs it;
-//  * the Cholesky keeps each row's reciprocal pivot in its lane: with
-//    q = rsqrt(d), L_jj = d q and L_ij = s_i q;
+//  * k <= 64 (systems of at most k / 2 <= 32 rows): an LDL^T factor whose
+//    trailing rows stay in registers, one row per lane, shifted one column per
+//    step so that a rolled loop keeps constant register indices; the
+//    multipliers go to shared memory for the two substitutions;
+//  * k > 64: a left-looking Cholesky that keeps each row's reciprocal pivot in
+//    its lane: with q = rsqrt(d), L_jj = d q and L_ij = s_i q;
 //  * no FP64 arithmetic: a system that meets the pivot floor defers its
 //    right-hand side to the FP64 kernel's second pass, which re-solves it from
 //    its starting partition.
@@ -232,21 +236,108 @@ __device__ __forceinline__ void subst32(int p, const float *__restrict__ Lw, int
     }
 }
 
+// Systems of at most PM rows (k <= 64; PM >= k / 2 >= p): LDL^T of
+// S_ab = Src(idx[a], idx[b]) with lane a keeping the live part of row a in
+// registers. At step j, s[0 .. p - j) holds columns j .. p - 1 of row a of the
+// trailing (Schur complement) matrix; the update writes column b + 1 into
+// s[b], so the row shifts one place per step and every register index stays a
+// constant inside a loop that is not unrolled over j (fully unrolled steps
+// overflowed the instruction cache). Row j reaches the other lanes by
+// shuffles, four columns at a time up to the live width. The multipliers
+// L_aj = S_aj / S_jj go to Lw[a * LS + j] (LS odd: conflict-free rows and
+// columns); lane a keeps rp = 1 / D_aa. col[b] is the offset of column
+// idx[b] within a row of Src (the list padded to a multiple of four with
+// offset 0). Returns false (uniformly) when a pivot is at most PIVOT_TOL of
+// its diagonal.
+template <int KW, int PM>
+__device__ __forceinline__ bool ldl_regs(const float *__restrict__ Src, const int *__restrict__ idx,
+                                         const int *__restrict__ col, int p,
+                                         float *__restrict__ Lw, int LS, float &rp, int lane)
+{
+    constexpr int RS = 32 * KW;
+    const int c = lane < p ? idx[lane] : 0;
+    const float *row = Src + c * RS;
+    const float dtol = PIVOT_TOL * row[(c & 31) * KW + (c >> 5)];
+    float s[PM];
+#pragma unroll
+    for (int b0 = 0; b0 < PM; b0 += 4) {
+        if (b0 < p) {
+            const int4 o = *reinterpret_cast<const int4 *>(col + b0);
+            s[b0] = row[o.x];
+            s[b0 + 1] = row[o.y];
+            s[b0 + 2] = row[o.z];
+            s[b0 + 3] = row[o.w];
+        } else {
+#pragma unroll
+            for (int b = b0; b < b0 + 4; ++b)
+                s[b] = 0.0f;
+        }
+    }
+    bool ok = true;
+    rp = 0.0f;
+    for (int j = 0; j < p; ++j) {
+        const float d = __shfl_sync(FULL, s[0], j);
+        const float q = rsqrtf(d);
+        const float r = q * q;
+        if (lane == j) {
+            ok = d > dtol;
+            rp = r;
+        }
+        const bool below = lane > j && lane < p;
+        const float m = below ? s[0] * r : 0.0f;
+        if (below)
+            Lw[lane * LS + j] = m;
+        const int w = p - j;   // live columns: s[0 .. w)
+#pragma unroll
+        for (int b0 = 0; b0 < PM; b0 += 4) {
+            if (b0 >= w)
+                break;
+#pragma unroll
+            for (int b = (b0 > 1 ? b0 : 1); b < b0 + 4; ++b)
+                s[b - 1] = fmaf(-m, __shfl_sync(FULL, s[b], j), s[b]);
+        }
+    }
+    return __all_sync(FULL, ok);
+}
+
+// Solve S z = r with the factor of ldl_regs (row a of r and z in lane a):
+// L y = r forward, then L^T z = D^{-1} y backward.
+__device__ __forceinline__ float ldl_solve(const float *__restrict__ Lw, int LS, float rp, int p,
+                                           float r, int lane)
+{
+    for (int j = 0; j + 1 < p; ++j) {
+        const float t = __shfl_sync(FULL, r, j);
+        if (lane > j && lane < p)
+            r = fmaf(-Lw[lane * LS + j], t, r);
+    }
+    float v = r * rp, z = 0.0f;
+    for (int j = p - 1; j >= 0; --j) {
+        const float zj = __shfl_sync(FULL, v, j);
+        if (lane < j)
+            v = fmaf(-Lw[j * LS + lane], zj, v);
+        if (lane == j)
+            z = zj;
+    }
+    return z;
+}
+
 // Shared memory: G and M (k rounded up to 4 rows of 32 KW floats each), then
-// per warp an index list, its values, a staging vector (32 KW each) and the
-// pmax x LS factor.
+// per warp an index list, its values, a staging vector (32 KW each), the
+// list's column offsets (k <= 64) and the pmax x LS factor.
 __host__ __device__ inline size_t mats_bytes32(int k, int KW)
 {
     return 2 * sizeof(float) * (size_t)((k + 3) & ~3) * 32 * KW;
 }
 __host__ __device__ inline size_t warp_bytes32(int KW, int pmax, int LS)
 {
-    return (3 * sizeof(float) * 32 * KW + sizeof(float) * (size_t)pmax * LS + 15) & ~size_t(15);
+    const size_t cols = KW <= 2 ? sizeof(int) * 32 * KW : 0;
+    return (3 * sizeof(float) * 32 * KW + cols + sizeof(float) * (size_t)pmax * LS + 15) &
+           ~size_t(15);
 }
 
 // 64 registers for KW <= 2 (two 16-warp CTAs per SM); the KW = 4 form needs
 // more and runs one CTA per SM.
-template <int KW>
+template <int KW, int PM>
 __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
     bpp_solve32_kernel(const SolveParams P, int pmax, int LS)
 {
@@ -276,7 +367,8 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
     int *widx = reinterpret_cast<int *>(wp);
     float *zbuf = reinterpret_cast<float *>(widx + RS);
     float *stage = zbuf + RS;
-    float *Lw = stage + RS;
+    int *wcol = reinterpret_cast<int *>(stage + RS);   // KW <= 2: column offsets of the list
+    float *Lw = stage + RS + (KW <= 2 ? RS : 0);
     __syncthreads();
 
     bool usable[KW];
@@ -291,7 +383,11 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
         dsq[s] = usable[s] ? sqrtf(Gs[i * RS + lane * KW + s]) : 1.0f;
     }
 
-    unsigned long long st_rounds = 0, st_max = 0, st_def = 0, st_nc = 0, st_nf = 0, st_rhs = 0;
+    // Per-warp statistics in shared memory (lane 0 updates them), so that
+    // they hold no registers through the solves.
+    __shared__ unsigned long long wst[S32_MAX_WARPS][6];   // rhs, rounds, max, fp64, nc, nf
+    if (lane < 6)
+        wst[warp][lane] = 0;
 
     for (;;) {
         unsigned long long j0 = 0;
@@ -419,6 +515,8 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
                         if (inS[s]) {
                             widx[rank[s]] = lane + 32 * s;
                             zbuf[rank[s]] = comp ? -u[s] : g[s];
+                            if constexpr (KW <= 2)
+                                wcol[rank[s]] = lane * KW + s;
                         }
                         pos += __popc(mk);
                     }
@@ -426,11 +524,18 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
                     if (lane < p4 - p) {
                         widx[p + lane] = 0;
                         zbuf[p + lane] = 0.0f;
+                        if constexpr (KW <= 2)
+                            wcol[p + lane] = 0;
                     }
                     __syncwarp();
-                    float inv[PT];
-                    if (p > 0 && !chol32<KW, PT>(comp ? Ms : Gs, widx, p, Lw, LS, inv, lane))
-                        return DEFERRED;
+                    float inv[PT], rp = 0.0f;
+                    if constexpr (KW <= 2) {
+                        if (p > 0 && !ldl_regs<KW, PM>(comp ? Ms : Gs, widx, wcol, p, Lw, LS, rp, lane))
+                            return DEFERRED;
+                    } else {
+                        if (p > 0 && !chol32<KW, PT>(comp ? Ms : Gs, widx, p, Lw, LS, inv, lane))
+                            return DEFERRED;
+                    }
                     // Pass 0 solves the system (zbuf = g_F, or -u_A in the
                     // complement form); pass 1 solves it again for the
                     // residual g_F - (G x)_F through the same factor (the
@@ -447,7 +552,10 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
                                 const int a = lane + 32 * t;
                                 r[t] = a < p ? zbuf[a] : 0.0f;
                             }
-                            subst32<PT>(p, Lw, LS, inv, r, lane);
+                            if constexpr (KW <= 2)
+                                r[0] = ldl_solve(Lw, LS, rp, p, r[0], lane);
+                            else
+                                subst32<PT>(p, Lw, LS, inv, r, lane);
                             __syncwarp();
 #pragma unroll
                             for (int t = 0; t < PT; ++t)
@@ -605,7 +713,7 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
                     const unsigned long long slot = atomicAdd(&P.counters[CNT_DEFERRED], 1ull);
                     if (slot < (unsigned long long)DEFER_CAP)
                         P.defer[slot] = j;
-                    st_def += 1;
+                    wst[warp][3] += 1;
                 }
                 continue;
             }
@@ -634,25 +742,28 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
                     P.rounds_out[j] = rounds;
                 if (P.status_out)
                     P.status_out[j] = (int8_t)status;
-                st_rhs += 1;
-                st_rounds += rounds;
-                st_max = st_max > (unsigned long long)rounds ? st_max : (unsigned long long)rounds;
-                st_nc += status == NMF_ERR_NOT_CONVERGED;
-                st_nf += status == NMF_ERR_NONFINITE;
+                wst[warp][0] += 1;
+                wst[warp][1] += rounds;
+                if (wst[warp][2] < (unsigned long long)rounds)
+                    wst[warp][2] = rounds;
+                wst[warp][4] += status == NMF_ERR_NOT_CONVERGED;
+                wst[warp][5] += status == NMF_ERR_NONFINITE;
             }
         }
     }
-    if (lane == 0 && (st_rhs || st_def)) {
-        atomicAdd(&P.stats->rhs, st_rhs);
-        atomicAdd(&P.stats->rounds, st_rounds);
-        atomicMax(&P.stats->max_rounds, st_max);
-        if (st_def) atomicAdd(&P.stats->fp64_solves, st_def);
-        if (st_nc) atomicAdd(&P.stats->not_converged, st_nc);
-        if (st_nf) atomicAdd(&P.stats->nonfinite, st_nf);
+    if (lane == 0 && (wst[warp][0] || wst[warp][3])) {
+        atomicAdd(&P.stats->rhs, wst[warp][0]);
+        atomicAdd(&P.stats->rounds, wst[warp][1]);
+        atomicMax(&P.stats->max_rounds, wst[warp][2]);
+        if (wst[warp][3]) atomicAdd(&P.stats->fp64_solves, wst[warp][3]);
+        if (wst[warp][4]) atomicAdd(&P.stats->not_converged, wst[warp][4]);
+        if (wst[warp][5]) atomicAdd(&P.stats->nonfinite, wst[warp][5]);
     }
 }
 
-template <int KW>
+// PM: the largest system held in registers (k <= 64), a multiple of four at
+// least k / 2 (p <= k / 2).
+template <int KW, int PM>
 nmf_status launch32(const SolveParams &P, cudaStream_t s)
 {
     const int k = P.k;
@@ -660,7 +771,9 @@ nmf_status launch32(const SolveParams &P, cudaStream_t s)
     int q = (pmax + 1) / 2;
     if (!(q & 1))
         ++q;
-    const int LS = 2 * q;   // 2 * odd: conflict-free float2 row reads and column accesses
+    // k > 64: 2 * odd, conflict-free float2 row reads and column accesses;
+    // k <= 64: odd, conflict-free rows and columns of single floats.
+    const int LS = KW <= 2 ? (pmax | 1) : 2 * q;
     int nwarps = P.warps < S32_MAX_WARPS ? P.warps : S32_MAX_WARPS;
     const size_t mats = mats_bytes32(k, KW);
     auto bytes = [&](int nw) { return mats + (size_t)nw * warp_bytes32(KW, pmax, LS); };
@@ -670,9 +783,9 @@ nmf_status launch32(const SolveParams &P, cudaStream_t s)
     if (smem > SMEM_LIMIT32)
         return NMF_ERR_INVALID_ARG;
     static SmemOptIn opt_in;
-    NMF_TRY(ensure_smem(bpp_solve32_kernel<KW>, opt_in, smem));
+    NMF_TRY(ensure_smem(bpp_solve32_kernel<KW, PM>, opt_in, smem));
     int per_sm = 0;
-    NMF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bpp_solve32_kernel<KW>,
+    NMF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bpp_solve32_kernel<KW, PM>,
                                                            nwarps * 32, smem));
     if (per_sm < 1)
         return NMF_ERR_INVALID_ARG;
@@ -680,7 +793,7 @@ nmf_status launch32(const SolveParams &P, cudaStream_t s)
     const int64_t need = cdiv(cdiv(P.nrhs, (int64_t)P.chunk), nwarps);
     if (need < blocks)
         blocks = need < 1 ? 1 : need;
-    bpp_solve32_kernel<KW><<<(unsigned)blocks, nwarps * 32, smem, s>>>(P, pmax, LS);
+    bpp_solve32_kernel<KW, PM><<<(unsigned)blocks, nwarps * 32, smem, s>>>(P, pmax, LS);
     NMF_LAUNCHED("bpp_solve32_kernel");
     return NMF_OK;
 }
@@ -690,10 +803,14 @@ nmf_status launch32(const SolveParams &P, cudaStream_t s)
 nmf_status launch_solve32(const SolveParams &P, cudaStream_t s)
 {
     if (P.k <= 32)
-        return launch32<1>(P, s);
+        return launch32<1, 16>(P, s);
+    if (P.k <= 48)
+        return launch32<2, 24>(P, s);
+    if (P.k <= 56)
+        return launch32<2, 28>(P, s);
     if (P.k <= 64)
-        return launch32<2>(P, s);
-    return launch32<4>(P, s);
+        return launch32<2, 32>(P, s);
+    return launch32<4, 4>(P, s);
 }
 
 }  // namespace bpp
