@@ -279,6 +279,7 @@ struct nmf_handle {
     // Host state.
     bool passive_valid = false;
     bool fused_obj = false;        // objective computed inside the next A H^T pass
+    bool gh_current = false;       // GH is the Gram of the current Ht (formed by an objective)
     bool obj_pending = false;      // f of the last iteration not yet computed
     int64_t f_count = 0;
     int64_t iterations = 0;
@@ -417,6 +418,7 @@ nmf_status objective_into(nmf_handle *h, double *f_dev, bool after_h = false)
             NMF_TRY(launch_gram(h->W, c.m, c.k, h->GW, h->gram_part, h->stream));
         }
         NMF_TRY(launch_gram(h->Ht, c.n, c.k, h->GH, h->gram_part, h->stream));
+        h->gh_current = true;   // the next W half-step reuses it
         return launch_objective_csr(h->Ht, h->Y, c.n, c.k, h->a_sq, h->GW, h->GH, h->obj_part,
                                     f_dev, h->stream);
     }
@@ -470,11 +472,12 @@ nmf_status one_iteration(nmf_handle *h)
     // fork); the main stream runs the product meanwhile and joins before the
     // solves. The BPP workspace is free again at each fork: the previous
     // half-step's solves are on the main stream before it.
-    auto fork_prepare = [&](const float *F, int64_t rows, double *G) -> nmf_status {
+    auto fork_prepare = [&](const float *F, int64_t rows, double *G, bool have_gram) -> nmf_status {
         NMF_CUDA(cudaEventRecord(h->ev_fork, h->stream));
         NMF_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
         PhaseTimer t(h, 0, h->side);
-        NMF_TRY(launch_gram(F, rows, c.k, G, h->gram_part, h->side));
+        if (!have_gram)
+            NMF_TRY(launch_gram(F, rows, c.k, G, h->gram_part, h->side));
         if (c.solver == NMF_SOLVER_BPP)
             NMF_TRY(launch_bpp_prep(c.k, G, h->bpp_work, h->stats_dev, h->side));
         NMF_CUDA(cudaEventRecord(h->ev_join, h->side));
@@ -488,7 +491,7 @@ nmf_status one_iteration(nmf_handle *h)
     const CsrGather gather_w{h->A.rowptr, h->A.colidx, h->A.vals, h->Ht};
     const CsrGather gather_h{h->t_rowptr, h->t_colidx, h->t_vals, h->W};
     // W <- argmin_{W >= 0} ||A - W H||: Gram H H^T, right-hand sides A H^T.
-    NMF_TRY(fork_prepare(h->Ht, c.n, h->GH));
+    NMF_TRY(fork_prepare(h->Ht, c.n, h->GH, h->gh_current));
     if (!fuse) {
         PhaseTimer t(h, 1);
         if (h->obj_pending) {
@@ -508,13 +511,14 @@ nmf_status one_iteration(nmf_handle *h)
                                 h->pgw2 + (h->iterations % F_HIST_CAP), h->stream));
     NMF_TRY(solve_half(h, c.m, h->GH, h->V, h->W, h->pW, warm, fuse ? &gather_w : nullptr));
     // H <- argmin_{H >= 0} ||A - W H||: Gram W^T W, right-hand sides (W^T A)^T.
-    NMF_TRY(fork_prepare(h->W, c.m, h->GW));
+    NMF_TRY(fork_prepare(h->W, c.m, h->GW, false));
     if (!fuse) {
         PhaseTimer t(h, 1);
         NMF_TRY(mm(h, 1, h->W, h->Y));
     }
     NMF_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     NMF_TRY(solve_half(h, c.n, h->GW, h->Y, h->Ht, h->pH, warm, fuse ? &gather_h : nullptr));
+    h->gh_current = false;
     // ... and the new iterate's part in H (W^T W and A^T W of the new W).
     if (h->pg_on)
         NMF_TRY(launch_pgrad_sq(h->GW, c.k, h->Y, h->Ht, c.n, h->pg_part,
@@ -891,6 +895,8 @@ extern "C" nmf_status nmf_set_factors(nmf_handle *h, const float *W, const float
     if (Ht)
         NMF_CUDA(cudaMemcpyAsync(h->Ht, Ht, sizeof(float) * (size_t)h->cfg.n * k,
                                  cudaMemcpyDeviceToDevice, h->stream));
+    if (Ht)
+        h->gh_current = false;
     h->passive_valid = false;
     h->pg_on = false;   // the recorded measures belong to the replaced iterates
     return NMF_OK;

@@ -301,17 +301,51 @@ __device__ __forceinline__ bool ldl_regs(const float *__restrict__ Src, const in
 }
 
 // Solve S z = r with the factor of ldl_regs (row a of r and z in lane a):
-// L y = r forward, then L^T z = D^{-1} y backward.
+// L y = r forward, then L^T z = D^{-1} y backward. Four steps at a time with
+// their multipliers loaded first, so only the shuffle and the FMA of each step
+// are on the dependency chain (a lane's loads may run past its row or the
+// factor: the per-warp area ends with 32 floats of slack; lanes >= p carry
+// values that are never read).
 __device__ __forceinline__ float ldl_solve(const float *__restrict__ Lw, int LS, float rp, int p,
                                            float r, int lane)
 {
-    for (int j = 0; j + 1 < p; ++j) {
+    const float *lrow = Lw + (lane < p ? lane : 0) * LS;
+    int j = 0;
+    for (; j + 4 < p; j += 4) {
+        const float l0 = lrow[j], l1 = lrow[j + 1], l2 = lrow[j + 2], l3 = lrow[j + 3];
+        float t = __shfl_sync(FULL, r, j);
+        if (lane > j) r = fmaf(-l0, t, r);
+        t = __shfl_sync(FULL, r, j + 1);
+        if (lane > j + 1) r = fmaf(-l1, t, r);
+        t = __shfl_sync(FULL, r, j + 2);
+        if (lane > j + 2) r = fmaf(-l2, t, r);
+        t = __shfl_sync(FULL, r, j + 3);
+        if (lane > j + 3) r = fmaf(-l3, t, r);
+    }
+    for (; j + 1 < p; ++j) {
         const float t = __shfl_sync(FULL, r, j);
-        if (lane > j && lane < p)
-            r = fmaf(-Lw[lane * LS + j], t, r);
+        if (lane > j)
+            r = fmaf(-lrow[j], t, r);
     }
     float v = r * rp, z = 0.0f;
-    for (int j = p - 1; j >= 0; --j) {
+    j = p - 1;
+    for (; j >= 3; j -= 4) {
+        const float l0 = Lw[j * LS + lane], l1 = Lw[(j - 1) * LS + lane];
+        const float l2 = Lw[(j - 2) * LS + lane], l3 = Lw[(j - 3) * LS + lane];
+        float zj = __shfl_sync(FULL, v, j);
+        if (lane < j) v = fmaf(-l0, zj, v);
+        if (lane == j) z = zj;
+        zj = __shfl_sync(FULL, v, j - 1);
+        if (lane < j - 1) v = fmaf(-l1, zj, v);
+        if (lane == j - 1) z = zj;
+        zj = __shfl_sync(FULL, v, j - 2);
+        if (lane < j - 2) v = fmaf(-l2, zj, v);
+        if (lane == j - 2) z = zj;
+        zj = __shfl_sync(FULL, v, j - 3);
+        if (lane < j - 3) v = fmaf(-l3, zj, v);
+        if (lane == j - 3) z = zj;
+    }
+    for (; j >= 0; --j) {
         const float zj = __shfl_sync(FULL, v, j);
         if (lane < j)
             v = fmaf(-Lw[j * LS + lane], zj, v);
@@ -330,7 +364,9 @@ __host__ __device__ inline size_t mats_bytes32(int k, int KW)
 }
 __host__ __device__ inline size_t warp_bytes32(int KW, int pmax, int LS)
 {
-    const size_t cols = KW <= 2 ? sizeof(int) * 32 * KW : 0;
+    // k <= 64: column offsets, and 32 floats of slack after the factor (read
+    // past its end by the unrolled substitutions).
+    const size_t cols = KW <= 2 ? sizeof(int) * 32 * KW + sizeof(float) * 32 : 0;
     return (3 * sizeof(float) * 32 * KW + cols + sizeof(float) * (size_t)pmax * LS + 15) &
            ~size_t(15);
 }
@@ -397,6 +433,9 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
         if (j0 >= (unsigned long long)P.nrhs)
             break;
         const int64_t jend = min((int64_t)j0 + P.chunk, P.nrhs);
+        // Fused gathers: row pointers of up to 31 consecutive rows, one per
+        // lane (rowptr[rb + lane]), read once per batch.
+        int64_t rb = -1, rpv = 0;
         for (int64_t j = (int64_t)j0; j < jend; ++j) {
             float g[KW], u[KW], x[KW], y[KW];
             bool inF[KW];
@@ -408,13 +447,41 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
 #pragma unroll
                 for (int s = 0; s < KW; ++s)
                     g[s] = 0.0f;
-                const int64_t beg = P.gat.rowptr[j], end = P.gat.rowptr[j + 1];
+                if (rb < 0 || j - rb >= 31) {
+                    rb = j;
+                    rpv = P.gat.rowptr[min(j + lane, P.nrhs)];
+                }
+                const int64_t beg = __shfl_sync(FULL, rpv, (int)(j - rb));
+                const int64_t end = __shfl_sync(FULL, rpv, (int)(j - rb) + 1);
                 for (int64_t p0 = beg; p0 < end; p0 += 32) {
                     const int64_t p = p0 + lane;
                     const int c = p < end ? P.gat.colidx[p] : 0;
                     const float v = p < end ? P.gat.vals[p] : 0.0f;
                     const int cnt = (int)min((int64_t)32, end - p0);
-                    for (int l = 0; l < cnt; ++l) {
+                    int l = 0;
+                    // Four entries at a time: their F rows are loaded before
+                    // the FMAs, which keep the entries' order.
+                    for (; l + 4 <= cnt; l += 4) {
+                        float fv[4][KW], vl[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int64_t cl = __shfl_sync(FULL, c, l + q);
+                            vl[q] = __shfl_sync(FULL, v, l + q);
+                            const float *frow = P.gat.F + cl * k;
+#pragma unroll
+                            for (int s = 0; s < KW; ++s) {
+                                const int i = lane + 32 * s;
+                                fv[q][s] = i < k ? frow[i] : 0.0f;
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+#pragma unroll
+                            for (int s = 0; s < KW; ++s)
+                                if (lane + 32 * s < k)
+                                    g[s] = fmaf(vl[q], fv[q][s], g[s]);
+                    }
+                    for (; l < cnt; ++l) {
                         const int64_t cl = __shfl_sync(FULL, c, l);
                         const float vl = __shfl_sync(FULL, v, l);
                         const float *frow = P.gat.F + cl * k;
