@@ -89,6 +89,13 @@ inline bool ranges_overlap(const void *a, const void *b, size_t bytes)
 // Internal launchers (all asynchronous on `s`).
 // ---------------------------------------------------------------------------
 
+// Gram X^T X on the tensor cores (gram_tc.cu): used by launch_gram when
+// gram_tc_usable (k <= 64, enough rows, X 16-byte aligned); writes
+// gram_tc_parts(rows) CTA partials in the layout of the SIMT Gram's.
+bool gram_tc_usable(const float *X, int64_t rows, int k);
+int gram_tc_parts(int64_t rows);
+nmf_status launch_gram_tc(const float *X, int64_t rows, int k, double *partials, cudaStream_t s);
+
 // Gram X^T X in FP64. `partials` must hold gram_partials_len(rows, k) doubles.
 int64_t gram_partials_len(int64_t rows, int k);
 nmf_status launch_gram(const float *X, int64_t rows, int k, double *G, double *partials,

@@ -246,6 +246,14 @@ int64_t gram_partials_len(int64_t rows, int k)
 nmf_status launch_gram(const float *X, int64_t rows, int k, double *G, double *partials,
                        cudaStream_t s)
 {
+    const int slots = gram_items(k, gram_threads_for(k)).NB * 16;
+    if (gram_tc_usable(X, rows, k)) {
+        NMF_TRY(launch_gram_tc(X, rows, k, partials, s));
+        gram_reduce_kernel<<<(int)cdiv(slots, 32), 256, 0, s>>>(partials, gram_tc_parts(rows), k,
+                                                                gram_threads_for(k), G);
+        NMF_LAUNCHED("gram_reduce_kernel");
+        return NMF_OK;
+    }
     const int parts = gram_parts(rows);
     if (k <= 16)
         gram_partial_kernel<16><<<parts, GRAM_THREADS, 0, s>>>(X, rows, k, partials);
@@ -256,7 +264,6 @@ nmf_status launch_gram(const float *X, int64_t rows, int k, double *G, double *p
     else
         gram_partial_kernel<128><<<parts, gram_threads<128>(), 0, s>>>(X, rows, k, partials);
     NMF_LAUNCHED("gram_partial_kernel");
-    const int slots = gram_items(k, gram_threads_for(k)).NB * 16;
     gram_reduce_kernel<<<(int)cdiv(slots, 32), 256, 0, s>>>(partials, parts, k,
                                                             gram_threads_for(k), G);
     NMF_LAUNCHED("gram_reduce_kernel");

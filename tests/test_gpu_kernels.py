@@ -49,6 +49,30 @@ def test_gram(nmf, k, rows):
     assert np.array_equal(G, G.T)
 
 
+@pytest.mark.parametrize("k", [1, 7, 16, 33, 50, 64])
+@pytest.mark.parametrize("signed", [False, True])
+def test_gram_tensor_cores(nmf, k, signed):
+    # Rows past 128 per SM take the tensor-core Gram (BF16 three-way splits,
+    # h^T h drained per 128-row tile into compensated sums): the same bound as
+    # the SIMT Gram's, a ragged last tile, and a view that is not 16-byte
+    # aligned (the SIMT path) giving the same answer within that bound.
+    rows = 128 * torch.cuda.get_device_properties(0).multi_processor_count * 2 + 77
+    rng = np.random.default_rng(70 + k)
+    lo = -1.0 if signed else 0.0
+    X = rng.uniform(lo, 1.0, (rows, k)).astype(np.float32)
+    ref = oracle.gram(X.astype(np.float64))
+    bound = 2e-6 * oracle.gram(np.abs(X).astype(np.float64)) + 1e-30
+    G = nmf.nmf_gram(dev(X)).cpu().numpy()
+    err = np.abs(G - ref) / bound
+    print(f"k={k} signed={signed}: max err / bound {err.max():.3f}")
+    assert np.all(np.abs(G - ref) <= bound)
+    assert np.array_equal(G, G.T)
+    buf = torch.empty(rows * k + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = dev(X).reshape(-1)
+    Gs = nmf.nmf_gram(buf[1:].view(rows, k)).cpu().numpy()
+    assert np.all(np.abs(Gs - ref) <= bound)
+
+
 # ----------------------------------------------------------------------------- products
 # Rows of A that are a multiple of 4 floats take the packed-FMA kernels (ragged
 # tiles, contraction splits of A^T W on the tall shapes); the others the
