@@ -13,14 +13,15 @@
 //    tiles with the 128-byte swizzle: per 64-row K-block, A = [h; m] (h for
 //    features 0..63 in operand rows 0..63, m in rows 64..127; zero past k)
 //    and l (rows 0..63);
-//  * one thread issues, per 16-row step, D_H = A h, D_R += A m and
-//    D_R += A l (M = 128, N = 64, BF16 operands, FP32 accumulators in TMEM).
+//  * one thread issues, per 16-row step, D_H = A h (N = 64) and
+//    D_R += A [m l] (N = 128: the l rows follow the m rows in shared memory;
+//    M = 128, BF16 operands, FP32 accumulators in TMEM).
 // The top half of D_H is h^T h, the tile's leading term: it is drained after
 // every tile into Kahan-compensated FP32 sums kept in TMEM (per group; 32
-// columns of the 64 top rows per drain warp). D_R, whose terms are 2^-8 of G or less,
-// accumulates over all the CTA's tiles: its top half is h^T (m + l), its
-// bottom half m^T (m + l). With lm and ll (below 2^-26 of G) dropped,
-// G = h^T h + m^T m + X + X^T, X = h^T (m + l),
+// columns of the 64 top rows per drain warp). D_R, whose terms are 2^-8 of G
+// or less, accumulates over all the CTA's tiles: [h^T m, h^T l] on top,
+// [m^T m, m^T l] below. With lm, ml and ll (below 2^-26 of G) dropped,
+// G = h^T h + m^T m + X + X^T, X = h^T m + h^T l,
 // formed per CTA in FP64 and written as upper-triangle 4 x 4 block partials
 // that the SIMT Gram's reduce kernel adds in CTA order.
 //
@@ -58,7 +59,7 @@ inline int gt_stages(int k)
     return n < GT_STG_MAX ? n : GT_STG_MAX;
 }
 inline int gt_smem(int k) { return GT_OFF_STG + gt_stages(k) * gt_stage_bytes(k) + 1024; }
-constexpr int GT_RS = 65;                          // row stride of the final D_R copy (floats)
+constexpr int GT_RS = 129;                         // row stride of the final D_R copy (floats)
 static_assert(128 * GT_RS * 4 <= 2 * GT_SPL_BYTES, "D_R copy fits the split buffers");
 
 __device__ __forceinline__ void split3(float v0, float v1, uint32_t &h, uint32_t &m, uint32_t &l)
@@ -150,11 +151,11 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
         // ---------------------------------------------------------------- MMAs
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_f32<64>();
+            const uint32_t idesc2 = idesc_bf16_f32<128>();
             const uint64_t spl0 = sw128_desc(sbase + GT_OFF_SPL);
             constexpr uint64_t SPL16 = (uint64_t)(GT_SPL_BYTES >> 4);
             constexpr uint64_t KB16 = (uint64_t)(GT_KB_BYTES >> 4);
-            constexpr uint64_t M16 = (uint64_t)(8192 >> 4);    // m rows of A (rows 64..127)
-            constexpr uint64_t L16 = (uint64_t)(16384 >> 4);   // l tile after A
+            constexpr uint64_t M16 = (uint64_t)(8192 >> 4);    // m rows of A, then l: [m l]
             const uint32_t dR = tmem + 128u;
             bool ok = true;
             for (int t = 0; t < nt && ok; ++t) {
@@ -174,8 +175,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
                                            (uint64_t)(kk * 2);
                         const bool step0 = kb == 0 && kk == 0;   // D_H starts each tile
                         mma_bf16(dH, a, a, idesc, step0 ? 0u : 1u);
-                        mma_bf16(dR, a, a + M16, idesc, (t == 0 && step0) ? 0u : 1u);
-                        mma_bf16(dR, a, a + L16, idesc, 1u);
+                        mma_bf16(dR, a, a + M16, idesc2, (t == 0 && step0) ? 0u : 1u);
                     }
                 }
                 mma_commit(spl_empty(b));
@@ -189,15 +189,15 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
         // Two groups of eight warps take alternate tiles (group g the tiles
         // t = g mod 2, split buffer g, D_H buffer g), so that one group's
         // waits overlap the other's work. TMEM columns: D_H 0..127, D_R
-        // 128..191, and for the h^T h rows (lanes 0..63) group g's Kahan
-        // sums at 192 + 128 g and compensations at 256 + 128 g. A drain warp
+        // 128..255, and for the h^T h rows (lanes 0..63) group g's Kahan
+        // sums at 256 + 128 g and compensations at 320 + 128 g. A drain warp
         // (lanes 32 quarter .. + 31, quarter 0 or 1) owns 32 columns of each.
         const int g = warp >> 3, gtid = threadIdx.x & 255;
         const int fi = gtid & 63;   // the feature this thread splits
         const int quarter = warp & 3, half = (warp >> 2) & 1;
         const bool drainer = quarter < 2;
         const uint32_t lanes = (uint32_t)(32 * quarter) << 16;
-        const uint32_t tks = tmem + lanes + 192u + 128u * g + 32u * half;   // sums; +64: comps
+        const uint32_t tks = tmem + lanes + 256u + 128u * g + 32u * half;   // sums; +64: comps
         if (drainer) {
             const float z[16] = {};
             tmem_st16(tks, z);
@@ -309,20 +309,23 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
         if (ok && drainer && last >= 0)
             ok = drain(last);
         // D_R once all MMAs are done: a copy in shared memory (the split
-        // buffers are free), rows 0..127 by 65 floats; warp w copies lanes
-        // 32 (w % 4) .. + 31, columns 16 (w / 4) .. + 15.
+        // buffers are free), rows 0..127 by 129 floats; warp w copies lanes
+        // 32 (w % 4) .. + 31, columns 32 (w / 4) .. + 31.
         float *Rs = reinterpret_cast<float *>(smem + GT_OFF_SPL);
         bool rok = ok && mbar_wait(r_full, 0, abort);
         rok = __all_sync(0xffffffffu, rok);
         if (rok) {
             tc_fence_after();
-            uint32_t r[16];
-            tmem_ld16_nowait(tmem + lanes + 128u + (uint32_t)(16 * (warp >> 2)), r);
-            tmem_wait_ld();
             const int row = 32 * quarter + lane;
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
-                Rs[row * GT_RS + 16 * (warp >> 2) + c] = __uint_as_float(r[c]);
+            for (int hh = 0; hh < 2; ++hh) {
+                uint32_t r[16];
+                tmem_ld16_nowait(tmem + lanes + 128u + (uint32_t)(32 * (warp >> 2) + 16 * hh), r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    Rs[row * GT_RS + 32 * (warp >> 2) + 16 * hh + c] = __uint_as_float(r[c]);
+            }
         }
         tc_fence_before();
         asm volatile("bar.sync 1, 512;" ::: "memory");
@@ -355,9 +358,9 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
                     continue;
                 double gij = ((double)__uint_as_float(s0[c]) - (double)__uint_as_float(c0[c])) +
                              ((double)__uint_as_float(s1[c]) - (double)__uint_as_float(c1[c]));
-                gij += (double)Rs[(64 + i) * GT_RS + j];
-                gij += (double)Rs[i * GT_RS + j];
-                gij += (double)Rs[j * GT_RS + i];
+                gij += (double)Rs[(64 + i) * GT_RS + j];                            // m^T m
+                gij += (double)Rs[i * GT_RS + j] + (double)Rs[i * GT_RS + 64 + j];   // X_ij
+                gij += (double)Rs[j * GT_RS + i] + (double)Rs[j * GT_RS + 64 + i];   // X_ji
                 const double v = good ? gij : (double)NAN;
                 const int blk = ta * TB - ta * (ta - 1) / 2 + (tb - ta);
                 out[blk * 16 + 4 * (i & 3) + (j & 3)] = v;
