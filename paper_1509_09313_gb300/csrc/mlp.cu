@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256)
 {
     extern __shared__ float sh[];
     float *Gs = sh;                              // k x k
-    float *stage_all = Gs + k * k;               // 8 warps x FEAT_R x 32 KW
+    float *stage_all = Gs + ((k * k + 3) & ~3);  // 8 warps x FEAT_R x 32 KW (16-byte aligned)
     __shared__ float s_mean;
     for (int e = threadIdx.x; e < k * k; e += blockDim.x)
         Gs[e] = (float)G[e];
@@ -73,12 +73,13 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *stage = stage_all + warp * FEAT_R * 32 * KW;
-    float d[KW], logd[KW];
+    float d[KW], rd[KW], logd[KW];
 #pragma unroll
     for (int s = 0; s < KW; ++s) {
         const int i = lane + 32 * s;
         const float gii = i < k ? Gs[i * k + i] : 0.0f;
         d[s] = gii > 0.0f ? sqrtf(gii) : 1.0f;
+        rd[s] = 1.0f / d[s];
         logd[s] = gii > 0.0f ? logf(gii / s_mean) : 0.0f;
     }
     // FEAT_R right-hand sides per pass of a warp: the row of G read for index
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(256)
                 g[r][s] = live && i < k ? B[j * k + i] : 0.0f;
                 x[r][s] = (live && i < k && Xp) ? Xp[j * k + i] : 0.0f;
                 y[r][s] = -g[r][s];
-                smax = fmaxf(smax, fabsf(g[r][s]) / d[s]);
+                smax = fmaxf(smax, fabsf(g[r][s]) * rd[s]);
             }
             for (int o = 16; o > 0; o >>= 1)
                 smax = fmaxf(smax, __shfl_xor_sync(FULL, smax, o));
@@ -111,7 +112,41 @@ __global__ void __launch_bounds__(256)
                 stage[(r * KW + s) * 32 + lane] = x[r][s];
         }
         __syncwarp();
-        for (int c = 0; c < k; ++c) {
+        // x_c of right-hand side r sits at stage[r 32 KW + c]: four of them
+        // per vector load. Rows of G past k are never read; lanes past k
+        // accumulate zeros.
+        int c = 0;
+        for (; c + 4 <= k; c += 4) {
+            float rv[4][KW];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int s = 0; s < KW; ++s) {
+                    const int i = lane + 32 * s;
+                    rv[q][s] = i < k ? Gs[(c + q) * k + i] : 0.0f;
+                }
+#pragma unroll
+            for (int r = 0; r < FEAT_R; ++r) {
+                const float4 xv = *reinterpret_cast<const float4 *>(stage + r * 32 * KW + c);
+                const float xq[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if constexpr (KW == 1) {
+                        y[r][0] = fmaf(rv[q][0], xq[q], y[r][0]);
+                    } else {
+#pragma unroll
+                        for (int s = 0; s < KW; s += 2) {
+                            const float2 t = __ffma2_rn(make_float2(rv[q][s], rv[q][s + 1]),
+                                                        make_float2(xq[q], xq[q]),
+                                                        make_float2(y[r][s], y[r][s + 1]));
+                            y[r][s] = t.x;
+                            y[r][s + 1] = t.y;
+                        }
+                    }
+                }
+            }
+        }
+        for (; c < k; ++c) {
             const float *row = Gs + c * k;
             float rv[KW];
 #pragma unroll
@@ -119,14 +154,12 @@ __global__ void __launch_bounds__(256)
                 const int i = lane + 32 * s;
                 rv[s] = i < k ? row[i] : 0.0f;
             }
-            const int cs = c >> 5, cl = c & 31;
 #pragma unroll
             for (int r = 0; r < FEAT_R; ++r) {
-                const float xc = stage[(r * KW + cs) * 32 + cl];
+                const float xc = stage[r * 32 * KW + c];
 #pragma unroll
                 for (int s = 0; s < KW; ++s)
-                    if (lane + 32 * s < k)
-                        y[r][s] = fmaf(rv[s], xc, y[r][s]);
+                    y[r][s] = fmaf(rv[s], xc, y[r][s]);
             }
         }
         __syncwarp();
@@ -141,7 +174,7 @@ __global__ void __launch_bounds__(256)
                 for (int s = 0; s < KW; ++s) {
                     const int i = lane + 32 * s;
                     if (i < k) {
-                        f[i] = y[r][s] / d[s] * sc[r];
+                        f[i] = y[r][s] * rd[s] * sc[r];
                         f[k + i] = logd[s];
                         f[2 * k + i] = x[r][s] * d[s] * sc[r];
                     }
@@ -157,7 +190,7 @@ __global__ void __launch_bounds__(256)
                 for (int s = 0; s < KW; ++s) {
                     const int i = lane + 32 * s;
                     if (i < k) {
-                        put(i, y[r][s] / d[s] * sc[r]);
+                        put(i, y[r][s] * rd[s] * sc[r]);
                         put(kpf + i, logd[s]);
                         put(2 * kpf + i, x[r][s] * d[s] * sc[r]);
                     }
@@ -448,7 +481,7 @@ nmf_status launch_features(const double *G, const float *B, const float *Xp, int
     if (nrhs == 0)
         return NMF_OK;
     const int kw = (k + 31) / 32;
-    const size_t smem = sizeof(float) * ((size_t)k * k + 8 * FEAT_R * 32 * kw);
+    const size_t smem = sizeof(float) * ((size_t)((k * k + 3) & ~3) + 8 * FEAT_R * 32 * kw);
     const unsigned blocks = (unsigned)std::min<int64_t>(cdiv(nrhs, 8 * FEAT_R), 4 * sm_count());
     auto go = [&](auto kern) -> nmf_status {
         if (smem > 48 * 1024)
@@ -603,7 +636,7 @@ nmf_status launch_mlp_features_split(const double *G, const float *B, const floa
     if (kpf < k || 3 * kpf > ldd || (ldd % 8))
         return NMF_ERR_INVALID_ARG;
     const int kw = (k + 31) / 32;
-    const size_t smem = sizeof(float) * ((size_t)k * k + 8 * FEAT_R * 32 * kw);
+    const size_t smem = sizeof(float) * ((size_t)((k * k + 3) & ~3) + 8 * FEAT_R * 32 * kw);
     const unsigned blocks = (unsigned)std::min<int64_t>(cdiv(nrhs, 8 * FEAT_R), 4 * sm_count());
     auto go = [&](auto kern) -> nmf_status {
         if (smem > 48 * 1024)
