@@ -16,9 +16,10 @@
 //  * one thread issues, per 16-row step, D_H = A h (N = 64) and
 //    D_R += A [m l] (N = 128: the l rows follow the m rows in shared memory;
 //    M = 128, BF16 operands, FP32 accumulators in TMEM).
-// The top half of D_H is h^T h, the tile's leading term: it is drained after
-// every tile into Kahan-compensated FP32 sums kept in TMEM (per group; 32
-// columns of the 64 top rows per drain warp). D_R, whose terms are 2^-8 of G
+// The top half of D_H is h^T h, the leading term: it accumulates a pair of
+// tiles (256 rows), then is drained into Kahan-compensated FP32 sums kept in
+// TMEM (per group; 32 columns of the 64 top rows per drain warp). D_R, whose
+// terms are 2^-8 of G
 // or less, accumulates over all the CTA's tiles: [h^T m, h^T l] on top,
 // [m^T m, m^T l] below. With lm, ml and ll (below 2^-26 of G) dropped,
 // G = h^T h + m^T m + X + X^T, X = h^T m + h^T l,
@@ -128,6 +129,10 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
     const int64_t ntiles = (rows + GT_ROWS - 1) / GT_ROWS;
     const int nt = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);   // >= 1
     auto tile_row0 = [&](int t) { return ((int64_t)blockIdx.x + (int64_t)t * gridDim.x) * GT_ROWS; };
+    // D_H of group g (tiles t = g mod 2) holds a pair of the group's tiles
+    // (256 rows) between drains: tile t is the (t / 2)-th of its group, in
+    // pair t / 4; a pair ends at its second tile or at the group's last.
+    auto pair_end = [&](int t) { return ((t >> 1) & 1) == 1 || t + 2 >= nt; };
     const uint32_t tile_bytes = (uint32_t)(GT_ROWS * k * 4);
 
     if (warp == GT_WORKERS) {
@@ -160,8 +165,9 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
             bool ok = true;
             for (int t = 0; t < nt && ok; ++t) {
                 const int b = t & 1, ub = t >> 1;
+                const bool pair_start = (ub & 1) == 0;
                 if (!mbar_wait_fast(spl_full(b), ub & 1, abort) ||
-                    !mbar_wait_fast(acc_empty(b), (ub & 1) ^ 1, abort)) {
+                    (pair_start && !mbar_wait_fast(acc_empty(b), ((ub >> 1) & 1) ^ 1, abort))) {
                     ok = false;
                     break;
                 }
@@ -173,13 +179,14 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
                     for (int kk = 0; kk < 4; ++kk) {
                         const uint64_t a = spl0 + (uint64_t)b * SPL16 + (uint64_t)kb * KB16 +
                                            (uint64_t)(kk * 2);
-                        const bool step0 = kb == 0 && kk == 0;   // D_H starts each tile
-                        mma_bf16(dH, a, a, idesc, step0 ? 0u : 1u);
+                        const bool step0 = kb == 0 && kk == 0;   // D_H starts each pair
+                        mma_bf16(dH, a, a, idesc, (pair_start && step0) ? 0u : 1u);
                         mma_bf16(dR, a, a + M16, idesc2, (t == 0 && step0) ? 0u : 1u);
                     }
                 }
                 mma_commit(spl_empty(b));
-                mma_commit(acc_full(b));
+                if (pair_end(t))
+                    mma_commit(acc_full(b));
             }
             if (ok)
                 mma_commit(r_full);
@@ -206,9 +213,9 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
             tmem_st16(tks + 80u, z);
             tmem_wait_st();
         }
-        auto drain = [&](int t) -> bool {
-            const int b = t & 1, ub = t >> 1;
-            if (!mbar_wait(acc_full(b), ub & 1, abort))
+        auto drain = [&](int t) -> bool {   // the pair that tile t ends
+            const int b = t & 1, pr = t >> 2;
+            if (!mbar_wait(acc_full(b), pr & 1, abort))
                 return false;
             tc_fence_after();
 #pragma unroll
@@ -300,7 +307,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
                 mbar_arrive(spl_full(b));
                 mbar_arrive(stg_empty(s));
             }
-            if (drainer && t >= 2 && !drain(t - 2)) {
+            if (drainer && t >= 2 && pair_end(t - 2) && !drain(t - 2)) {
                 ok = false;
                 break;
             }
