@@ -19,9 +19,8 @@
 // The top half of D_H is h^T h, the leading term: it accumulates a pair of
 // tiles (256 rows), then is drained into Kahan-compensated FP32 sums kept in
 // TMEM (per group; 32 columns of the 64 top rows per drain warp). D_R, whose
-// terms are 2^-8 of G
-// or less, accumulates over all the CTA's tiles: [h^T m, h^T l] on top,
-// [m^T m, m^T l] below. With lm, ml and ll (below 2^-26 of G) dropped,
+// terms are 2^-8 of G or less, accumulates over all the CTA's tiles:
+// [h^T m, h^T l] on top, [m^T m, m^T l] below. With lm, ml and ll (below 2^-26 of G) dropped,
 // G = h^T h + m^T m + X + X^T, X = h^T m + h^T l,
 // formed per CTA in FP64 and written as upper-triangle 4 x 4 block partials
 // that the SIMT Gram's reduce kernel adds in CTA order.
