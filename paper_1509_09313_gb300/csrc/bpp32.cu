@@ -597,7 +597,8 @@ __global__ void __launch_bounds__(S32_MAX_WARPS * 32, KW == 4 ? 1 : 2)
                     __syncwarp();
                     float inv[PT], rp = 0.0f;
                     if constexpr (KW <= 2) {
-                        if (p > 0 && !ldl_regs<KW, PM>(comp ? Ms : Gs, widx, wcol, p, Lw, LS, rp, lane))
+                        if (p > 0 &&
+                            !ldl_regs<KW, PM>(comp ? Ms : Gs, widx, wcol, p, Lw, LS, rp, lane))
                             return DEFERRED;
                     } else {
                         if (p > 0 && !chol32<KW, PT>(comp ? Ms : Gs, widx, p, Lw, LS, inv, lane))

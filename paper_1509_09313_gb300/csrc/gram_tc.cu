@@ -20,8 +20,8 @@
 // tiles (256 rows), then is drained into Kahan-compensated FP32 sums kept in
 // TMEM (per group; 32 columns of the 64 top rows per drain warp). D_R, whose
 // terms are 2^-8 of G or less, accumulates over all the CTA's tiles:
-// [h^T m, h^T l] on top, [m^T m, m^T l] below. With lm, ml and ll (below 2^-26 of G) dropped,
-// G = h^T h + m^T m + X + X^T, X = h^T m + h^T l,
+// [h^T m, h^T l] on top, [m^T m, m^T l] below. With lm, ml and ll (below
+// 2^-26 of G) dropped, G = h^T h + m^T m + X + X^T, X = h^T m + h^T l,
 // formed per CTA in FP64 and written as upper-triangle 4 x 4 block partials
 // that the SIMT Gram's reduce kernel adds in CTA order.
 //
@@ -127,7 +127,9 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
 
     const int64_t ntiles = (rows + GT_ROWS - 1) / GT_ROWS;
     const int nt = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);   // >= 1
-    auto tile_row0 = [&](int t) { return ((int64_t)blockIdx.x + (int64_t)t * gridDim.x) * GT_ROWS; };
+    auto tile_row0 = [&](int t) {
+        return ((int64_t)blockIdx.x + (int64_t)t * gridDim.x) * GT_ROWS;
+    };
     // D_H of group g (tiles t = g mod 2) holds a pair of the group's tiles
     // (256 rows) between drains: tile t is the (t / 2)-th of its group, in
     // pair t / 4; a pair ends at its second tile or at the group's last.
@@ -293,7 +295,8 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
                         split3(v[q][2 * w], v[q][2 * w + 1], h[w], m[w], l[w]);
                     unsigned char *blk = spl + (c >> 3) * GT_KB_BYTES;
                     const uint32_t sw = (uint32_t)(((c & 7) ^ (fi & 7)) << 4);
-                    *reinterpret_cast<uint4 *>(blk + fi * 128 + sw) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4 *>(blk + fi * 128 + sw) =
+                        make_uint4(h[0], h[1], h[2], h[3]);
                     *reinterpret_cast<uint4 *>(blk + (64 + fi) * 128 + sw) =
                         make_uint4(m[0], m[1], m[2], m[3]);
                     *reinterpret_cast<uint4 *>(blk + 16384 + fi * 128 + sw) =
