@@ -124,6 +124,31 @@ def test_sparse_objective_standalone(nmf):
     h.nmf_destroy()
 
 
+def test_sparse_set_factors_resume(nmf):
+    # A sparse handle reuses the Gram of H formed by the objective for the next
+    # W half-step; replacing H^T must drop it. After set_factors the handle
+    # continues bitwise like a fresh handle started from the same factors.
+    m, n, k = 3000, 2000, 20
+    csr = synth.csr_uniform(m, n, 60000, seed=9)
+    W0, Ht0 = synth.init_factors(m, n, k, seed=9)
+    dcsr = tuple(dev(x) for x in csr)
+    h = nmf.nmf_init(dcsr, dev(W0), dev(Ht0), shape=(m, n), start="warm")
+    h.nmf_iterate(3)
+    W3, H3 = h.nmf_get_factors()
+    Hp = (H3 * 1.25 + 0.01).contiguous()
+    h.nmf_set_factors(W3.contiguous(), Hp)
+    h.nmf_iterate(2)
+    W5, H5 = h.nmf_get_factors()
+    h2 = nmf.nmf_init(dcsr, W3.contiguous(), Hp.clone(), shape=(m, n), start="warm")
+    h2.nmf_iterate(2)
+    W5b, H5b = h2.nmf_get_factors()
+    assert torch.equal(W5, W5b) and torch.equal(H5, H5b)
+    f, f2 = h.nmf_objective(), h2.nmf_objective()
+    assert f == f2
+    h.nmf_destroy()
+    h2.nmf_destroy()
+
+
 def _bf16x3_runs(nmf, A, W0, Ht0, T):
     # The same run with and without the pre-split copies of A and A^T.
     out = []
